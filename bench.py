@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the tiled band bidiagonalization (GE2BND) on GB300.
+
+One step = one full reduction B = Q^T A P (pack, the whole task DAG of QR/LQ panel and update kernels,
+band extraction) of one synthetic matrix already resident in HBM.  Throughput is counted with the
+paper's operation count for BiDiag, 4 m n^2 - 4 n^3 / 3 flops (Sec. 6.2 credits R-BiDiag with the same
+count), reported in TFLOP/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--tree T] [--impl ours|reference]
+
+N > 1 (torchrun, one process per GPU): independent replicas, one matrix per rank, no collective on the
+data path; value = total flops of all ranks / max-over-ranks time ("scaling": "weak").
+--impl reference times the plain CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "square8192": dict(m=8192, n=8192, nb=256, ib=32, variant="bidiag", kind="sv", seeds=(2, 3),
+                       desc="square FP64 8192x8192, A = U diag(s) V^T (Haar U, V; s geometric 1..1e-8), "
+                            "nb=256 ib=32, BiDiag"),
+    "square512": dict(m=512, n=512, nb=64, ib=16, variant="bidiag", kind="gauss", seeds=(1,),
+                      desc="square FP64 512x512 N(0,1), nb=64 ib=16, BiDiag"),
+    "tall65536x1024": dict(m=65536, n=1024, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(4,),
+                           desc="tall-skinny FP64 65536x1024 N(0,1), nb=256 ib=32, R-BiDiag"),
+    "tall65536x2048": dict(m=65536, n=2048, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(5,),
+                           desc="tall-skinny FP64 65536x2048 N(0,1), nb=256 ib=32, R-BiDiag"),
+}
+# FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock/SM (4 flops) x
+# 2070 MHz = 1258.6 GFLOP/s (a DFMA loop measured 1.20 TFLOP/s, cuBLAS DGEMM 1.10, FP64 MMA 1.05).
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+# DRAM bytes per executor launch from the ncu capture summarised under profiles/ (None until taken
+# for the current kernel).
+EXEC_TRAFFIC_BYTES = None
+CPU_SAMPLE_SECONDS = 12.0
+
+
+def metric_flops(m, n):
+    return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
+
+
+def make_input(w, rank, device):
+    from paper_1611_06892_gb300 import inputs
+    m, n = w["m"], w["n"]
+    if w["kind"] == "sv":
+        s = inputs.geometric_sv(n)
+        su, sv = w["seeds"]
+        return inputs.torch_prescribed_singular_values(m, n, s, su + 1000 * rank, sv + 1000 * rank, device)
+    return inputs.torch_gaussian(m, n, w["seeds"][0] + 1000 * rank, device)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_sample(path, w, tree, seconds, max_tasks=None):
+    """Times the oracle (single BLAS thread) on the first tasks of the workload's task list."""
+    import numpy as np
+
+    from oracle import bidiag as OB
+    from oracle import trees as T
+
+    A = np.load(path, mmap_mode="r")
+    variant = {"bidiag": T.BIDIAG, "rbidiag": T.RBIDIAG}[w["variant"]]
+    treec = {"flatts": T.FLATTS, "flattt": T.FLATTT, "greedy": T.GREEDY, "auto": T.AUTO}[tree]
+    st = OB.new_state(np.asarray(A), w["nb"], w["ib"], treec, variant, resources=w.get("resources", 152))
+    units = 0
+    done = 0
+    t0 = time.perf_counter()
+    for idx, t in enumerate(st["tasks"]):
+        OB.run_tasks(st, [(idx, t)])
+        units += T.WEIGHT[t[0]]
+        done += 1
+        if time.perf_counter() - t0 > seconds or (max_tasks and done >= max_tasks):
+            break
+    el = time.perf_counter() - t0
+    flops = units * w["nb"] ** 3 / 3.0
+    return {"tasks": done, "total_tasks": len(st["tasks"]), "flops": flops, "seconds": el}
+
+
+def run_cpu_sample_subprocess(A_host_np, w, tree, seconds, max_tasks=None):
+    import numpy as np
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "A.npy")
+        np.save(path, A_host_np)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", path, "--workload", w["name"],
+               "--tree", tree, "--cpu-seconds", str(seconds)]
+        if max_tasks:
+            cmd += ["--cpu-max-tasks", str(max_tasks)]
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        if out.returncode != 0:
+            raise RuntimeError(out.stderr[-2000:])
+        return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS))
+    ap.add_argument("--tree", default="auto", choices=("flatts", "flattt", "greedy", "auto"))
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=CPU_SAMPLE_SECONDS)
+    ap.add_argument("--cpu-max-tasks", type=int, default=None)
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload], name=args.workload)
+    if args.workload == "square512" and args.tree == "auto":
+        args.tree = "flatts"
+
+    if args.cpu_sample:
+        r = cpu_sample(args.cpu_sample, w, args.tree, args.cpu_seconds, args.cpu_max_tasks)
+        print(json.dumps(r))
+        return 0
+
+    world, rank, local = dist_setup()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
+    flops = metric_flops(m, n)
+    config = {"workload": w["desc"] + f", tree={args.tree}", "m": m, "n": n, "nb": nb, "ib": ib,
+              "tree": args.tree, "variant": w["variant"],
+              "l2": f"input {m * n * 8 / 2**20:.0f} MiB > 129 MB L2 (no flush needed)" if m * n * 8 > 129e6
+              else "input smaller than L2"}
+    base = {"metric": "GE2BND TFLOP/s (4mn^2 - 4n^3/3 flops)", "unit": "TFLOP/s", "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config}
+
+    if args.impl == "reference":
+        # the plain CPU oracle on bounded samples of the same workload; rank 0 only
+        if rank != 0:
+            return 0
+        A = make_input(w, 0, device)
+        A_host = A.cpu().numpy()
+        del A
+        torch.cuda.empty_cache()
+        per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+        res = [run_cpu_sample_subprocess(A_host, w, args.tree, per_step) for _ in range(args.warmup + args.steps)]
+        timed = res[args.warmup:]
+        val = sum(r["flops"] for r in timed) / sum(r["seconds"] for r in timed) / 1e12
+        sample = (f"first {timed[0]['tasks']} of {timed[0]['total_tasks']} tasks of the task list "
+                  f"(~{per_step:.0f} s each step), single BLAS thread")
+        line = dict(base, impl="reference", value=val, ms_per_step=1e3 * statistics.mean(r["seconds"] for r in timed),
+                    cpu_baseline={"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+                    e2e={"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                    gpu_launches=0)
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import paper_1611_06892_gb300 as G
+    if not os.path.exists(G.LIB_PATH):
+        from paper_1611_06892_gb300 import build
+        build.build()
+    G.load_library()
+
+    A = make_input(w, rank, device)
+    h = G.Handle(device=local)
+    h.set_option(G.OPT_TIMING, 1)
+    stream = h.stream
+
+    def step():
+        r = h.band(A, nb, ib, args.tree, w["variant"])
+        h.sync()
+        ms = h.last_exec_ms()
+        r.free()
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    exec_ms = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    el_ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    ms_per_step = el_ms / args.steps
+    value = world * flops / (ms_per_step * 1e-3) / 1e12
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    A_host = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    A_host.copy_(A)
+    ab_host = torch.empty((n, nb + 1), dtype=torch.float64, pin_memory=True).t()
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        barrier(world)
+        t0 = time.perf_counter()
+        G.bidiag_band_host(h.h, m, n, A_host.data_ptr(), m, nb, ib, G.TREES[args.tree], G.VARIANTS[w["variant"]],
+                           ab_host.data_ptr(), nb + 1)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device)
+
+    exec_mean = statistics.mean(exec_ms)
+    achieved = flops / (exec_mean * 1e-3) / 1e9
+    line = dict(base, value=value, ms_per_step=ms_per_step,
+                e2e={"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": m * n * 8,
+                     "d2h_bytes_per_step": (nb + 1) * n * 8},
+                roofline={"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": EXEC_TRAFFIC_BYTES,
+                          "kernel": "exec_kernel (persistent dataflow executor)",
+                          "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"},
+                exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
+    if world == 1 and rank == 0 and not args.no_cpu:
+        A_np = A.cpu().numpy()
+        r = run_cpu_sample_subprocess(A_np, w, args.tree, CPU_SAMPLE_SECONDS)
+        line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {r['tasks']} of {r['total_tasks']} tasks of the same task list "
+                                          f"({r['seconds']:.1f} s), single BLAS thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * bidiag.h - C ABI of the GB300 tiled band-bidiagonalization library.
+ *
+ * The library reduces a dense real m x n matrix A (m >= n) to upper band-bidiagonal form
+ *     B = Q^T A P,   Q (m x m) and P (n x n) orthogonal,  B with nb super-diagonals,
+ * with the tiled BiDiag and R-BiDiag algorithms (Faverge, Langou, Robert, Dongarra, "Bidiagonalization
+ * with parallel tiled algorithms", Sec. 3.4 and 3.5), whose QR and LQ steps eliminate tiles with the
+ * GEQRT/TSQRT/TTQRT panel kernels and UNMQR/TSMQR/TTMQR update kernels of Table 1 (Sec. 3.2, Algorithms
+ * 2 and 3; LQ steps use the same kernels on the transposed geometry, Algorithm 4), scheduled by the
+ * FlatTS, FlatTT, Greedy (Sec. 3.3) or Auto (Sec. 5) reduction tree.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major, FP64, sizes are int64_t.  Pointers named d_* are device pointers on the
+ *    handle's device; pointers named h_* are host pointers.
+ *  - Return value: BIDIAG_OK (0) on success; a negative value -i when argument i (1-based) is invalid
+ *    (LAPACK "info" style); a positive BIDIAG_ERR_* code otherwise.  No function throws across the ABI.
+ *    bidiag_last_error() returns a text for the last failure on a handle.
+ *  - Work is stream-ordered on the handle's stream; results are valid once bidiag_sync() returned
+ *    BIDIAG_OK (bidiag_band_host synchronises by itself).
+ *  - Tile indices are 0-based.  Tile (a, b) covers rows [a nb, min((a+1) nb, m)) and columns
+ *    [b nb, min((b+1) nb, n)); the last tile row/column may be ragged.
+ */
+#ifndef BIDIAG_H
+#define BIDIAG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bidiag_ctx* bidiag_handle;
+typedef struct bidiag_result* bidiag_result_t;
+
+/* Reduction trees: Sec. 3.3 (FlatTS, FlatTT, Greedy) and Sec. 5 (Auto). */
+enum { BIDIAG_FLATTS = 0, BIDIAG_FLATTT = 1, BIDIAG_GREEDY = 2, BIDIAG_AUTO = 3 };
+/* Variants: Sec. 3.4 (BiDiag) and Sec. 3.5 (R-BiDiag = QR(p,q) then BiDiag of the top square). */
+enum { BIDIAG_BIDIAG = 0, BIDIAG_RBIDIAG = 1 };
+/* Status codes. */
+enum {
+  BIDIAG_OK = 0,
+  BIDIAG_ERR_CUDA = 1,        /* a CUDA runtime call failed; text in bidiag_last_error */
+  BIDIAG_ERR_NOMEM = 2,       /* device or host allocation failed */
+  BIDIAG_ERR_TIMEOUT = 3,     /* a device-side dependency wait ran out (see bidiag_set_option) */
+  BIDIAG_ERR_UNSUPPORTED = 4  /* valid but unsupported request, e.g. m < n */
+};
+/* Options for bidiag_set_option. */
+enum {
+  BIDIAG_OPT_WAIT_LIMIT_NS = 1,   /* bound of every device-side dependency wait, ns (default 2e10) */
+  BIDIAG_OPT_AUTO_RESOURCES = 2,  /* "nbcores" R of the Auto tree (default: the device's SM count) */
+  BIDIAG_OPT_DEBUG_UNSET_DEP = 3, /* 1: the next bidiag_band adds to its first task a dependency on a
+                                     flag nothing sets, so that its wait runs out (failure-path test) */
+  BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16 or 32, default 32) */
+  BIDIAG_OPT_TIMING = 5           /* 1: time the executor launch of each bidiag_band with CUDA events */
+};
+
+/* Task type codes of the canonical task list (GELQT etc. are the same codes in LQ phases). */
+enum { BIDIAG_T_GEQRT = 0, BIDIAG_T_UNMQR = 1, BIDIAG_T_TSQRT = 2, BIDIAG_T_TSMQR = 3,
+       BIDIAG_T_TTQRT = 4, BIDIAG_T_TTMQR = 5, BIDIAG_T_COPY = 6 };
+/* Phase codes: QR / LQ steps of BiDiag (R-BiDiag: of the second phase), PQR = R-BiDiag's QR(p,q). */
+enum { BIDIAG_PH_QR = 0, BIDIAG_PH_LQ = 1, BIDIAG_PH_PQR = 2 };
+
+/*
+ * Reflector store of a result (Sec. 3.6 "Memory usage": R-BiDiag keeps its pre-QR reflectors apart).
+ * All pointers are device pointers owned by the result.
+ *  tiles   : p*q tiles of nb*nb doubles, tile (a, b) at tiles + (b*p + a)*nb*nb, column-major inside
+ *            with leading dimension nb, zero padded beyond m / n.  After the reduction it holds the
+ *            Householder vectors of every tile kernel in the positions they eliminated (GEQRT/GELQT:
+ *            strict lower/upper triangle; TSQRT: the whole eliminated tile; TTQRT: the upper/lower
+ *            triangle of the eliminated tile) and, for BiDiag, the band entries.
+ *  tiles2  : R-BiDiag only (else NULL): q*q tiles, same layout, holding the second phase.
+ *  T       : one block of ib*nb doubles per panel task (tslot order): the ib x ib upper-triangular T
+ *            factors of the compact WY form of each group of ib reflectors side by side
+ *            (block b at T + slot*ib*nb + b*ib*ib, column-major, ld ib); tau_j = diag(T).
+ *  tslot   : host array, one entry per canonical task: its T slot for a panel task, -1 otherwise.
+ */
+typedef struct bidiag_reflectors {
+  const double* tiles;
+  const double* tiles2;
+  const double* T;
+  const int32_t* tslot;
+  int64_t ntasks;
+  int64_t m, n;
+  int32_t nb, ib, p, q, npanels, variant;
+} bidiag_reflectors;
+
+/* Creates a handle bound to CUDA device `device` and stream `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  Owns the plan cache and the scheduler workspace.
+ * Errors: -1 (h NULL), -2 (bad device), BIDIAG_ERR_CUDA, BIDIAG_ERR_NOMEM. */
+int bidiag_create(bidiag_handle* h, int device, void* cuda_stream);
+
+/* Sets an option (BIDIAG_OPT_*) on the handle.  Errors: -2 unknown option, -3 bad value. */
+int bidiag_set_option(bidiag_handle h, int option, int64_t value);
+
+/*
+ * GE2BND: reduces the m x n matrix at d_A (device, column-major, leading dimension lda; read only) to
+ * band form with tile size nb, inner blocking ib (Sec. 6.2: internal blocking of the TS/TT kernels),
+ * tree and variant.  Preconditions (else -i): m >= 1 (-2), 1 <= n (-3), d_A != NULL (-4), lda >= m
+ * (-5), 1 <= nb <= 256 (-6), 1 <= ib <= min(nb, 64) and nb % ib == 0 (-7), tree in 0..3 (-8), variant
+ * in 0..1 (-9), out != NULL (-10).  m < n returns BIDIAG_ERR_UNSUPPORTED (Sec. 3.6: the transposed
+ * problem).  *out receives a new result object (free with bidiag_result_free) that owns the band, the
+ * reflector store and the canonical task list.  The call enqueues the work and returns.
+ */
+int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_t lda,
+                int nb, int ib, int tree, int variant, bidiag_result_t* out);
+
+/*
+ * Same reduction for host buffers: copies h_A (column-major, lda) to the device, reduces it, copies the
+ * band back into h_ab (LAPACK upper-band storage, (nb+1) x n, leading dimension ldab >= nb+1) and
+ * synchronises.  h_A and h_ab should be pinned for full copy speed.  The result object is kept in *out
+ * when out != NULL (else freed).  Errors as bidiag_band, plus -11 (h_ab NULL) and -12 (ldab).
+ */
+int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, int64_t lda,
+                     int nb, int ib, int tree, int variant, double* h_ab, int64_t ldab,
+                     bidiag_result_t* out);
+
+/* Band B in LAPACK upper-band storage (device): B(i, j) at ab[(nb + i - j) + j*ldab] for
+ * max(0, j-nb) <= i <= j < n, ldab = nb + 1.  B is n x n (rows n..m-1 of Q^T A P are zero); every
+ * entry outside the band is an exact zero by construction. */
+int bidiag_result_band(bidiag_result_t r, const double** ab, int64_t* ldab, int64_t* n, int* nb);
+
+/* Canonical task list (host memory owned by the result): ntasks records of 6 int32
+ * (type, phase, k, i, piv, j) in program order, oriented coordinates (an LQ step's oriented tile (a,b)
+ * is tile (b,a)); -1 where a field is unused.  COPY(i, j) copies tile (i, j)'s R into the second
+ * phase of R-BiDiag. */
+int bidiag_result_tasks(bidiag_result_t r, const int32_t** tasks, int64_t* ntasks);
+
+/* Fills *desc with the reflector store (see bidiag_reflectors). */
+int bidiag_result_reflectors(bidiag_result_t r, bidiag_reflectors* desc);
+
+/* Applies Q from the result to the m x ncols device matrix d_C (leading dimension ldc >= m):
+ * trans = 0: C <- Q C, trans = 1: C <- Q^T C.  Errors: -3 trans, -4 ncols < 0, -5 d_C, -6 ldc. */
+int bidiag_apply_q(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols, double* d_C,
+                   int64_t ldc);
+
+/* Applies P from the result to the nrows x n device matrix d_C (leading dimension ldc >= nrows):
+ * trans = 0: C <- C P, trans = 1: C <- C P^T.  Errors: -3 trans, -4 nrows < 0, -5 d_C, -6 ldc. */
+int bidiag_apply_p(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, double* d_C,
+                   int64_t ldc);
+
+/* Waits for the handle's stream and returns the device-side status of the work enqueued since the
+ * last call: BIDIAG_OK, BIDIAG_ERR_TIMEOUT (a dependency wait ran out; the context stays usable) or
+ * BIDIAG_ERR_CUDA. */
+int bidiag_sync(bidiag_handle h);
+
+/* Duration (ms, CUDA events on the handle's stream) of the executor kernel of the last bidiag_band
+ * enqueued with BIDIAG_OPT_TIMING on; call after bidiag_sync.  Errors: -2 ms NULL, BIDIAG_ERR_UNSUPPORTED
+ * when timing was off. */
+int bidiag_last_exec_ms(bidiag_handle h, float* ms);
+
+/* Text of the last failure on the handle ("" if none).  Valid until the next call on h. */
+const char* bidiag_last_error(bidiag_handle h);
+
+/* Releases a result (stream-ordered on the handle's stream that made it). */
+int bidiag_result_free(bidiag_result_t r);
+
+/* Releases the handle (synchronises its stream first). */
+int bidiag_destroy(bidiag_handle h);
+
+/* ---------------------------------------------------------------------------------------------
+ * Host-only planner queries (no device work; usable without a GPU).  They expose the planner's
+ * elimination list, task list and task DAG so that they can be checked against the paper's critical
+ * path formulas (Sec. 4) and an independent implementation.  `resources` is the Auto tree's R.
+ * --------------------------------------------------------------------------------------------- */
+
+/* Canonical elimination list: records of 5 int32 (phase, k, i, piv, kind[0 = TS, 1 = TT]).  When
+ * out == NULL or cap is too small only *count is set. */
+int bidiag_plan_eliminations(int64_t p, int64_t q, int tree, int variant, int64_t resources,
+                             int32_t* out, int64_t cap, int64_t* count);
+
+/* Canonical task list, 6 int32 per task as in bidiag_result_tasks, plus its DAG: level[t] (0 without
+ * predecessors, else 1 + max level of its predecessors) when level != NULL, and the critical path in
+ * Table 1 units (GEQRT 4, UNMQR 6, TSQRT 6, TSMQR 12, TTQRT 2, TTMQR 6, COPY 0) in *cp when cp != NULL. */
+int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resources,
+                      int32_t* tasks, int32_t* level, int64_t cap, int64_t* count, int64_t* cp);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIDIAG_H */

@@ -1,0 +1,302 @@
+"""Python binding of the GB300 tiled band-bidiagonalization library (``libbidiag.so``, C ABI in
+``include/bidiag.h``).
+
+Argument marshalling only: every step of the reduction runs in the library's CUDA kernels; PyTorch
+provides device memory and streams.  The library must have been built (``build.build()``); importing
+the binding without it raises immediately - there is no CPU fallback.
+
+Low-level functions carry the C names (``bidiag_create``, ``bidiag_band``, ...); ``Handle`` and
+``Result`` wrap them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbidiag.so")
+
+FLATTS, FLATTT, GREEDY, AUTO = 0, 1, 2, 3
+TREES = {"flatts": FLATTS, "flattt": FLATTT, "greedy": GREEDY, "auto": AUTO}
+BIDIAG, RBIDIAG = 0, 1
+VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG}
+OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING = 1, 2, 3, 4, 5
+
+_lib = None
+
+
+class BidiagError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bidiag error {code}: {msg}")
+        self.code = code
+
+
+class Reflectors(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_void_p), ("tiles2", ctypes.c_void_p), ("T", ctypes.c_void_p),
+                ("tslot", ctypes.POINTER(ctypes.c_int32)), ("ntasks", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("q", ctypes.c_int32), ("npanels", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
+
+
+def load_library(path=LIB_PATH):
+    """Loads libbidiag.so (raises if it is missing: build it with paper_1611_06892_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run `python -m paper_1611_06892_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "bidiag_create": (cint, [P(vp), cint, vp]),
+        "bidiag_set_option": (cint, [vp, cint, i64]),
+        "bidiag_band": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, P(vp)]),
+        "bidiag_band_host": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, P(vp)]),
+        "bidiag_result_band": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
+        "bidiag_result_tasks": (cint, [vp, P(P(i32)), P(i64)]),
+        "bidiag_result_reflectors": (cint, [vp, P(Reflectors)]),
+        "bidiag_apply_q": (cint, [vp, vp, cint, i64, vp, i64]),
+        "bidiag_apply_p": (cint, [vp, vp, cint, i64, vp, i64]),
+        "bidiag_sync": (cint, [vp]),
+        "bidiag_last_exec_ms": (cint, [vp, P(ctypes.c_float)]),
+        "bidiag_last_error": (ctypes.c_char_p, [vp]),
+        "bidiag_result_free": (cint, [vp]),
+        "bidiag_destroy": (cint, [vp]),
+        "bidiag_plan_eliminations": (cint, [i64, i64, cint, cint, i64, P(i32), i64, P(i64)]),
+        "bidiag_plan_tasks": (cint, [i64, i64, cint, cint, i64, P(i32), P(i32), i64, P(i64), P(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(h, rc):
+    if rc != 0:
+        msg = load_library().bidiag_last_error(h).decode() if h else ""
+        raise BidiagError(rc, msg)
+
+
+# ---- thin wrappers with the C names ------------------------------------------------------------
+def bidiag_create(device=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(None, load_library().bidiag_create(ctypes.byref(h), device, stream))
+    return h
+
+
+def bidiag_set_option(h, option, value):
+    _check(h, load_library().bidiag_set_option(h, option, value))
+
+
+def bidiag_band(h, m, n, d_A, lda, nb, ib, tree, variant):
+    r = ctypes.c_void_p()
+    _check(h, load_library().bidiag_band(h, m, n, d_A, lda, nb, ib, tree, variant, ctypes.byref(r)))
+    return r
+
+
+def bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab, keep=False):
+    r = ctypes.c_void_p()
+    _check(h, load_library().bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab,
+                                              ctypes.byref(r) if keep else None))
+    return r if keep else None
+
+
+def bidiag_sync(h):
+    _check(h, load_library().bidiag_sync(h))
+
+
+def bidiag_last_exec_ms(h):
+    ms = ctypes.c_float()
+    _check(h, load_library().bidiag_last_exec_ms(h, ctypes.byref(ms)))
+    return ms.value
+
+
+def bidiag_apply_q(h, r, trans, ncols, d_C, ldc):
+    _check(h, load_library().bidiag_apply_q(h, r, trans, ncols, d_C, ldc))
+
+
+def bidiag_apply_p(h, r, trans, nrows, d_C, ldc):
+    _check(h, load_library().bidiag_apply_p(h, r, trans, nrows, d_C, ldc))
+
+
+def bidiag_result_free(r):
+    load_library().bidiag_result_free(r)
+
+
+def bidiag_destroy(h):
+    load_library().bidiag_destroy(h)
+
+
+def bidiag_plan_eliminations(p, q, tree, variant, resources=1):
+    lib = load_library()
+    cnt = ctypes.c_int64()
+    _check(None, lib.bidiag_plan_eliminations(p, q, tree, variant, resources, None, 0, ctypes.byref(cnt)))
+    out = np.zeros((max(cnt.value, 1), 5), dtype=np.int32)
+    _check(None, lib.bidiag_plan_eliminations(p, q, tree, variant, resources,
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                              cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def bidiag_plan_tasks(p, q, tree, variant, resources=1):
+    """(tasks (ntasks x 6), levels (ntasks), critical path in Table 1 units)."""
+    lib = load_library()
+    cnt = ctypes.c_int64()
+    cp = ctypes.c_int64()
+    _check(None, lib.bidiag_plan_tasks(p, q, tree, variant, resources, None, None, 0, ctypes.byref(cnt), None))
+    tasks = np.zeros((max(cnt.value, 1), 6), dtype=np.int32)
+    lv = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    _check(None, lib.bidiag_plan_tasks(p, q, tree, variant, resources, tasks.ctypes.data_as(I32),
+                                       lv.ctypes.data_as(I32), cnt.value, ctypes.byref(cnt), ctypes.byref(cp)))
+    return tasks[:cnt.value], lv[:cnt.value], cp.value
+
+
+# ---- torch-facing wrappers ---------------------------------------------------------------------
+class _CudaArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, strides_elems):
+        self.__cuda_array_interface__ = {
+            "shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False), "version": 3,
+            "strides": tuple(8 * s for s in strides_elems)}
+
+
+def _device_view(ptr, shape, strides):
+    import torch
+    return torch.as_tensor(_CudaArray(ptr, shape, strides), device="cuda")
+
+
+def _colmajor(A):
+    """Column-major FP64 CUDA tensor (copy only if needed) and its leading dimension."""
+    import torch
+    if A.dtype != torch.float64 or not A.is_cuda:
+        raise TypeError("A must be a float64 CUDA tensor")
+    m, n = A.shape
+    if A.stride(0) == 1 and (A.stride(1) >= max(1, m) or n == 1):
+        return A, max(A.stride(1), m)
+    Ac = A.t().contiguous().t()
+    return Ac, max(m, 1)
+
+
+class Handle:
+    """Library handle on a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        dev = torch.cuda.current_device() if device is None else int(device)
+        s = torch.cuda.current_stream(dev) if stream is None else stream
+        self.stream = s
+        self.h = bidiag_create(dev, ctypes.c_void_p(s.cuda_stream))
+        self.device = dev
+
+    def set_option(self, option, value):
+        bidiag_set_option(self.h, option, value)
+
+    def band(self, A, nb, ib, tree="greedy", variant="bidiag"):
+        tree = TREES[tree] if isinstance(tree, str) else tree
+        variant = VARIANTS[variant] if isinstance(variant, str) else variant
+        Ac, lda = _colmajor(A)
+        m, n = A.shape
+        r = bidiag_band(self.h, m, n, ctypes.c_void_p(Ac.data_ptr()), lda, nb, ib, tree, variant)
+        return Result(self, r, keep=Ac)
+
+    def sync(self):
+        bidiag_sync(self.h)
+
+    def last_exec_ms(self):
+        return bidiag_last_exec_ms(self.h)
+
+    def close(self):
+        if self.h:
+            bidiag_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result:
+    """A reduction result: band B, reflector store, canonical task list."""
+
+    def __init__(self, handle, r, keep=None):
+        self.handle = handle
+        self.r = r
+        self._keep = keep
+        lib = load_library()
+        ab = ctypes.c_void_p()
+        ldab = ctypes.c_int64()
+        n = ctypes.c_int64()
+        nb = ctypes.c_int()
+        _check(handle.h, lib.bidiag_result_band(r, ctypes.byref(ab), ctypes.byref(ldab), ctypes.byref(n),
+                                                ctypes.byref(nb)))
+        self.ab_ptr, self.ldab, self.n, self.nb = ab.value, ldab.value, n.value, nb.value
+        desc = Reflectors()
+        _check(handle.h, lib.bidiag_result_reflectors(r, ctypes.byref(desc)))
+        self.desc = desc
+
+    def band(self):
+        """Copy of B in LAPACK upper-band storage, shape (nb + 1, n)."""
+        return _device_view(self.ab_ptr, (self.nb + 1, self.n), (1, self.ldab)).clone()
+
+    def tasks(self):
+        lib = load_library()
+        ptr = ctypes.POINTER(ctypes.c_int32)()
+        nt = ctypes.c_int64()
+        _check(self.handle.h, lib.bidiag_result_tasks(self.r, ctypes.byref(ptr), ctypes.byref(nt)))
+        return np.ctypeslib.as_array(ptr, shape=(nt.value, 6)).copy()
+
+    def tiles(self, second=False):
+        """Copy of the tile buffer (grid rows x grid cols x nb x nb; [a, b] is tile (a, b), column-major)."""
+        d = self.desc
+        ptr = d.tiles2 if second else d.tiles
+        if not ptr:
+            return None
+        rows = d.q if second else d.p
+        cols = d.q
+        nb = d.nb
+        t = _device_view(ptr, (cols * rows * nb * nb,), (1,)).clone()
+        return t.view(cols, rows, nb, nb).permute(1, 0, 3, 2)   # [a, b, r, c]
+
+    def T(self):
+        d = self.desc
+        return _device_view(d.T, (max(d.npanels, 1), d.ib, d.nb), (d.ib * d.nb, 1, d.ib)).clone()
+
+    def tslot(self):
+        d = self.desc
+        return np.ctypeslib.as_array(d.tslot, shape=(d.ntasks,)).copy()
+
+    def apply_q(self, C, trans):
+        Cc, ldc = _colmajor(C)
+        bidiag_apply_q(self.handle.h, self.r, trans, C.shape[1], ctypes.c_void_p(Cc.data_ptr()), ldc)
+        if Cc.data_ptr() != C.data_ptr():
+            C.copy_(Cc)
+        return C
+
+    def apply_p(self, C, trans):
+        Cc, ldc = _colmajor(C)
+        bidiag_apply_p(self.handle.h, self.r, trans, C.shape[0], ctypes.c_void_p(Cc.data_ptr()), ldc)
+        if Cc.data_ptr() != C.data_ptr():
+            C.copy_(Cc)
+        return C
+
+    def free(self):
+        if self.r:
+            bidiag_result_free(self.r)
+            self.r = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,626 @@
+// C ABI of the library (declared in include/bidiag.h): handles, results, argument checks, the plan
+// cache, buffer management and the launches of the pack / executor / extract kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bidiag.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace {
+
+struct PlanDev {
+  bd::Plan plan;
+  bd::DevTask* d_tasks = nullptr;
+  int32_t* d_deps = nullptr;
+  int* d_done = nullptr;
+  int nflags = 0;
+  std::vector<int32_t> dump;   // canonical task list, 6 int32 per task
+  ~PlanDev() {
+    if (d_tasks) cudaFree(d_tasks);
+    if (d_deps) cudaFree(d_deps);
+    if (d_done) cudaFree(d_done);
+  }
+};
+
+using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int>;
+
+}  // namespace
+
+struct bidiag_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nsm = 0;
+  size_t smem_optin = 0;
+  std::string err;
+  std::map<PlanKey, std::shared_ptr<PlanDev>> cache;
+  int* d_ctrl = nullptr;         // [0] queue head, [1..3] device error word
+  uint64_t wait_ns = 20000000000ull;
+  int64_t auto_res = -1;
+  int debug_unset = 0;
+  int strip_w = 32;
+  int timing = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool timed = false;
+};
+
+struct bidiag_result {
+  bidiag_ctx* h = nullptr;
+  std::shared_ptr<PlanDev> pd;
+  int64_t m = 0, n = 0;
+  int nb = 0, ib = 0, tree = 0, variant = 0, p = 0, q = 0;
+  double* tiles = nullptr;
+  double* tiles2 = nullptr;
+  double* T = nullptr;
+  double* ab = nullptr;
+  int64_t ldab = 0;
+};
+
+namespace {
+
+int fail(bidiag_handle h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(bidiag_handle h, cudaError_t e, const char* what) {
+  return fail(h, e == cudaErrorMemoryAllocation ? BIDIAG_ERR_NOMEM : BIDIAG_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                 \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+void dump_tasks(const std::vector<bd::Task>& tasks, std::vector<int32_t>& out) {
+  out.resize(tasks.size() * 6);
+  for (size_t x = 0; x < tasks.size(); ++x) {
+    const bd::Task& t = tasks[x];
+    int32_t* o = &out[x * 6];
+    o[0] = t.type; o[1] = t.phase; o[2] = t.k; o[3] = t.i; o[4] = t.piv; o[5] = t.j;
+  }
+}
+
+int upload_program(bidiag_handle h, PlanDev& pd, const std::vector<bd::DevTask>& dev, const std::vector<int32_t>& deps,
+                   int extra_flags) {
+  const size_t nt = dev.size();
+  pd.nflags = (int)nt + extra_flags;
+  CK(h, cudaMalloc(&pd.d_tasks, std::max<size_t>(1, nt) * sizeof(bd::DevTask)));
+  CK(h, cudaMalloc(&pd.d_deps, std::max<size_t>(1, deps.size()) * sizeof(int32_t)));
+  CK(h, cudaMalloc(&pd.d_done, std::max<size_t>(1, pd.nflags) * sizeof(int)));
+  if (nt) CK(h, cudaMemcpy(pd.d_tasks, dev.data(), nt * sizeof(bd::DevTask), cudaMemcpyHostToDevice));
+  if (!deps.empty()) CK(h, cudaMemcpy(pd.d_deps, deps.data(), deps.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return BIDIAG_OK;
+}
+
+int64_t resources_of(bidiag_handle h) { return h->auto_res > 0 ? h->auto_res : h->nsm; }
+
+// Executor launch of a program held in pd with the given buffers.
+int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t n0, double* b1, int64_t n1, double* b2,
+             int64_t n2, double* T, int npanels, int nb, int ib, int w, bool timed = false) {
+  if (ntasks == 0) return BIDIAG_OK;
+  const size_t smem = bd::exec_smem_bytes(nb, ib, w);
+  CK(h, bd::exec_set_smem(smem));
+  const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem));
+  bd::ExecParams prm{};
+  prm.tasks = pd.d_tasks;
+  prm.deps = pd.d_deps;
+  prm.ntasks = ntasks;
+  prm.nflags = pd.nflags;
+  prm.done = pd.d_done;
+  prm.head = h->d_ctrl;
+  prm.err = h->d_ctrl + 1;
+  prm.buf[0] = b0; prm.ntiles[0] = n0;
+  prm.buf[1] = b1; prm.ntiles[1] = n1;
+  prm.buf[2] = b2; prm.ntiles[2] = n2;
+  prm.T = T;
+  prm.npanels = npanels;
+  prm.nb = nb;
+  prm.ib = ib;
+  prm.w = w;
+  prm.wait_ns = h->wait_ns;
+  CK(h, cudaMemsetAsync(pd.d_done, 0, sizeof(int) * (size_t)pd.nflags, h->stream));
+  CK(h, cudaMemsetAsync(h->d_ctrl, 0, sizeof(int), h->stream));
+  const int grid = std::min<int64_t>((int64_t)h->nsm * per_sm, ntasks);
+  if (timed) CK(h, cudaEventRecord(h->ev[0], h->stream));
+  CK(h, bd::launch_exec(prm, grid, smem, h->stream));
+  if (timed) CK(h, cudaEventRecord(h->ev[1], h->stream));
+  return BIDIAG_OK;
+}
+
+int choose_strip(bidiag_handle h, int nb, int ib, int* w) {
+  int cand[2] = {h->strip_w, 16};
+  for (int c : cand) {
+    const int ww = std::min(c, nb);
+    if (bd::exec_smem_bytes(nb, ib, ww) <= h->smem_optin) {
+      *w = ww;
+      return BIDIAG_OK;
+    }
+  }
+  return fail(h, BIDIAG_ERR_UNSUPPORTED, "tile size / inner blocking need more shared memory than the device has");
+}
+
+int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int w,
+             std::shared_ptr<PlanDev>* out) {
+  const int64_t R = resources_of(h);
+  const bool debug = h->debug_unset != 0;
+  PlanKey key{m, n, nb, ib, tree, variant, R, w};
+  if (!debug) {
+    auto it = h->cache.find(key);
+    if (it != h->cache.end()) {
+      *out = it->second;
+      return BIDIAG_OK;
+    }
+  }
+  auto pd = std::make_shared<PlanDev>();
+  try {
+    bd::build_plan(pd->plan, m, n, nb, ib, tree, variant, R, w);
+  } catch (const std::bad_alloc&) {
+    return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning");
+  } catch (const std::exception& e) {
+    return fail(h, BIDIAG_ERR_UNSUPPORTED, std::string("planner: ") + e.what());
+  }
+  dump_tasks(pd->plan.tasks, pd->dump);
+  std::vector<int32_t> deps = pd->plan.deps;
+  std::vector<bd::DevTask> dev = pd->plan.dev;
+  int extra = 1;
+  if (debug && !dev.empty()) {
+    // failure-path test: the first queued task also waits for a flag that nothing sets
+    const int32_t never = (int32_t)dev.size();
+    std::vector<int32_t> nd;
+    nd.push_back(never);
+    for (size_t y = 0; y < dev.size(); ++y) {
+      const int32_t b = (int32_t)nd.size();
+      if (y == 0) {
+        for (int32_t d = dev[y].dep_begin; d < dev[y].dep_end; ++d) nd.push_back(deps[d]);
+        dev[y].dep_begin = 0;
+        dev[y].dep_end = (int32_t)nd.size();
+        continue;
+      }
+      for (int32_t d = dev[y].dep_begin; d < dev[y].dep_end; ++d) nd.push_back(deps[d]);
+      dev[y].dep_begin = b;
+      dev[y].dep_end = (int32_t)nd.size();
+    }
+    deps.swap(nd);
+    h->debug_unset = 0;
+  }
+  int rc = upload_program(h, *pd, dev, deps, extra);
+  if (rc) return rc;
+  if (!debug) h->cache[key] = pd;
+  *out = pd;
+  return BIDIAG_OK;
+}
+
+template <typename T>
+int dev_alloc(bidiag_handle h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return BIDIAG_OK;
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMallocAsync");
+  return BIDIAG_OK;
+}
+
+void free_result_buffers(bidiag_result* r) {
+  cudaStream_t s = r->h ? r->h->stream : nullptr;
+  if (r->tiles) cudaFreeAsync(r->tiles, s);
+  if (r->tiles2) cudaFreeAsync(r->tiles2, s);
+  if (r->T) cudaFreeAsync(r->T, s);
+  if (r->ab) cudaFreeAsync(r->ab, s);
+  r->tiles = r->tiles2 = r->T = r->ab = nullptr;
+}
+
+// Replays the panel tasks of one side (QR side: left = true; LQ side: left = false) on a tiled copy of C.
+int apply_side(bidiag_handle h, bidiag_result_t r, bool left, int trans, int64_t other, double* C, int64_t ldc) {
+  const bd::Plan& pl = r->pd->plan;
+  const int nb = r->nb, ib = r->ib;
+  const int64_t crow = left ? r->m : other, ccol = left ? other : r->n;
+  if (crow == 0 || ccol == 0) return BIDIAG_OK;
+  const int64_t rows_t = (crow + nb - 1) / nb, cols_t = (ccol + nb - 1) / nb;
+  const int64_t nblk = left ? cols_t : rows_t;   // independent tile columns of the oriented C
+  int w = 0;
+  int rc = choose_strip(h, nb, ib, &w);
+  if (rc) return rc;
+  const int S = (nb + w - 1) / w;
+  // panel tasks of this side, in application order
+  std::vector<int32_t> panels;
+  for (size_t x = 0; x < pl.tasks.size(); ++x) {
+    const bd::Task& t = pl.tasks[x];
+    if (!(t.type == bd::GEQRT || t.type == bd::TSQRT || t.type == bd::TTQRT)) continue;
+    if ((t.phase == bd::PH_LQ) == left) continue;
+    panels.push_back((int32_t)x);
+  }
+  // left: Q^T C forward (trans = 1) / Q C backward.  right: C P forward with Q^T-mode on C^T (trans = 0),
+  // C P^T backward with Q-mode.
+  const bool forward = left ? (trans == 1) : (trans == 0);
+  const bool notrans = !forward;
+  if (!forward) std::reverse(panels.begin(), panels.end());
+  std::vector<bd::DevTask> dev;
+  std::vector<int32_t> deps;
+  std::vector<int32_t> last((size_t)rows_t * cols_t * S, -1);   // last writer per (C tile, strip)
+  auto cref = [&](int64_t orow, int64_t ocol) {                  // oriented C tile -> buffer-2 reference
+    const int64_t a = left ? orow : ocol, b = left ? ocol : orow;
+    return std::make_pair(bd::tile_ref(2, b * rows_t + a), b * rows_t + a);
+  };
+  for (int32_t x : panels) {
+    const bd::Task& t = pl.tasks[x];
+    const int buf = (r->variant == BIDIAG_RBIDIAG && t.phase != bd::PH_PQR) ? 1 : 0;
+    const int grid_rows = buf == 0 ? r->p : r->q;
+    const bool lq = t.phase == bd::PH_LQ;
+    const int ax = lq ? t.k : t.i, ay = lq ? t.i : t.k;     // actual tile of oriented (i, k)
+    const int32_t vref = bd::tile_ref(buf, (int64_t)ay * grid_rows + ax);
+    const int utype = t.type == bd::GEQRT ? bd::UNMQR : (t.type == bd::TSQRT ? bd::TSMQR : bd::TTMQR);
+    for (int64_t b = 0; b < nblk; ++b) {
+      auto ci = cref(t.i, b);
+      std::pair<int32_t, int64_t> cp{-1, -1};
+      if (utype != bd::UNMQR) cp = cref(t.piv, b);
+      for (int s = 0; s < S; ++s) {
+        bd::DevTask d{};
+        d.op = utype | ((lq ? 1 : 0) << 4) | ((notrans ? 1 : 0) << 5) | (s << 8);
+        d.x = vref;
+        d.a = cp.first;
+        d.c = ci.first;
+        d.tslot = pl.tslot[x];
+        d.flags = 0;
+        d.dep_begin = (int32_t)deps.size();
+        const int32_t me = (int32_t)dev.size();
+        int32_t& lc = last[(size_t)ci.second * S + s];
+        if (lc >= 0) deps.push_back(lc);
+        if (cp.second >= 0) {
+          int32_t& lp = last[(size_t)cp.second * S + s];
+          if (lp >= 0 && lp != lc) deps.push_back(lp);
+          lp = me;
+        }
+        lc = me;
+        d.dep_end = (int32_t)deps.size();
+        dev.push_back(d);
+      }
+    }
+  }
+  if (dev.empty()) return BIDIAG_OK;
+  PlanDev prog;
+  rc = upload_program(h, prog, dev, deps, 1);
+  if (rc) return rc;
+  double* Ct = nullptr;
+  rc = dev_alloc(h, &Ct, (size_t)rows_t * cols_t * nb * nb);
+  if (rc) return rc;
+  CK(h, bd::launch_pack(C, ldc, crow, ccol, nb, Ct, rows_t, cols_t, h->stream));
+  rc = run_exec(h, prog, (int)dev.size(), r->tiles, (int64_t)r->p * r->q, r->tiles2,
+                r->tiles2 ? (int64_t)r->q * r->q : 0, Ct, rows_t * cols_t, r->T, pl.npanels, nb, ib, w);
+  if (rc) return rc;
+  CK(h, bd::launch_unpack(Ct, rows_t, nb, crow, ccol, C, ldc, h->stream));
+  CK(h, cudaFreeAsync(Ct, h->stream));
+  // the program buffers are freed by ~PlanDev; wait for the stream so that they outlive the launch
+  CK(h, cudaStreamSynchronize(h->stream));
+  return BIDIAG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bidiag_create(bidiag_handle* h, int device, void* cuda_stream) {
+  if (!h) return -1;
+  *h = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return -2;
+  bidiag_ctx* c = new (std::nothrow) bidiag_ctx();
+  if (!c) return BIDIAG_ERR_NOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_ctrl, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_ctrl, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    return e == cudaErrorMemoryAllocation ? BIDIAG_ERR_NOMEM : BIDIAG_ERR_CUDA;
+  }
+  c->smem_optin = (size_t)optin - 64;   // headroom for the executor's static shared memory
+  if (const char* s = std::getenv("BIDIAG_WAIT_LIMIT_NS")) c->wait_ns = std::strtoull(s, nullptr, 10);
+  if (const char* s = std::getenv("BIDIAG_AUTO_RES")) c->auto_res = std::atoll(s);
+  *h = c;
+  return BIDIAG_OK;
+}
+
+int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
+  if (!h) return -1;
+  switch (option) {
+    case BIDIAG_OPT_WAIT_LIMIT_NS:
+      if (value <= 0) return -3;
+      h->wait_ns = (uint64_t)value;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_AUTO_RESOURCES:
+      if (value < 0) return -3;
+      h->auto_res = value;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_DEBUG_UNSET_DEP:
+      h->debug_unset = value != 0;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_STRIP:
+      if (value != 16 && value != 32) return -3;
+      h->strip_w = (int)value;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_TIMING:
+      h->timing = value != 0;
+      return BIDIAG_OK;
+    default:
+      return -2;
+  }
+}
+
+int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_t lda, int nb, int ib, int tree,
+                int variant, bidiag_result_t* out) {
+  if (!h) return -1;
+  if (m < 1) return fail(h, -2, "m < 1");
+  if (n < 1) return fail(h, -3, "n < 1");
+  if (!d_A) return fail(h, -4, "A is NULL");
+  if (lda < m) return fail(h, -5, "lda < m");
+  if (nb < 1 || nb > bd::kMaxNb) return fail(h, -6, "nb out of range");
+  if (ib < 1 || ib > std::min(nb, 64) || nb % ib) return fail(h, -7, "ib out of range or does not divide nb");
+  if (tree < 0 || tree > 3) return fail(h, -8, "unknown tree");
+  if (variant < 0 || variant > 1) return fail(h, -9, "unknown variant");
+  if (!out) return fail(h, -10, "out is NULL");
+  *out = nullptr;
+  if (m < n) return fail(h, BIDIAG_ERR_UNSUPPORTED, "m < n: reduce the transpose");
+  CK(h, cudaSetDevice(h->device));
+  int w = 0;
+  int rc = choose_strip(h, nb, ib, &w);
+  if (rc) return rc;
+  std::shared_ptr<PlanDev> pd;
+  rc = get_plan(h, m, n, nb, ib, tree, variant, w, &pd);
+  if (rc) return rc;
+  bidiag_result* r = new (std::nothrow) bidiag_result();
+  if (!r) return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed");
+  r->h = h;
+  r->pd = pd;
+  r->m = m;
+  r->n = n;
+  r->nb = nb;
+  r->ib = ib;
+  r->tree = tree;
+  r->variant = variant;
+  r->p = pd->plan.p;
+  r->q = pd->plan.q;
+  r->ldab = nb + 1;
+  const size_t tile_elems = (size_t)nb * nb;
+  if ((rc = dev_alloc(h, &r->tiles, (size_t)r->p * r->q * tile_elems)) ||
+      (variant == BIDIAG_RBIDIAG && (rc = dev_alloc(h, &r->tiles2, (size_t)r->q * r->q * tile_elems))) ||
+      (rc = dev_alloc(h, &r->T, (size_t)std::max(1, pd->plan.npanels) * ib * nb)) ||
+      (rc = dev_alloc(h, &r->ab, (size_t)(nb + 1) * n))) {
+    free_result_buffers(r);
+    delete r;
+    return rc;
+  }
+  auto bail = [&](int code) {
+    free_result_buffers(r);
+    delete r;
+    return code;
+  };
+  cudaError_t e = bd::launch_pack(d_A, lda, m, n, nb, r->tiles, r->p, r->q, h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "pack"));
+  if (r->tiles2) {
+    e = cudaMemsetAsync(r->tiles2, 0, (size_t)r->q * r->q * tile_elems * sizeof(double), h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+  }
+  const bool timed = h->timing != 0;
+  if (timed && !h->ev[0]) {
+    e = cudaEventCreate(&h->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
+  }
+  rc = run_exec(h, *pd, (int)pd->plan.dev.size(), r->tiles, (int64_t)r->p * r->q, r->tiles2,
+                r->tiles2 ? (int64_t)r->q * r->q : 0, nullptr, 0, r->T, pd->plan.npanels, nb, ib, w, timed);
+  h->timed = timed;
+  if (rc) return bail(rc);
+  e = bd::launch_extract(r->tiles2 ? r->tiles2 : r->tiles, r->tiles2 ? r->q : r->p, nb, n, r->ab, r->ldab, h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "extract"));
+  *out = r;
+  return BIDIAG_OK;
+}
+
+int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, int64_t lda, int nb, int ib, int tree,
+                     int variant, double* h_ab, int64_t ldab, bidiag_result_t* out) {
+  if (!h) return -1;
+  if (out) *out = nullptr;
+  if (!h_A) return fail(h, -4, "A is NULL");
+  if (lda < m) return fail(h, -5, "lda < m");
+  if (!h_ab) return fail(h, -11, "ab is NULL");
+  if (ldab < nb + 1) return fail(h, -12, "ldab < nb + 1");
+  if (m < 1) return fail(h, -2, "m < 1");
+  if (n < 1) return fail(h, -3, "n < 1");
+  CK(h, cudaSetDevice(h->device));
+  double* dA = nullptr;
+  int rc = dev_alloc(h, &dA, (size_t)lda * n);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(dA, h_A, sizeof(double) * (size_t)lda * n, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dA, h->stream);
+    return cuda_fail(h, e, "copy A to device");
+  }
+  bidiag_result_t r = nullptr;
+  rc = bidiag_band(h, m, n, dA, lda, nb, ib, tree, variant, &r);
+  cudaFreeAsync(dA, h->stream);
+  if (rc) return rc;
+  e = cudaMemcpy2DAsync(h_ab, sizeof(double) * ldab, r->ab, sizeof(double) * r->ldab, sizeof(double) * (nb + 1), n,
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) {
+    bidiag_result_free(r);
+    return cuda_fail(h, e, "copy band to host");
+  }
+  rc = bidiag_sync(h);
+  if (rc || !out) {
+    bidiag_result_free(r);
+    return rc;
+  }
+  *out = r;
+  return BIDIAG_OK;
+}
+
+int bidiag_result_band(bidiag_result_t r, const double** ab, int64_t* ldab, int64_t* n, int* nb) {
+  if (!r) return -1;
+  if (ab) *ab = r->ab;
+  if (ldab) *ldab = r->ldab;
+  if (n) *n = r->n;
+  if (nb) *nb = r->nb;
+  return BIDIAG_OK;
+}
+
+int bidiag_result_tasks(bidiag_result_t r, const int32_t** tasks, int64_t* ntasks) {
+  if (!r) return -1;
+  if (tasks) *tasks = r->pd->dump.data();
+  if (ntasks) *ntasks = (int64_t)r->pd->plan.tasks.size();
+  return BIDIAG_OK;
+}
+
+int bidiag_result_reflectors(bidiag_result_t r, bidiag_reflectors* desc) {
+  if (!r) return -1;
+  if (!desc) return -2;
+  desc->tiles = r->tiles;
+  desc->tiles2 = r->tiles2;
+  desc->T = r->T;
+  desc->tslot = r->pd->plan.tslot.data();
+  desc->ntasks = (int64_t)r->pd->plan.tasks.size();
+  desc->m = r->m;
+  desc->n = r->n;
+  desc->nb = r->nb;
+  desc->ib = r->ib;
+  desc->p = r->p;
+  desc->q = r->q;
+  desc->npanels = r->pd->plan.npanels;
+  desc->variant = r->variant;
+  return BIDIAG_OK;
+}
+
+int bidiag_apply_q(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols, double* d_C, int64_t ldc) {
+  if (!h) return -1;
+  if (!r) return fail(h, -2, "result is NULL");
+  if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
+  if (ncols < 0) return fail(h, -4, "ncols < 0");
+  if (!d_C && ncols > 0) return fail(h, -5, "C is NULL");
+  if (ldc < r->m) return fail(h, -6, "ldc < m");
+  CK(h, cudaSetDevice(h->device));
+  return apply_side(h, r, true, trans, ncols, d_C, ldc);
+}
+
+int bidiag_apply_p(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, double* d_C, int64_t ldc) {
+  if (!h) return -1;
+  if (!r) return fail(h, -2, "result is NULL");
+  if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
+  if (nrows < 0) return fail(h, -4, "nrows < 0");
+  if (!d_C && nrows > 0) return fail(h, -5, "C is NULL");
+  if (ldc < std::max<int64_t>(1, nrows)) return fail(h, -6, "ldc < nrows");
+  CK(h, cudaSetDevice(h->device));
+  return apply_side(h, r, false, trans, nrows, d_C, ldc);
+}
+
+int bidiag_sync(bidiag_handle h) {
+  if (!h) return -1;
+  CK(h, cudaSetDevice(h->device));
+  CK(h, cudaStreamSynchronize(h->stream));
+  int err[3] = {0, 0, 0};
+  CK(h, cudaMemcpy(err, h->d_ctrl + 1, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err[0] != bd::DERR_OK) {
+    CK(h, cudaMemset(h->d_ctrl + 1, 0, sizeof(err)));
+    if (err[0] == bd::DERR_TIMEOUT)
+      return fail(h, BIDIAG_ERR_TIMEOUT, "device dependency wait ran out at queue position " +
+                                             std::to_string(err[1]) + " waiting for " + std::to_string(err[2]));
+    return fail(h, BIDIAG_ERR_CUDA, "executor rejected an invalid task at queue position " + std::to_string(err[1]));
+  }
+  h->err.clear();
+  return BIDIAG_OK;
+}
+
+int bidiag_last_exec_ms(bidiag_handle h, float* ms) {
+  if (!h) return -1;
+  if (!ms) return -2;
+  if (!h->timed || !h->ev[0]) return fail(h, BIDIAG_ERR_UNSUPPORTED, "timing was off for the last reduction");
+  CK(h, cudaEventElapsedTime(ms, h->ev[0], h->ev[1]));
+  return BIDIAG_OK;
+}
+
+const char* bidiag_last_error(bidiag_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+int bidiag_result_free(bidiag_result_t r) {
+  if (!r) return -1;
+  if (r->h) cudaSetDevice(r->h->device);
+  free_result_buffers(r);
+  delete r;
+  return BIDIAG_OK;
+}
+
+int bidiag_destroy(bidiag_handle h) {
+  if (!h) return -1;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  h->cache.clear();
+  if (h->d_ctrl) cudaFree(h->d_ctrl);
+  if (h->ev[0]) cudaEventDestroy(h->ev[0]);
+  if (h->ev[1]) cudaEventDestroy(h->ev[1]);
+  delete h;
+  return BIDIAG_OK;
+}
+
+int bidiag_plan_eliminations(int64_t p, int64_t q, int tree, int variant, int64_t resources, int32_t* out, int64_t cap,
+                             int64_t* count) {
+  if (p < 1 || q < 1 || q > p) return -1;
+  if (tree < 0 || tree > 3) return -3;
+  if (variant < 0 || variant > 1) return -4;
+  if (!count) return -8;
+  try {
+    auto el = bd::make_eliminations((int)p, (int)q, tree, variant, resources);
+    *count = (int64_t)el.size();
+    if (out && cap >= (int64_t)el.size()) {
+      for (size_t x = 0; x < el.size(); ++x) {
+        out[5 * x + 0] = el[x].phase; out[5 * x + 1] = el[x].k; out[5 * x + 2] = el[x].i;
+        out[5 * x + 3] = el[x].piv; out[5 * x + 4] = el[x].kind;
+      }
+    }
+  } catch (...) {
+    return BIDIAG_ERR_NOMEM;
+  }
+  return BIDIAG_OK;
+}
+
+int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resources, int32_t* tasks, int32_t* level,
+                      int64_t cap, int64_t* count, int64_t* cp) {
+  if (p < 1 || q < 1 || q > p) return -1;
+  if (tree < 0 || tree > 3) return -3;
+  if (variant < 0 || variant > 1) return -4;
+  if (!count) return -9;
+  try {
+    auto ts = bd::make_tasks((int)p, (int)q, tree, variant, resources);
+    *count = (int64_t)ts.size();
+    const bool fits = cap >= (int64_t)ts.size();
+    if (level || cp) {
+      std::vector<int32_t> lv;
+      int64_t c = 0;
+      bd::make_dag(ts, (int)p, (int)q, variant, nullptr, &lv, &c);
+      if (cp) *cp = c;
+      if (level && fits) std::copy(lv.begin(), lv.end(), level);
+    }
+    if (tasks && fits) {
+      std::vector<int32_t> d;
+      dump_tasks(ts, d);
+      std::copy(d.begin(), d.end(), tasks);
+    }
+  } catch (...) {
+    return BIDIAG_ERR_NOMEM;
+  }
+  return BIDIAG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,573 @@
+// FP64 tile kernels of the tiled QR / LQ steps and the persistent dataflow executor (sm_103a).
+//
+// Kernels (Table 1, Sec. 3.2 of Faverge, Langou, Robert, Dongarra, arXiv 1611.06892):
+//   GEQRT  QR of one tile                      UNMQR  apply its Q^T to a tile of the same row
+//   TSQRT  triangle on top of square           TSMQR  apply to the pair of tile rows
+//   TTQRT  triangle on top of triangle         TTMQR  apply to the pair of tile rows
+// An LQ step (Algorithm 4) runs the same kernels on transposed tiles: every tile access goes through
+// an orientation flag `tr`, so GELQT/UNMLQ/... are GEQRT/UNMQR/... on the transposed geometry.
+//
+// GB300's FP64 units deliver 2 FMA/clock/SM (about 1.2 TFLOP/s per GPU, measured): FP64 DMMA is not
+// faster than DFMA on this part, so the contractions are register/shared-memory DFMA loops.  Each task
+// stages its operands in shared memory (tile columns padded to an odd leading dimension against bank
+// conflicts), reads and writes global memory through L2 only (ld/st.cg: tiles written by other SMs are
+// never served stale from L1), and applies reflectors in compact-WY blocks of ib (Sec. 6.2's inner
+// blocking): W = op(T) (C_top + V^T C), C_top -= W, C -= V W.
+//
+// Householder convention (LAPACK style): for x = [alpha; tail], sigma2 = tail . tail; sigma2 == 0 gives
+// H = I (tau = 0, beta = alpha); otherwise beta = -sgn(alpha) sqrt(alpha^2 + sigma2) with sgn(alpha) = -1
+// only for alpha < 0, tau = (beta - alpha) / beta, v = [1; tail / (alpha - beta)].
+#include <cstdio>
+
+#include "kernels.cuh"
+
+namespace bd {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ double ldg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ void stg(double* p, double v) { __stcg(p, v); }
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__host__ __device__ inline int odd_ld(int rows) { return rows | 1; }
+
+// Shared-memory layout (offsets in doubles), identical on host and device.
+struct Layout {
+  int lp;                    // leading dimension of tile-column buffers
+  int P, Cs, Cp, Rt, Tb, G, W, W2, tau, red, total;
+};
+__host__ __device__ inline Layout layout_panel(int nb, int ib) {
+  Layout L{};
+  L.lp = odd_ld(nb);
+  int o = 0;
+  L.P = o;  o += L.lp * ib;
+  L.Cs = o; o += L.lp * kChunk;
+  L.Rt = o; o += ib * (ib > kChunk ? ib : kChunk);
+  L.Tb = o; o += ib * ib;
+  L.G = o;  o += ib * ib;
+  L.W = o;  o += ib * kChunk;
+  L.W2 = o; o += ib * kChunk;
+  L.tau = o; o += ib;
+  L.red = o; o += 32;
+  L.Cp = -1;
+  L.total = o;
+  return L;
+}
+__host__ __device__ inline Layout layout_update(int nb, int ib, int w) {
+  Layout L{};
+  L.lp = odd_ld(nb);
+  int o = 0;
+  L.Cp = o; o += L.lp * w;
+  L.Cs = o; o += L.lp * w;
+  L.P = o;  o += L.lp * ib;   // V block
+  L.Tb = o; o += ib * ib;
+  L.W = o;  o += ib * w;
+  L.W2 = o; o += ib * w;
+  L.Rt = L.G = L.tau = L.red = -1;
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ int toff(int r, int c, int nb, int tr) { return tr ? r * nb + c : r + c * nb; }
+
+enum Mask : int { M_NONE = 0, M_UPPER = 1, M_UNITLOWER = 2 };
+
+// s[r + c*lds] = oriented X(r0 + r, c0 + c); M_UPPER zeroes entries below the diagonal, M_UNITLOWER
+// gives the unit lower trapezoid (1 on, 0 above the diagonal).  Coalesced in both orientations.
+__device__ void load_block(double* s, int lds, const double* g, int nb, int tr, int r0, int c0, int rows, int cols,
+                           int mask) {
+  const int n = rows * cols;
+  for (int o = threadIdx.x; o < n; o += kThreads) {
+    int r, c;
+    if (!tr) { r = o % rows; c = o / rows; } else { c = o % cols; r = o / cols; }
+    const int R = r0 + r, C = c0 + c;
+    double v;
+    if (mask == M_UPPER && R > C) v = 0.0;
+    else if (mask == M_UNITLOWER && R <= C) v = (R == C) ? 1.0 : 0.0;
+    else v = ldg(g + toff(R, C, nb, tr));
+    s[r + c * lds] = v;
+  }
+}
+// Writes s back to oriented X(r0 + r, c0 + c); M_UPPER writes only entries on or above the diagonal.
+__device__ void store_block(const double* s, int lds, double* g, int nb, int tr, int r0, int c0, int rows, int cols,
+                            int mask) {
+  const int n = rows * cols;
+  for (int o = threadIdx.x; o < n; o += kThreads) {
+    int r, c;
+    if (!tr) { r = o % rows; c = o / rows; } else { c = o % cols; r = o / cols; }
+    const int R = r0 + r, C = c0 + c;
+    if (mask == M_UPPER && R > C) continue;
+    stg(g + toff(R, C, nb, tr), s[r + c * lds]);
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Sum over the CTA, the same value (same order) in every thread.
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) s += red[w];
+  return s;
+}
+
+enum PanelMode : int { PM_GE = 0, PM_TS = 1, PM_TT = 2 };
+
+// Unblocked factorization of kb panel columns held in P (ld lp).
+//  GE: reflector jj has alpha = P[jj, jj] and tail P[jj+1 .. rows-1, jj].
+//  TS: alpha = Rt[jj, jj] (top triangle), tail P[0 .. rows-1, jj].
+//  TT: as TS with tail P[0 .. min(rows, voff + jj + 1) - 1, jj] (the eliminated tile is a triangle).
+__device__ void factor_panel(int mode, double* P, int lp, int rows, int kb, double* Rt, int lrt, int voff,
+                             double* tau_s, double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int jj = 0; jj < kb; ++jj) {
+    int t0, t1;
+    double* alpha_p;
+    if (mode == PM_GE) {
+      t0 = jj + 1; t1 = rows; alpha_p = &P[jj + jj * lp];
+    } else {
+      t0 = 0; t1 = (mode == PM_TT) ? min(rows, voff + jj + 1) : rows; alpha_p = &Rt[jj + jj * lrt];
+    }
+    double part = 0.0;
+    for (int r = t0 + threadIdx.x; r < t1; r += kThreads) {
+      const double x = P[r + jj * lp];
+      part += x * x;
+    }
+    const double sigma2 = block_sum(part, red);
+    const double alpha = *alpha_p;
+    double beta, tau, denom;
+    if (sigma2 == 0.0) {
+      beta = alpha; tau = 0.0; denom = 1.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sigma2);
+      beta = alpha < 0.0 ? nrm : -nrm;
+      tau = (beta - alpha) / beta;
+      denom = alpha - beta;
+    }
+    for (int r = t0 + threadIdx.x; r < t1; r += kThreads)
+      P[r + jj * lp] = (tau != 0.0) ? P[r + jj * lp] / denom : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *alpha_p = beta;
+      tau_s[jj] = tau;
+    }
+    if (tau != 0.0) {
+      for (int c = jj + 1 + warp; c < kb; c += kWarps) {
+        double s = 0.0;
+        for (int r = t0 + lane; r < t1; r += 32) s += P[r + jj * lp] * P[r + c * lp];
+        s = warp_sum(s);
+        double* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
+        const double wv = *top + s;
+        __syncwarp();
+        if (lane == 0) *top = *top - tau * wv;
+        const double tw = tau * wv;
+        for (int r = t0 + lane; r < t1; r += 32) P[r + c * lp] -= P[r + jj * lp] * tw;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// T factor (kb x kb, upper) of the kb reflectors in P: T[l,l] = tau_l,
+// T[0:l, l] = -tau_l T[0:l, 0:l] (V[:, 0:l]^T v_l).  G is kb x kb scratch.
+__device__ void build_t(int mode, const double* P, int lp, int rows, int kb, int voff, const double* tau_s, double* Tb,
+                        int ldt, double* G) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int pr = warp; pr < kb * kb; pr += kWarps) {
+    const int a = pr % kb, l = pr / kb;
+    if (a >= l) continue;
+    double s = 0.0;
+    if (mode == PM_GE) {
+      for (int r = l + 1 + lane; r < rows; r += 32) s += P[r + a * lp] * P[r + l * lp];
+      s = warp_sum(s) + P[l + a * lp];
+    } else {
+      const int r1 = (mode == PM_TT) ? min(rows, voff + a + 1) : rows;
+      for (int r = lane; r < r1; r += 32) s += P[r + a * lp] * P[r + l * lp];
+      s = warp_sum(s);
+    }
+    if (lane == 0) G[a + l * kb] = s;
+  }
+  __syncthreads();
+  for (int l = 0; l < kb; ++l) {
+    for (int a = threadIdx.x; a < kb; a += kThreads) {
+      double v = 0.0;
+      if (a == l) {
+        v = tau_s[l];
+      } else if (a < l) {
+        double s = 0.0;
+        for (int t = a; t < l; ++t) s += Tb[a + t * ldt] * G[t + l * kb];
+        v = -tau_s[l] * s;
+      }
+      Tb[a + l * ldt] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// W = op(T) (Ctop + V^T C); Ctop -= W; C -= V W.  V: vrows x kb, C: vrows x ncols, Ctop: kb x ncols or
+// null.  op(T) = T^T applies Q^T (reflectors in increasing order), op(T) = T applies Q.
+__device__ void apply_block(const double* V, int lv, int vrows, int kb, const double* Tb, int ldt, bool notrans,
+                            double* Ctop, int lct, double* C, int lc, int ncols, double* W, double* W2) {
+  for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
+    const int a = o % kb, c = o / kb;
+    double s = Ctop ? Ctop[a + c * lct] : 0.0;
+    const double* v = V + a * lv;
+    const double* cc = C + c * lc;
+    for (int r = 0; r < vrows; ++r) s += v[r] * cc[r];
+    W[o] = s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
+    const int a = o % kb, c = o / kb;
+    double s = 0.0;
+    if (!notrans) {
+      for (int t = 0; t <= a; ++t) s += Tb[t + a * ldt] * W[t + c * kb];
+    } else {
+      for (int t = a; t < kb; ++t) s += Tb[a + t * ldt] * W[t + c * kb];
+    }
+    W2[o] = s;
+  }
+  __syncthreads();
+  if (Ctop) {
+    for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
+      const int a = o % kb, c = o / kb;
+      Ctop[a + c * lct] -= W2[o];
+    }
+  }
+  for (int o = threadIdx.x; o < vrows * ncols; o += kThreads) {
+    const int r = o % vrows, c = o / vrows;
+    double s = 0.0;
+    for (int a = 0; a < kb; ++a) s += V[r + a * lv] * W2[a + c * kb];
+    C[r + c * lc] -= s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Panel tasks
+// ---------------------------------------------------------------------------------------------
+__device__ void task_geqrt(double* sm, double* X, int tr, double* Tg, int nb, int ib) {
+  const Layout L = layout_panel(nb, ib);
+  double *P = sm + L.P, *Cs = sm + L.Cs, *Tb = sm + L.Tb, *G = sm + L.G, *W = sm + L.W, *W2 = sm + L.W2;
+  double *tau = sm + L.tau, *red = sm + L.red;
+  const int lp = L.lp;
+  for (int c0 = 0; c0 < nb; c0 += ib) {
+    const int kb = ib, rows = nb - c0;
+    load_block(P, lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
+    __syncthreads();
+    factor_panel(PM_GE, P, lp, rows, kb, nullptr, 0, 0, tau, red);
+    build_t(PM_GE, P, lp, rows, kb, 0, tau, Tb, kb, G);
+    store_block(P, lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
+    for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
+    __syncthreads();
+    for (int o = threadIdx.x; o < rows * kb; o += kThreads) {   // materialize the unit lower trapezoid
+      const int r = o % rows, a = o / rows;
+      if (r <= a) P[r + a * lp] = (r == a) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int cc = c0 + kb; cc < nb; cc += kChunk) {
+      const int ncols = min(kChunk, nb - cc);
+      load_block(Cs, lp, X, nb, tr, c0, cc, rows, ncols, M_NONE);
+      __syncthreads();
+      apply_block(P, lp, rows, kb, Tb, kb, false, nullptr, 0, Cs, lp, ncols, W, W2);
+      store_block(Cs, lp, X, nb, tr, c0, cc, rows, ncols, M_NONE);
+      __syncthreads();
+    }
+  }
+}
+
+// TSQRT (tt = false) / TTQRT (tt = true): eliminate tile X under the triangle of pivot tile A.
+__device__ void task_tsqrt(double* sm, double* X, double* A, int tr, double* Tg, int nb, int ib, bool tt) {
+  const Layout L = layout_panel(nb, ib);
+  double *P = sm + L.P, *Cs = sm + L.Cs, *Rt = sm + L.Rt, *Tb = sm + L.Tb, *G = sm + L.G, *W = sm + L.W;
+  double *W2 = sm + L.W2, *tau = sm + L.tau, *red = sm + L.red;
+  const int lp = L.lp;
+  const int mode = tt ? PM_TT : PM_TS;
+  for (int c0 = 0; c0 < nb; c0 += ib) {
+    const int kb = ib;
+    const int vrows = tt ? c0 + kb : nb;
+    load_block(Rt, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
+    load_block(P, lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+    __syncthreads();
+    factor_panel(mode, P, lp, vrows, kb, Rt, kb, c0, tau, red);
+    build_t(mode, P, lp, vrows, kb, c0, tau, Tb, kb, G);
+    store_block(Rt, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
+    store_block(P, lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+    for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
+    __syncthreads();
+    for (int cc = c0 + kb; cc < nb; cc += kChunk) {
+      const int ncols = min(kChunk, nb - cc);
+      load_block(Rt, kb, A, nb, tr, c0, cc, kb, ncols, M_NONE);
+      load_block(Cs, lp, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
+      __syncthreads();
+      apply_block(P, lp, vrows, kb, Tb, kb, false, Rt, kb, Cs, lp, ncols, W, W2);
+      store_block(Rt, kb, A, nb, tr, c0, cc, kb, ncols, M_NONE);
+      store_block(Cs, lp, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
+      __syncthreads();
+    }
+  }
+}
+
+// UNMQR / TSMQR / TTMQR on one column strip [s*w, s*w + ncols) of the C tiles (oriented).
+__device__ void task_update(double* sm, int type, const double* X, double* Cp, double* C, int tr, bool notrans,
+                            const double* Tg, int nb, int ib, int w, int s) {
+  const Layout L = layout_update(nb, ib, w);
+  double *Cps = sm + L.Cp, *Cs = sm + L.Cs, *V = sm + L.P, *Tb = sm + L.Tb, *W = sm + L.W, *W2 = sm + L.W2;
+  const int lp = L.lp;
+  const int col0 = s * w;
+  const int ncols = min(w, nb - col0);
+  load_block(Cs, lp, C, nb, tr, 0, col0, nb, ncols, M_NONE);
+  if (type != UNMQR) load_block(Cps, lp, Cp, nb, tr, 0, col0, nb, ncols, M_NONE);
+  const int nblk = nb / ib;
+  for (int bb = 0; bb < nblk; ++bb) {
+    const int b = notrans ? nblk - 1 - bb : bb;
+    const int c0 = b * ib, kb = ib;
+    int vrows;
+    double *Ctop, *Cb;
+    if (type == UNMQR) {
+      vrows = nb - c0;
+      load_block(V, lp, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+      Ctop = nullptr;
+      Cb = Cs + c0;
+    } else if (type == TSMQR) {
+      vrows = nb;
+      load_block(V, lp, X, nb, tr, 0, c0, vrows, kb, M_NONE);
+      Ctop = Cps + c0;
+      Cb = Cs;
+    } else {
+      vrows = c0 + kb;
+      load_block(V, lp, X, nb, tr, 0, c0, vrows, kb, M_UPPER);
+      Ctop = Cps + c0;
+      Cb = Cs;
+    }
+    for (int o = threadIdx.x; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
+    __syncthreads();
+    apply_block(V, lp, vrows, kb, Tb, kb, notrans, Ctop, lp, Cb, lp, ncols, W, W2);
+  }
+  store_block(Cs, lp, C, nb, tr, 0, col0, nb, ncols, M_NONE);
+  if (type != UNMQR) store_block(Cps, lp, Cp, nb, tr, 0, col0, nb, ncols, M_NONE);
+}
+
+__device__ void task_copy(const double* src, double* dst, int nb, bool diag) {
+  for (int o = threadIdx.x; o < nb * nb; o += kThreads) {
+    const int r = o % nb, c = o / nb;
+    stg(dst + o, (diag && r > c) ? 0.0 : ldg(src + o));
+  }
+}
+
+__device__ __forceinline__ double* tile_ptr(const ExecParams& prm, int32_t ref, bool& ok) {
+  if (ref < 0) { ok = false; return nullptr; }
+  const int buf = (int)((uint32_t)ref >> 28);
+  const int64_t idx = ref & 0x0fffffff;
+  if (buf > 2 || prm.buf[buf] == nullptr || idx >= prm.ntiles[buf]) { ok = false; return nullptr; }
+  return prm.buf[buf] + (size_t)idx * prm.nb * prm.nb;
+}
+
+// Persistent dataflow executor: CTAs take sub-tasks from a queue in topological priority order,
+// wait (bounded) until the sub-tasks they depend on are done, run them and publish completion.
+// Taking tasks in queue order makes the scheme deadlock-free whatever the number of resident CTAs.
+__global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm) {
+  extern __shared__ double sm[];
+  __shared__ int s_idx;
+  __shared__ int s_abort;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_idx = (ld_relaxed(prm.err) != 0) ? prm.ntasks : atomicAdd(prm.head, 1);
+      s_abort = 0;
+    }
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= prm.ntasks) break;
+    const DevTask t = prm.tasks[idx];
+    if (warp == 0) {
+      int bad = 0;
+      for (int d = t.dep_begin + lane; d < t.dep_end; d += 32) {
+        const int dep = prm.deps[d];
+        if (dep < 0 || dep >= prm.nflags) { bad = 2; break; }
+        const uint64_t t0 = gtime();
+        while (ld_acquire(prm.done + dep) == 0) {
+          if (ld_relaxed(prm.err) != 0) { bad = 3; break; }
+          if (gtime() - t0 > prm.wait_ns) {
+            if (atomicCAS(prm.err, 0, DERR_TIMEOUT) == 0) {
+              prm.err[1] = idx;
+              prm.err[2] = dep;
+            }
+            bad = 1;
+            break;
+          }
+          __nanosleep(256);
+        }
+        if (bad) break;
+      }
+      bad = __reduce_max_sync(kFull, bad);
+      if (lane == 0 && bad) {
+        if (bad == 2 && atomicCAS(prm.err, 0, DERR_BADTASK) == 0) { prm.err[1] = idx; prm.err[2] = -1; }
+        s_abort = 1;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (s_abort) break;
+
+    const int type = t.op & 15;
+    const int tr = (t.op >> 4) & 1;
+    const bool notrans = (t.op >> 5) & 1;
+    const int strip = (t.op >> 8) & 0xffff;
+    bool ok = true;
+    double* X = tile_ptr(prm, t.x, ok);
+    double* Tg = (t.tslot >= 0 && t.tslot < prm.npanels) ? prm.T + (size_t)t.tslot * prm.ib * prm.nb : nullptr;
+    switch (type) {
+      case GEQRT:
+        if (ok && Tg) task_geqrt(sm, X, tr, Tg, prm.nb, prm.ib); else ok = false;
+        break;
+      case TSQRT:
+      case TTQRT: {
+        double* A = tile_ptr(prm, t.a, ok);
+        if (ok && Tg) task_tsqrt(sm, X, A, tr, Tg, prm.nb, prm.ib, type == TTQRT); else ok = false;
+        break;
+      }
+      case UNMQR:
+      case TSMQR:
+      case TTMQR: {
+        double* A = (type == UNMQR) ? nullptr : tile_ptr(prm, t.a, ok);
+        double* C = tile_ptr(prm, t.c, ok);
+        if (ok && Tg && strip * prm.w < prm.nb)
+          task_update(sm, type, X, A, C, tr, notrans, Tg, prm.nb, prm.ib, prm.w, strip);
+        else
+          ok = false;
+        break;
+      }
+      case COPY: {
+        double* C = tile_ptr(prm, t.c, ok);
+        if (ok) task_copy(X, C, prm.nb, t.flags & 1);
+        break;
+      }
+      default:
+        ok = false;
+    }
+    if (!ok && threadIdx.x == 0 && atomicCAS(prm.err, 0, DERR_BADTASK) == 0) {
+      prm.err[1] = idx;
+      prm.err[2] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(prm.done + idx, 1);
+    }
+  }
+}
+
+__global__ void pack_kernel(const double* __restrict__ A, int64_t lda, int64_t m, int64_t n, int nb,
+                            double* __restrict__ tiles, int64_t rows_t) {
+  const int64_t tile = blockIdx.x;
+  const int64_t a = tile % rows_t, b = tile / rows_t;
+  double* dst = tiles + (size_t)tile * nb * nb;
+  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+    const int r = o % nb, c = o / nb;
+    const int64_t gi = a * nb + r, gj = b * nb + c;
+    dst[o] = (gi < m && gj < n) ? A[gi + gj * lda] : 0.0;
+  }
+}
+
+__global__ void unpack_kernel(const double* __restrict__ tiles, int64_t rows_t, int nb, int64_t m, int64_t n,
+                              double* __restrict__ A, int64_t lda) {
+  const int64_t tile = blockIdx.x;
+  const int64_t a = tile % rows_t, b = tile / rows_t;
+  const double* src = tiles + (size_t)tile * nb * nb;
+  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+    const int r = o % nb, c = o / nb;
+    const int64_t gi = a * nb + r, gj = b * nb + c;
+    if (gi < m && gj < n) A[gi + gj * lda] = src[o];
+  }
+}
+
+// ab(d, j) = B(j + d - nb, j) for d = 0..nb: the diagonal tile's upper triangle and the super-diagonal
+// tile's lower triangle are exactly the band entries; rows < 0 are zero.
+__global__ void extract_kernel(const double* __restrict__ tiles, int64_t rows_t, int nb, int64_t n,
+                               double* __restrict__ ab, int64_t ldab) {
+  const int64_t j = blockIdx.x;
+  for (int d = threadIdx.x; d <= nb; d += blockDim.x) {
+    const int64_t i = j + d - nb;
+    double v = 0.0;
+    if (i >= 0) {
+      const int64_t a = i / nb, b = j / nb;
+      v = tiles[(size_t)(b * rows_t + a) * nb * nb + (i % nb) + (j % nb) * nb];
+    }
+    ab[d + j * ldab] = v;
+  }
+}
+
+}  // namespace
+
+size_t exec_smem_bytes(int nb, int ib, int w) {
+  const Layout a = layout_panel(nb, ib), b = layout_update(nb, ib, w);
+  return sizeof(double) * (size_t)(a.total > b.total ? a.total : b.total);
+}
+
+cudaError_t exec_set_smem(size_t smem) {
+  return cudaFuncSetAttribute(exec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int exec_max_ctas_per_sm(size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, exec_kernel, kThreads, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st) {
+  exec_kernel<<<grid, kThreads, smem, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const double* A, int64_t lda, int64_t m, int64_t n, int nb, double* tiles, int64_t rows_t,
+                        int64_t cols_t, cudaStream_t st) {
+  if (rows_t * cols_t == 0) return cudaSuccess;
+  pack_kernel<<<(unsigned)(rows_t * cols_t), 256, 0, st>>>(A, lda, m, n, nb, tiles, rows_t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const double* tiles, int64_t rows_t, int nb, int64_t m, int64_t n, double* A, int64_t lda,
+                          cudaStream_t st) {
+  const int64_t cols_t = (n + nb - 1) / nb;
+  if (rows_t * cols_t == 0) return cudaSuccess;
+  unpack_kernel<<<(unsigned)(rows_t * cols_t), 256, 0, st>>>(tiles, rows_t, nb, m, n, A, lda);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
+                           cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  extract_kernel<<<(unsigned)n, 256, 0, st>>>(tiles, rows_t, nb, n, ab, ldab);
+  return cudaGetLastError();
+}
+
+}  // namespace bd

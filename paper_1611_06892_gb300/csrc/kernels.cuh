@@ -1,0 +1,50 @@
+// Device-side interface shared by the C ABI (capi.cu) and the kernels (kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace bd {
+
+constexpr int kThreads = 256;       // threads of every executor CTA
+constexpr int kMaxNb = 256;
+constexpr int kChunk = 32;          // column chunk of the trailing update inside a panel task
+
+// Error word layout written by the executor: err[0] = code (0 ok, 1 wait ran out, 2 bad task),
+// err[1] = queue position of the failing task, err[2] = dependency it waited for.
+enum DevErr : int { DERR_OK = 0, DERR_TIMEOUT = 1, DERR_BADTASK = 2 };
+
+struct ExecParams {
+  const DevTask* tasks;
+  const int32_t* deps;
+  int32_t ntasks;
+  int32_t nflags;       // number of entries of done[] (>= ntasks; extra entries are never set)
+  int* done;
+  int* head;
+  int* err;
+  double* buf[3];       // tile buffers: A tiles, R copy (R-BiDiag), apply target
+  int64_t ntiles[3];
+  double* T;
+  int32_t npanels;
+  int nb, ib, w;        // tile size, inner blocking, strip width
+  uint64_t wait_ns;
+};
+
+// Shared memory (bytes) the executor needs for (nb, ib, w).
+size_t exec_smem_bytes(int nb, int ib, int w);
+
+cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st);
+cudaError_t exec_set_smem(size_t smem);
+int exec_max_ctas_per_sm(size_t smem);
+
+// Column-major (ld) matrix <-> zero-padded tile buffer (grid of rows_t x cols_t tiles of nb x nb).
+cudaError_t launch_pack(const double* A, int64_t lda, int64_t m, int64_t n, int nb, double* tiles, int64_t rows_t,
+                        int64_t cols_t, cudaStream_t st);
+cudaError_t launch_unpack(const double* tiles, int64_t rows_t, int nb, int64_t m, int64_t n, double* A, int64_t lda,
+                          cudaStream_t st);
+// Band extraction: ab((nb+1) x n, ld ldab) from the tile buffer (grid rows rows_t).
+cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
+                           cudaStream_t st);
+
+}  // namespace bd

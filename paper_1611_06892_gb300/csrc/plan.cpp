@@ -1,0 +1,510 @@
+// Host planner: reduction trees, canonical task lists and the task DAG of tiled BiDiag / R-BiDiag,
+// and the device program (sub-tasks + dependencies in a topological priority order).
+//
+// Trees (Sec. 3.3 and Sec. 5 of Faverge, Langou, Robert, Dongarra, arXiv 1611.06892):
+//  * FlatTS / FlatTT: the pivot is the first panel tile; every other tile is eliminated into it in
+//    order, with TS (Algorithm 2) or TT (Algorithm 3) kernels.
+//  * Greedy: halving rule - with ready rows r_0 < ... < r_{z-1} and h = floor(z/2), r_{z-h+t} is
+//    eliminated into r_{z-2h+t}; repeated on the survivors (depth ceil(log2 z), Sec. 4).  For the
+//    multi-column QR(p,q) of R-BiDiag it is time-stepped: at time s the rows ready in column k are
+//    those eliminated in column k-1 at a time < s (all rows for k = 0) and not yet eliminated in k.
+//  * Auto (Sec. 5): FlatTS groups of a consecutive tiles, heads joined by the halving Greedy rule with
+//    TT kernels; a is the largest value in [1, u] with ceil(u/a) * v >= 2 * R (else 1), u and v being
+//    the live numbers of panel tiles and trailing tiles of the step.
+// Sequences: BiDiag QR(1); LQ(1); ...; LQ(q-1); QR(q) (Sec. 3.4); R-BiDiag QR(p,q); LQ(1); QR(2); ...
+// on a separate copy of R (Sec. 3.5 and 3.6).  A tile already in triangle form is not factored again
+// (end of Sec. 3.2).
+#include "plan.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <stdexcept>
+
+namespace bd {
+
+namespace {
+
+struct Pair {
+  int i, piv;
+};
+
+// Halving Greedy: list of rounds of (eliminated, pivot).
+std::vector<std::vector<Pair>> halving_rounds(std::vector<int> rows) {
+  std::vector<std::vector<Pair>> rounds;
+  while (rows.size() > 1) {
+    const int z = (int)rows.size(), h = z / 2;
+    std::vector<Pair> rnd;
+    std::vector<char> gone(z, 0);
+    for (int t = 0; t < h; ++t) {
+      rnd.push_back({rows[z - h + t], rows[z - 2 * h + t]});
+      gone[z - h + t] = 1;
+    }
+    std::vector<int> keep;
+    for (int x = 0; x < z; ++x)
+      if (!gone[x]) keep.push_back(rows[x]);
+    rows.swap(keep);
+    rounds.push_back(rnd);
+  }
+  return rounds;
+}
+
+int auto_a(int u, int v, int64_t R) {
+  for (int a = u; a >= 1; --a) {
+    const int64_t groups = (u + a - 1) / a;
+    if (groups * (int64_t)v >= 2 * R) return a;
+  }
+  return 1;
+}
+
+struct El {
+  int i, piv, kind;
+};
+
+std::vector<El> one_step(const std::vector<int>& rows, int v, int tree, int64_t R) {
+  std::vector<El> out;
+  if (rows.size() < 2) return out;
+  if (tree == FLATTS || tree == FLATTT) {
+    for (size_t x = 1; x < rows.size(); ++x) out.push_back({rows[x], rows[0], tree == FLATTS ? K_TS : K_TT});
+  } else if (tree == GREEDY) {
+    for (auto& rnd : halving_rounds(rows))
+      for (auto& pr : rnd) out.push_back({pr.i, pr.piv, K_TT});
+  } else if (tree == AUTO) {
+    const int u = (int)rows.size();
+    const int a = auto_a(u, v, R);
+    std::vector<int> heads;
+    for (int s = 0; s < u; s += a) {
+      heads.push_back(rows[s]);
+      for (int x = s + 1; x < std::min(u, s + a); ++x) out.push_back({rows[x], rows[s], K_TS});
+    }
+    for (auto& rnd : halving_rounds(heads))
+      for (auto& pr : rnd) out.push_back({pr.i, pr.piv, K_TT});
+  } else {
+    throw std::invalid_argument("tree");
+  }
+  return out;
+}
+
+// Time-stepped greedy over all columns of QR(p, q): (k, i, piv) in (time, column) order.
+struct CEl {
+  int k, i, piv;
+};
+std::vector<CEl> greedy_columns(int p, int q) {
+  const int kmax = std::min(p, q);
+  std::vector<int> t_elim((size_t)p * kmax, -1);  // time at which row i was eliminated in column k
+  auto T = [&](int i, int k) -> int& { return t_elim[(size_t)k * p + i]; };
+  std::vector<int> remaining(kmax);
+  int total = 0;
+  for (int k = 0; k < kmax; ++k) total += (remaining[k] = p - 1 - k);
+  std::vector<CEl> out;
+  for (int s = 0; total > 0; ++s) {
+    for (int k = 0; k < kmax; ++k) {
+      if (!remaining[k]) continue;
+      std::vector<int> ready;
+      for (int i = k; i < p; ++i) {
+        if (T(i, k) >= 0) continue;
+        if (k == 0 || (T(i, k - 1) >= 0 && T(i, k - 1) < s)) ready.push_back(i);
+      }
+      const int z = (int)ready.size(), h = z / 2;
+      for (int t = 0; t < h; ++t) {
+        const int i = ready[z - h + t], piv = ready[z - 2 * h + t];
+        T(i, k) = s;
+        out.push_back({k, i, piv});
+        --remaining[k];
+        --total;
+      }
+    }
+  }
+  return out;
+}
+
+struct Step {
+  int phase, k;
+  std::vector<int> rows;
+  int ntrail;
+};
+
+std::vector<Step> steps_of(int p, int q, int variant) {
+  std::vector<Step> st;
+  auto range = [](int a, int b) {
+    std::vector<int> r;
+    for (int x = a; x < b; ++x) r.push_back(x);
+    return r;
+  };
+  if (variant == V_BIDIAG) {
+    for (int k = 0; k < q; ++k) {
+      st.push_back({PH_QR, k, range(k, p), q - k - 1});
+      if (k < q - 1) st.push_back({PH_LQ, k, range(k + 1, q), p - k - 1});
+    }
+  } else {
+    for (int k = 0; k + 1 < q; ++k) {
+      st.push_back({PH_LQ, k, range(k + 1, q), q - k - 1});
+      st.push_back({PH_QR, k + 1, range(k + 1, q), q - k - 2});
+    }
+  }
+  return st;
+}
+
+// Expansion of eliminations into kernel tasks (Algorithms 2 and 3).
+struct Expander {
+  std::vector<Task>& out;
+  std::vector<char> tri;  // (phase, k, row) already triangular
+  int p;
+  Expander(std::vector<Task>& o, int p_) : out(o), tri((size_t)3 * (p_ + 1) * (p_ + 1), 0), p(p_) {}
+  char& flag(int phase, int k, int r) { return tri[((size_t)phase * (p + 1) + k) * (p + 1) + r]; }
+  bool factor(int phase, int k, int r) {
+    if (flag(phase, k, r)) return false;
+    flag(phase, k, r) = 1;
+    out.push_back({GEQRT, phase, k, r, -1, -1});
+    return true;
+  }
+  void elim(int phase, int k, const El& e, int ntrail) {
+    if (e.kind == K_TS) {
+      const bool fp = factor(phase, k, e.piv);
+      out.push_back({TSQRT, phase, k, e.i, e.piv, -1});
+      for (int j = k + 1; j <= k + ntrail; ++j) {
+        if (fp) out.push_back({UNMQR, phase, k, e.piv, -1, j});
+        out.push_back({TSMQR, phase, k, e.i, e.piv, j});
+      }
+    } else {
+      const bool fp = factor(phase, k, e.piv);
+      const bool fi = factor(phase, k, e.i);
+      for (int j = k + 1; j <= k + ntrail; ++j) {
+        if (fp) out.push_back({UNMQR, phase, k, e.piv, -1, j});
+        if (fi) out.push_back({UNMQR, phase, k, e.i, -1, j});
+      }
+      out.push_back({TTQRT, phase, k, e.i, e.piv, -1});
+      for (int j = k + 1; j <= k + ntrail; ++j) out.push_back({TTMQR, phase, k, e.i, e.piv, j});
+    }
+  }
+  void single(int phase, int k, int row, int ntrail) {
+    if (!factor(phase, k, row)) return;
+    for (int j = k + 1; j <= k + ntrail; ++j) out.push_back({UNMQR, phase, k, row, -1, j});
+  }
+};
+
+}  // namespace
+
+std::vector<Elim> make_eliminations(int p, int q, int tree, int variant, int64_t R) {
+  std::vector<Elim> out;
+  if (variant == V_RBIDIAG) {
+    if (tree == GREEDY) {
+      for (auto& e : greedy_columns(p, q)) out.push_back({PH_PQR, e.k, e.i, e.piv, K_TT});
+    } else {
+      for (int k = 0; k < std::min(p, q); ++k) {
+        std::vector<int> rows;
+        for (int r = k; r < p; ++r) rows.push_back(r);
+        for (auto& e : one_step(rows, q - k - 1, tree, R)) out.push_back({PH_PQR, k, e.i, e.piv, e.kind});
+      }
+    }
+  }
+  for (auto& s : steps_of(p, q, variant))
+    for (auto& e : one_step(s.rows, s.ntrail, tree, R)) out.push_back({s.phase, s.k, e.i, e.piv, e.kind});
+  return out;
+}
+
+std::vector<Task> make_tasks(int p, int q, int tree, int variant, int64_t R) {
+  if (!(p >= q && q >= 1)) throw std::invalid_argument("need p >= q >= 1");
+  std::vector<Task> tasks;
+  Expander ex(tasks, p);
+  if (variant == V_RBIDIAG) {
+    if (tree == GREEDY) {
+      std::vector<char> seen(q, 0);
+      for (auto& e : greedy_columns(p, q)) {
+        ex.elim(PH_PQR, e.k, {e.i, e.piv, K_TT}, q - e.k - 1);
+        seen[e.k] = 1;
+      }
+      for (int k = 0; k < std::min(p, q); ++k)
+        if (!seen[k]) ex.single(PH_PQR, k, k, q - k - 1);
+    } else {
+      for (int k = 0; k < std::min(p, q); ++k) {
+        std::vector<int> rows;
+        for (int r = k; r < p; ++r) rows.push_back(r);
+        auto el = one_step(rows, q - k - 1, tree, R);
+        if (el.empty()) ex.single(PH_PQR, k, k, q - k - 1);
+        for (auto& e : el) ex.elim(PH_PQR, k, e, q - k - 1);
+      }
+    }
+    for (int a = 0; a < q; ++a)
+      for (int b = a; b < q; ++b) tasks.push_back({COPY, PH_PQR, -1, a, -1, b});
+  }
+  for (auto& s : steps_of(p, q, variant)) {
+    auto el = one_step(s.rows, s.ntrail, tree, R);
+    if (el.empty()) ex.single(s.phase, s.k, s.rows[0], s.ntrail);
+    for (auto& e : el) ex.elim(s.phase, s.k, e, s.ntrail);
+  }
+  return tasks;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Task DAG.  Data items: strict upper (SU), diagonal (D) and strict lower (SL) part of every tile of
+// A (buffer 0) and of the R copy (buffer 1), plus the reflector object (V, T) of each panel task.
+// Edges: read-after-write, write-after-write, write-after-read.
+// ---------------------------------------------------------------------------------------------
+namespace {
+enum Part { SU = 0, D = 1, SL = 2 };
+
+struct Access {
+  int rd[6], nrd = 0;
+  int wr[9], nwr = 0;
+};
+
+struct ItemMap {
+  int p, q;
+  int id(int buf, int a, int b, int part) const { return ((buf * q + b) * p + a) * 3 + part; }
+  int size() const { return 2 * q * p * 3; }
+};
+
+Access access_of(const Task& t, int variant, const ItemMap& im) {
+  Access ac;
+  const int buf = (variant == V_RBIDIAG && t.phase != PH_PQR) ? 1 : 0;
+  const bool lq = t.phase == PH_LQ;
+  auto put = [&](int* arr, int& n, int a, int b, int part) {
+    const int x = lq ? b : a, y = lq ? a : b;
+    arr[n++] = im.id(buf, x, y, part);
+  };
+  auto up = [&](int* arr, int& n, int a, int b) {
+    put(arr, n, a, b, D);
+    put(arr, n, a, b, lq ? SL : SU);  // oriented strict upper
+  };
+  auto lo = [&](int* arr, int& n, int a, int b) { put(arr, n, a, b, lq ? SU : SL); };
+  auto full = [&](int* arr, int& n, int a, int b) {
+    put(arr, n, a, b, SU);
+    put(arr, n, a, b, D);
+    put(arr, n, a, b, SL);
+  };
+  switch (t.type) {
+    case GEQRT: full(ac.wr, ac.nwr, t.i, t.k); break;
+    case UNMQR: lo(ac.rd, ac.nrd, t.i, t.k); full(ac.wr, ac.nwr, t.i, t.j); break;
+    case TSQRT: up(ac.wr, ac.nwr, t.piv, t.k); full(ac.wr, ac.nwr, t.i, t.k); break;
+    case TSMQR: full(ac.rd, ac.nrd, t.i, t.k); full(ac.wr, ac.nwr, t.piv, t.j); full(ac.wr, ac.nwr, t.i, t.j); break;
+    case TTQRT: up(ac.wr, ac.nwr, t.piv, t.k); up(ac.wr, ac.nwr, t.i, t.k); break;
+    case TTMQR: up(ac.rd, ac.nrd, t.i, t.k); full(ac.wr, ac.nwr, t.piv, t.j); full(ac.wr, ac.nwr, t.i, t.j); break;
+    case COPY: {
+      const int a = t.i, b = t.j;
+      if (a == b) {
+        ac.rd[ac.nrd++] = im.id(0, a, a, D);
+        ac.rd[ac.nrd++] = im.id(0, a, a, SU);
+      } else {
+        for (int part = 0; part < 3; ++part) ac.rd[ac.nrd++] = im.id(0, a, b, part);
+      }
+      for (int part = 0; part < 3; ++part) ac.wr[ac.nwr++] = im.id(1, a, b, part);
+      break;
+    }
+    default: throw std::invalid_argument("task type");
+  }
+  return ac;
+}
+
+const int kWeight[7] = {4, 6, 6, 12, 2, 6, 0};  // Table 1
+}  // namespace
+
+void make_dag(const std::vector<Task>& tasks, int p, int q, int variant, std::vector<std::vector<int32_t>>* preds,
+              std::vector<int32_t>* level, int64_t* cp) {
+  ItemMap im{p, q};
+  std::vector<int32_t> last_w(im.size(), -1);
+  std::vector<std::vector<int32_t>> readers(im.size());
+  // owner panel of each update (reflector object)
+  std::vector<int32_t> owner(tasks.size(), -1);
+  {
+    // key (type, phase, k, i) -> last panel index
+    std::vector<int32_t> last_panel((size_t)3 * 3 * (q + 1) * (p + 1), -1);
+    auto key = [&](int ptype, int phase, int k, int i) {
+      return (((size_t)ptype * 3 + phase) * (q + 1) + k) * (p + 1) + i;
+    };
+    for (size_t x = 0; x < tasks.size(); ++x) {
+      const Task& t = tasks[x];
+      switch (t.type) {
+        case GEQRT: last_panel[key(0, t.phase, t.k, t.i)] = (int32_t)x; break;
+        case TSQRT: last_panel[key(1, t.phase, t.k, t.i)] = (int32_t)x; break;
+        case TTQRT: last_panel[key(2, t.phase, t.k, t.i)] = (int32_t)x; break;
+        case UNMQR: owner[x] = last_panel[key(0, t.phase, t.k, t.i)]; break;
+        case TSMQR: owner[x] = last_panel[key(1, t.phase, t.k, t.i)]; break;
+        case TTMQR: owner[x] = last_panel[key(2, t.phase, t.k, t.i)]; break;
+        default: break;
+      }
+    }
+  }
+  std::vector<int32_t> lv(tasks.size(), 0);
+  std::vector<int64_t> fin(tasks.size(), 0);
+  if (preds) preds->assign(tasks.size(), {});
+  int64_t best = 0;
+  std::vector<int32_t> pr;
+  for (size_t x = 0; x < tasks.size(); ++x) {
+    const Access ac = access_of(tasks[x], variant, im);
+    pr.clear();
+    for (int r = 0; r < ac.nrd; ++r)
+      if (last_w[ac.rd[r]] >= 0) pr.push_back(last_w[ac.rd[r]]);
+    for (int w = 0; w < ac.nwr; ++w) {
+      if (last_w[ac.wr[w]] >= 0) pr.push_back(last_w[ac.wr[w]]);
+      for (int32_t rr : readers[ac.wr[w]]) pr.push_back(rr);
+    }
+    if (owner[x] >= 0) pr.push_back(owner[x]);
+    std::sort(pr.begin(), pr.end());
+    pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+    int32_t l = 0;
+    int64_t f = 0;
+    for (int32_t d : pr) {
+      if (d == (int32_t)x) continue;
+      l = std::max(l, lv[d] + 1);
+      f = std::max(f, fin[d]);
+    }
+    lv[x] = l;
+    fin[x] = f + kWeight[tasks[x].type];
+    best = std::max(best, fin[x]);
+    if (preds) (*preds)[x] = pr;
+    for (int r = 0; r < ac.nrd; ++r) readers[ac.rd[r]].push_back((int32_t)x);
+    for (int w = 0; w < ac.nwr; ++w) {
+      last_w[ac.wr[w]] = (int32_t)x;
+      readers[ac.wr[w]].clear();
+    }
+  }
+  if (level) *level = lv;
+  if (cp) *cp = best;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device program: every update task is split into `nstrips` column strips of its C tiles (columns
+// in the step's orientation); panel and COPY tasks are one sub-task each.  A strip of an update
+// depends only on the same strip of a preceding update of the same orientation; any other
+// dependency is on every sub-task of the predecessor.  Sub-tasks are ordered by decreasing bottom
+// level (longest weighted path to the end), which is a topological order since weights are > 0.
+// ---------------------------------------------------------------------------------------------
+void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t R, int strip_w) {
+  pl.m = m;
+  pl.n = n;
+  pl.nb = nb;
+  pl.ib = ib;
+  pl.tree = tree;
+  pl.variant = variant;
+  pl.resources = R;
+  pl.p = (int)((m + nb - 1) / nb);
+  pl.q = (int)((n + nb - 1) / nb);
+  pl.strip_w = std::min(strip_w, nb);
+  pl.nstrips = (nb + pl.strip_w - 1) / pl.strip_w;
+  const int p = pl.p, q = pl.q, S = pl.nstrips;
+  pl.elims = make_eliminations(p, q, tree, variant, R);
+  pl.tasks = make_tasks(p, q, tree, variant, R);
+  std::vector<std::vector<int32_t>> preds;
+  make_dag(pl.tasks, p, q, variant, &preds, &pl.level, &pl.critical_path);
+  const size_t nt = pl.tasks.size();
+
+  // T slots and owners
+  pl.tslot.assign(nt, -1);
+  pl.owner.assign(nt, -1);
+  pl.npanels = 0;
+  for (size_t x = 0; x < nt; ++x) {
+    const int ty = pl.tasks[x].type;
+    if (ty == GEQRT || ty == TSQRT || ty == TTQRT) pl.tslot[x] = pl.npanels++;
+  }
+  {
+    std::vector<int32_t> lastp((size_t)3 * 3 * (q + 1) * (p + 1), -1);
+    auto key = [&](int ptype, int phase, int k, int i) {
+      return (((size_t)ptype * 3 + phase) * (q + 1) + k) * (p + 1) + i;
+    };
+    for (size_t x = 0; x < nt; ++x) {
+      const Task& t = pl.tasks[x];
+      if (t.type == GEQRT) lastp[key(0, t.phase, t.k, t.i)] = (int32_t)x;
+      if (t.type == TSQRT) lastp[key(1, t.phase, t.k, t.i)] = (int32_t)x;
+      if (t.type == TTQRT) lastp[key(2, t.phase, t.k, t.i)] = (int32_t)x;
+      if (t.type == UNMQR) pl.owner[x] = lastp[key(0, t.phase, t.k, t.i)];
+      if (t.type == TSMQR) pl.owner[x] = lastp[key(1, t.phase, t.k, t.i)];
+      if (t.type == TTMQR) pl.owner[x] = lastp[key(2, t.phase, t.k, t.i)];
+    }
+  }
+
+  // sub-tasks in program order
+  auto is_update = [](int ty) { return ty == UNMQR || ty == TSMQR || ty == TTMQR; };
+  std::vector<int32_t> first(nt + 1, 0);
+  for (size_t x = 0; x < nt; ++x) first[x + 1] = first[x] + (is_update(pl.tasks[x].type) ? S : 1);
+  const int32_t nsub = first[nt];
+  std::vector<DevTask> sub(nsub);
+  std::vector<int64_t> wsub(nsub);
+  std::vector<std::vector<int32_t>> sdeps(nsub);
+  auto tref = [&](int buf, int a, int b, bool lq) {
+    // actual tile of oriented (a, b)
+    const int x = lq ? b : a, y = lq ? a : b;
+    const int rows = buf == 0 ? p : q;
+    return tile_ref(buf, (int64_t)y * rows + x);
+  };
+  for (size_t x = 0; x < nt; ++x) {
+    const Task& t = pl.tasks[x];
+    const int buf = (variant == V_RBIDIAG && t.phase != PH_PQR) ? 1 : 0;
+    const bool lq = t.phase == PH_LQ;
+    DevTask d{};
+    d.op = t.type | ((lq ? 1 : 0) << 4);
+    d.x = d.a = d.c = -1;
+    d.tslot = -1;
+    d.flags = 0;
+    switch (t.type) {
+      case GEQRT: d.x = tref(buf, t.i, t.k, lq); d.tslot = pl.tslot[x]; break;
+      case TSQRT:
+      case TTQRT:
+        d.x = tref(buf, t.i, t.k, lq);
+        d.a = tref(buf, t.piv, t.k, lq);
+        d.tslot = pl.tslot[x];
+        break;
+      case UNMQR:
+        d.x = tref(buf, t.i, t.k, lq);
+        d.c = tref(buf, t.i, t.j, lq);
+        d.tslot = pl.tslot[pl.owner[x]];
+        break;
+      case TSMQR:
+      case TTMQR:
+        d.x = tref(buf, t.i, t.k, lq);
+        d.a = tref(buf, t.piv, t.j, lq);
+        d.c = tref(buf, t.i, t.j, lq);
+        d.tslot = pl.tslot[pl.owner[x]];
+        break;
+      case COPY:
+        d.x = tile_ref(0, (int64_t)t.j * p + t.i);
+        d.c = tile_ref(1, (int64_t)t.j * q + t.i);
+        d.flags = t.i == t.j ? 1 : 0;
+        break;
+    }
+    const int ns = first[x + 1] - first[x];
+    for (int s = 0; s < ns; ++s) {
+      DevTask e = d;
+      e.op |= (s << 8);
+      sub[first[x] + s] = e;
+      wsub[first[x] + s] = is_update(t.type) ? kWeight[t.type] : (t.type == COPY ? 1 : (int64_t)kWeight[t.type] * S);
+    }
+    for (int32_t pd : preds[x]) {
+      if (pd == (int32_t)x) continue;
+      const Task& u = pl.tasks[pd];
+      const bool strip_wise = is_update(t.type) && is_update(u.type) && (u.phase == PH_LQ) == lq &&
+                              ((variant == V_RBIDIAG && u.phase != PH_PQR) ? 1 : 0) == buf;
+      for (int s = 0; s < ns; ++s) {
+        if (strip_wise) {
+          sdeps[first[x] + s].push_back(first[pd] + s);
+        } else {
+          for (int32_t y = first[pd]; y < first[pd + 1]; ++y) sdeps[first[x] + s].push_back(y);
+        }
+      }
+    }
+  }
+  // bottom levels (program order is topological: deps point backwards)
+  std::vector<int64_t> bottom(nsub, 0);
+  for (int32_t y = nsub - 1; y >= 0; --y) {
+    bottom[y] += wsub[y];
+    for (int32_t d : sdeps[y]) bottom[d] = std::max(bottom[d], bottom[y]);
+  }
+  std::vector<int32_t> order(nsub);
+  for (int32_t y = 0; y < nsub; ++y) order[y] = y;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return bottom[a] > bottom[b]; });
+  std::vector<int32_t> pos(nsub);
+  for (int32_t y = 0; y < nsub; ++y) pos[order[y]] = y;
+  pl.dev.resize(nsub);
+  pl.deps.clear();
+  for (int32_t y = 0; y < nsub; ++y) {
+    DevTask e = sub[order[y]];
+    e.dep_begin = (int32_t)pl.deps.size();
+    for (int32_t d : sdeps[order[y]]) {
+      if (pos[d] >= y) throw std::logic_error("priority order is not topological");
+      pl.deps.push_back(pos[d]);
+    }
+    e.dep_end = (int32_t)pl.deps.size();
+    pl.dev[y] = e;
+  }
+}
+
+}  // namespace bd

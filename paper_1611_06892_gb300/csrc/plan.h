@@ -1,0 +1,63 @@
+// Host planner of the tiled BiDiag / R-BiDiag reduction: reduction trees -> canonical task list ->
+// task DAG -> device sub-tasks in a topological priority order for the persistent executor.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace bd {
+
+enum TaskType : int { GEQRT = 0, UNMQR = 1, TSQRT = 2, TSMQR = 3, TTQRT = 4, TTMQR = 5, COPY = 6 };
+enum Phase : int { PH_QR = 0, PH_LQ = 1, PH_PQR = 2 };
+enum Tree : int { FLATTS = 0, FLATTT = 1, GREEDY = 2, AUTO = 3 };
+enum Variant : int { V_BIDIAG = 0, V_RBIDIAG = 1 };
+enum Kind : int { K_TS = 0, K_TT = 1 };
+
+struct Task {
+  int type, phase, k, i, piv, j;
+};
+struct Elim {
+  int phase, k, i, piv, kind;
+};
+
+// One unit of work of the persistent executor (32 bytes).  Tile references pack a buffer id in the
+// top 4 bits and the tile index (column-major tile grid of that buffer) in the low 28 bits.
+struct DevTask {
+  int32_t op;        // type | tr << 4 | notrans << 5 | strip << 8
+  int32_t x;         // reflector / panel tile (COPY: source tile)
+  int32_t a;         // pivot tile (TS/TT panels) or top C tile (TSMQR/TTMQR)
+  int32_t c;         // C tile of UNMQR / bottom C tile of TSMQR, TTMQR (COPY: destination tile)
+  int32_t tslot;     // T slot of the panel task
+  int32_t dep_begin; // deps in [dep_begin, dep_end) of the dependency array
+  int32_t dep_end;
+  int32_t flags;     // bit 0: diagonal COPY (upper triangle only)
+};
+
+inline int32_t tile_ref(int buf, int64_t idx) { return (int32_t)(((uint32_t)buf << 28) | (uint32_t)idx); }
+
+struct Plan {
+  int64_t m = 0, n = 0;
+  int nb = 0, ib = 0, tree = 0, variant = 0, p = 0, q = 0, strip_w = 32, nstrips = 1;
+  int64_t resources = 0;
+  std::vector<Elim> elims;
+  std::vector<Task> tasks;
+  std::vector<int32_t> level;
+  std::vector<int32_t> tslot;      // per task
+  std::vector<int32_t> owner;      // per update task: panel task index
+  int npanels = 0;
+  int64_t critical_path = 0;       // Table 1 units
+  // device program
+  std::vector<DevTask> dev;        // in queue (priority) order
+  std::vector<int32_t> deps;       // indices into dev (queue positions)
+};
+
+// Trees and task lists (independent of any device state).
+std::vector<Elim> make_eliminations(int p, int q, int tree, int variant, int64_t resources);
+std::vector<Task> make_tasks(int p, int q, int tree, int variant, int64_t resources);
+// Task DAG: predecessor lists, levels and the Table 1 critical path.
+void make_dag(const std::vector<Task>& tasks, int p, int q, int variant,
+              std::vector<std::vector<int32_t>>* preds, std::vector<int32_t>* level, int64_t* cp);
+// Full plan for a reduction: tasks, DAG, device sub-tasks ordered by critical-path priority.
+void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
+                int strip_w);
+
+}  // namespace bd

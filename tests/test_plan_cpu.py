@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI library (no GPU): it loads, exports every declared symbol, and its
+planner reproduces the oracle's elimination lists, task lists, DAG levels and critical paths."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1611_06892_gb300 as G
+from oracle import trees as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built_library():
+    if not os.path.exists(G.LIB_PATH):
+        from paper_1611_06892_gb300 import build
+        build.build()
+    return G.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bidiag.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bidiag_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    lib = ctypes.CDLL(G.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("variant", (T.BIDIAG, T.RBIDIAG), ids=("bidiag", "rbidiag"))
+@pytest.mark.parametrize("tree", (T.FLATTS, T.FLATTT, T.GREEDY, T.AUTO), ids=("flatts", "flattt", "greedy", "auto"))
+def test_planner_matches_oracle(tree, variant):
+    """Canonical elimination list, task list and level of every task match bit-exact (p, q <= 11)."""
+    for p in range(1, 12):
+        for q in range(1, p + 1):
+            for R in (1, 3, 40):
+                el_o = np.array(T.eliminations(p, q, tree, variant, R), dtype=np.int32).reshape(-1, 5)
+                el_c = G.bidiag_plan_eliminations(p, q, tree, variant, R)
+                assert np.array_equal(el_o, el_c), (p, q, R)
+                tasks = T.task_list(p, q, tree, variant, R)
+                tk_c, lv_c, cp_c = G.bidiag_plan_tasks(p, q, tree, variant, R)
+                assert np.array_equal(np.array(tasks, dtype=np.int32).reshape(-1, 6), tk_c), (p, q, R)
+                lv_o, _, cp_o = T.dag(tasks, variant)
+                assert np.array_equal(np.array(lv_o, dtype=np.int32), lv_c) and cp_o == cp_c, (p, q, R)
+
+
+def test_planner_cfg_sizes_match_oracle():
+    """The bench's tile grids: 32 x 32 (8192^2, nb 256) and 256 x 4 (65536 x 1024)."""
+    for (p, q, variant) in ((32, 32, T.BIDIAG), (256, 4, T.RBIDIAG)):
+        for tree in (T.FLATTS, T.GREEDY, T.AUTO):
+            tasks = T.task_list(p, q, tree, variant, 152)
+            tk_c, lv_c, cp_c = G.bidiag_plan_tasks(p, q, tree, variant, 152)
+            assert np.array_equal(np.array(tasks, dtype=np.int32).reshape(-1, 6), tk_c)
+            lv_o, _, cp_o = T.dag(tasks, variant)
+            assert np.array_equal(np.array(lv_o, dtype=np.int32), lv_c) and cp_o == cp_c
+
+
+def test_planner_printed_critical_paths():
+    """The planner's own DAG reproduces the printed R-BiDiagGreedy values (Sec. 4.3.2)."""
+    for p, q, val in ((65, 5, 262), (66, 5, 260), (134, 10, 680), (133, 10, 682), (535, 50, 4946), (534, 50, 4948)):
+        assert G.bidiag_plan_tasks(p, q, T.GREEDY, T.RBIDIAG)[2] == val
+
+
+def test_switch_ratio_q100():
+    """Sec. 4.3.3: for q = 100 the BiDiagGreedy / R-BiDiagGreedy crossover is delta_s = 5.67, i.e. it
+    lies between p = 566 and p = 568 tiles."""
+    q = 100
+
+    def better_r(p):
+        return G.bidiag_plan_tasks(p, q, T.GREEDY, T.RBIDIAG)[2] < G.bidiag_plan_tasks(p, q, T.GREEDY, T.BIDIAG)[2]
+
+    assert not better_r(560)
+    assert better_r(575)
+    lo, hi = 560, 575
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if better_r(mid):
+            hi = mid
+        else:
+            lo = mid
+    assert 5.66 <= hi / q <= 5.68
+
+
+def test_planner_argument_errors():
+    lib = G.load_library()
+    cnt = ctypes.c_int64()
+    assert lib.bidiag_plan_tasks(3, 4, 0, 0, 1, None, None, 0, ctypes.byref(cnt), None) == -1   # q > p
+    assert lib.bidiag_plan_tasks(4, 3, 7, 0, 1, None, None, 0, ctypes.byref(cnt), None) == -3
+    assert lib.bidiag_plan_tasks(4, 3, 0, 5, 1, None, None, 0, ctypes.byref(cnt), None) == -4
+    assert lib.bidiag_plan_eliminations(4, 3, 0, 0, 1, None, 0, None) == -8
