@@ -154,7 +154,8 @@ const char* bidiag_last_error(bidiag_handle h);
 /* Releases a result (stream-ordered on the handle's stream that made it). */
 int bidiag_result_free(bidiag_result_t r);
 
-/* Releases the handle (synchronises its stream first). */
+/* Releases the handle (synchronises its stream first).  Results made on it that are still alive lose
+ * their device buffers; bidiag_result_free must still be called on them to release the host object. */
 int bidiag_destroy(bidiag_handle h);
 
 /* ---------------------------------------------------------------------------------------------

@@ -8,6 +8,7 @@
 #include <map>
 #include <memory>
 #include <new>
+#include <set>
 #include <stdexcept>
 #include <string>
 #include <tuple>
@@ -52,6 +53,7 @@ struct bidiag_ctx {
   int timing = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool timed = false;
+  std::set<bidiag_result*> live;   // results made on this handle and not yet freed
 };
 
 struct bidiag_result {
@@ -428,6 +430,7 @@ int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_
   if (rc) return bail(rc);
   e = bd::launch_extract(r->tiles2 ? r->tiles2 : r->tiles, r->tiles2 ? r->q : r->p, nb, n, r->ab, r->ldab, h->stream);
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "extract"));
+  h->live.insert(r);
   *out = r;
   return BIDIAG_OK;
 }
@@ -508,6 +511,7 @@ int bidiag_result_reflectors(bidiag_result_t r, bidiag_reflectors* desc) {
 int bidiag_apply_q(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols, double* d_C, int64_t ldc) {
   if (!h) return -1;
   if (!r) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result was made on another handle or its handle was destroyed");
   if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
   if (ncols < 0) return fail(h, -4, "ncols < 0");
   if (!d_C && ncols > 0) return fail(h, -5, "C is NULL");
@@ -519,6 +523,7 @@ int bidiag_apply_q(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols,
 int bidiag_apply_p(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, double* d_C, int64_t ldc) {
   if (!h) return -1;
   if (!r) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result was made on another handle or its handle was destroyed");
   if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
   if (nrows < 0) return fail(h, -4, "nrows < 0");
   if (!d_C && nrows > 0) return fail(h, -5, "C is NULL");
@@ -556,8 +561,11 @@ const char* bidiag_last_error(bidiag_handle h) { return h ? h->err.c_str() : "nu
 
 int bidiag_result_free(bidiag_result_t r) {
   if (!r) return -1;
-  if (r->h) cudaSetDevice(r->h->device);
-  free_result_buffers(r);
+  if (r->h) {
+    cudaSetDevice(r->h->device);
+    r->h->live.erase(r);
+    free_result_buffers(r);
+  }
   delete r;
   return BIDIAG_OK;
 }
@@ -565,6 +573,13 @@ int bidiag_result_free(bidiag_result_t r) {
 int bidiag_destroy(bidiag_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  // results still alive lose their buffers now; freeing them later only releases the host object
+  for (bidiag_result* r : h->live) {
+    free_result_buffers(r);
+    r->h = nullptr;
+  }
+  h->live.clear();
   cudaStreamSynchronize(h->stream);
   h->cache.clear();
   if (h->d_ctrl) cudaFree(h->d_ctrl);
