@@ -42,8 +42,12 @@ enum {
   BIDIAG_ERR_CUDA = 1,        /* a CUDA runtime call failed; text in bidiag_last_error */
   BIDIAG_ERR_NOMEM = 2,       /* device or host allocation failed */
   BIDIAG_ERR_TIMEOUT = 3,     /* a device-side dependency wait ran out (see bidiag_set_option) */
-  BIDIAG_ERR_UNSUPPORTED = 4  /* valid but unsupported request, e.g. m < n */
+  BIDIAG_ERR_UNSUPPORTED = 4, /* valid but unsupported request, e.g. m < n */
+  BIDIAG_ERR_SCRATCH = 5      /* bidiag_band_noalloc: the problem needs more than its fixed scratch */
 };
+
+/* Size of the fixed device scratch array behind bidiag_band_noalloc (bytes). */
+#define BIDIAG_NOALLOC_SCRATCH_BYTES (8u << 20)
 /* Options for bidiag_set_option. */
 enum {
   BIDIAG_OPT_WAIT_LIMIT_NS = 1,   /* bound of every device-side dependency wait, ns (default 2e10) */
@@ -113,6 +117,34 @@ int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_
 int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, int64_t lda,
                      int nb, int ib, int tree, int variant, double* h_ab, int64_t ldab,
                      bidiag_result_t* out);
+
+/*
+ * The same reduction without any device allocation, for callers that may not allocate device memory:
+ * code embedded in an application whose GPU memory is wholly owned by another allocator (a framework's
+ * caching allocator that has reserved the device, say), or a service that forbids device allocation
+ * after start-up because cudaMalloc can stall the whole device and can fail at an unpredictable moment.
+ * The paper has no counterpart: this is a deployment convenience of this library.
+ *
+ * The caller passes the input d_A (m x n, column-major, lda; read only) and the output d_ab (the band in
+ * LAPACK upper-band storage, (nb+1) x n, leading dimension ldab >= nb+1), both device pointers on the
+ * current device, and a stream (NULL = legacy default stream).  Every other buffer (tile copy of A,
+ * R copy, T factors, task program, flags) lives in one array of BIDIAG_NOALLOC_SCRATCH_BYTES (8 MiB) in
+ * device global memory that the library declares statically; every GPU that loads the library holds
+ * it until the process exits.  A problem that does not fit returns BIDIAG_ERR_SCRATCH before any work
+ * is enqueued (a 512 x 512 BiDiag with nb = 64 needs about 3.3 MiB).  No cudaMalloc, cudaFree or
+ * allocating library routine is called; the task program is planned in host memory.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and keeps
+ * it; make that first call before any stream capture on the device.  All calls share the one array
+ * and each call leaves its contents behind, so calls whose work overlaps on the GPU (other threads or
+ * other streams at the same time) race and corrupt each other's results: serialise them.  The call
+ * enqueues the work, waits for the stream and returns the device-side status (BIDIAG_OK,
+ * BIDIAG_ERR_TIMEOUT, BIDIAG_ERR_CUDA).  No reflectors are kept (only the band is returned).
+ * Argument errors: -1 m, -2 n, -3 d_A, -4 lda, -5 nb, -6 ib, -7 tree, -8 variant, -9 d_ab, -10 ldab;
+ * m < n returns BIDIAG_ERR_UNSUPPORTED.
+ */
+int bidiag_band_noalloc(int64_t m, int64_t n, const double* d_A, int64_t lda, int nb, int ib, int tree,
+                        int variant, double* d_ab, int64_t ldab, void* cuda_stream);
 
 /* Band B in LAPACK upper-band storage (device): B(i, j) at ab[(nb + i - j) + j*ldab] for
  * max(0, j-nb) <= i <= j < n, ldab = nb + 1.  B is n x n (rows n..m-1 of Q^T A P are zero); every

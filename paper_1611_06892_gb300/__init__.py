@@ -22,7 +22,8 @@ FLATTS, FLATTT, GREEDY, AUTO = 0, 1, 2, 3
 TREES = {"flatts": FLATTS, "flattt": FLATTT, "greedy": GREEDY, "auto": AUTO}
 BIDIAG, RBIDIAG = 0, 1
 VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG}
-OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, 1, 2, 3, 4
+OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = 0, 1, 2, 3, 4, 5
+NOALLOC_SCRATCH_BYTES = 8 << 20
 OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING = 1, 2, 3, 4, 5
 
 _lib = None
@@ -57,6 +58,7 @@ def load_library(path=LIB_PATH):
         "bidiag_set_option": (cint, [vp, cint, i64]),
         "bidiag_band": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, P(vp)]),
         "bidiag_band_host": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, P(vp)]),
+        "bidiag_band_noalloc": (cint, [i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, vp]),
         "bidiag_result_band": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
         "bidiag_result_tasks": (cint, [vp, P(P(i32)), P(i64)]),
         "bidiag_result_reflectors": (cint, [vp, P(Reflectors)]),
@@ -106,6 +108,11 @@ def bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab, keep=
     _check(h, load_library().bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab,
                                               ctypes.byref(r) if keep else None))
     return r if keep else None
+
+
+def bidiag_band_noalloc(m, n, d_A, lda, nb, ib, tree, variant, d_ab, ldab, stream=None):
+    """Reduction that allocates no device memory (fixed static scratch); returns the status code."""
+    return load_library().bidiag_band_noalloc(m, n, d_A, lda, nb, ib, tree, variant, d_ab, ldab, stream)
 
 
 def bidiag_sync(h):
