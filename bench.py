@@ -32,6 +32,9 @@ WORKLOADS = {
     "square8192": dict(m=8192, n=8192, nb=256, ib=32, variant="bidiag", kind="sv", seeds=(2, 3),
                        desc="square FP64 8192x8192, A = U diag(s) V^T (Haar U, V; s geometric 1..1e-8), "
                             "nb=256 ib=32, BiDiag"),
+    "square4096": dict(m=4096, n=4096, nb=256, ib=32, variant="bidiag", kind="sv", seeds=(2, 3),
+                       desc="square FP64 4096x4096, A = U diag(s) V^T (Haar U, V; s geometric 1..1e-8), "
+                            "nb=256 ib=32, BiDiag"),
     "square512": dict(m=512, n=512, nb=64, ib=16, variant="bidiag", kind="gauss", seeds=(1,),
                       desc="square FP64 512x512 N(0,1), nb=64 ib=16, BiDiag"),
     "tall65536x1024": dict(m=65536, n=1024, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(4,),
@@ -286,13 +289,13 @@ def main():
         G.bidiag_band_host(h.h, m, n, A_host.data_ptr(), m, nb, ib, G.TREES[args.tree], G.VARIANTS[w["variant"]],
                            ab_host.data_ptr(), nb + 1)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device)
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device) if e2e_t else None
 
     exec_mean = statistics.mean(exec_ms)
     achieved = flops / (exec_mean * 1e-3) / 1e9
     line = dict(base, value=value, ms_per_step=ms_per_step,
-                e2e={"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": m * n * 8,
-                     "d2h_bytes_per_step": (nb + 1) * n * 8},
+                e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
+                     "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (nb + 1) * n * 8},
                 roofline={"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                           "frac": achieved / FP64_PEAK_GFLOPS, "traffic": EXEC_TRAFFIC_BYTES,
                           "kernel": "exec_kernel (persistent dataflow executor)",

@@ -55,7 +55,8 @@ enum {
   BIDIAG_OPT_DEBUG_UNSET_DEP = 3, /* 1: the next bidiag_band adds to its first task a dependency on a
                                      flag nothing sets, so that its wait runs out (failure-path test) */
   BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16 or 32, default 32) */
-  BIDIAG_OPT_TIMING = 5           /* 1: time the executor launch of each bidiag_band with CUDA events */
+  BIDIAG_OPT_TIMING = 5,          /* 1: time the executor launch of each bidiag_band with CUDA events */
+  BIDIAG_OPT_TRACE = 6            /* 1: record a per-task trace of each bidiag_band (see bidiag_trace) */
 };
 
 /* Task type codes of the canonical task list (GELQT etc. are the same codes in LQ phases). */
@@ -179,6 +180,11 @@ int bidiag_sync(bidiag_handle h);
  * enqueued with BIDIAG_OPT_TIMING on; call after bidiag_sync.  Errors: -2 ms NULL, BIDIAG_ERR_UNSUPPORTED
  * when timing was off. */
 int bidiag_last_exec_ms(bidiag_handle h, float* ms);
+
+/* Per-task trace of the last bidiag_band enqueued with BIDIAG_OPT_TRACE on (call after bidiag_sync):
+ * *count records of 4 int64 in queue order: start and end (%globaltimer ns), SM id, and the task's op
+ * word (type | orientation << 4 | strip << 8).  Copied to host `out` when cap >= *count. */
+int bidiag_trace(bidiag_handle h, int64_t* out, int64_t cap, int64_t* count);
 
 /* Text of the last failure on the handle ("" if none).  Valid until the next call on h. */
 const char* bidiag_last_error(bidiag_handle h);

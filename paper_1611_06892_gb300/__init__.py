@@ -24,7 +24,7 @@ BIDIAG, RBIDIAG = 0, 1
 VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG}
 OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = 0, 1, 2, 3, 4, 5
 NOALLOC_SCRATCH_BYTES = 8 << 20
-OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING = 1, 2, 3, 4, 5
+OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING, OPT_TRACE = 1, 2, 3, 4, 5, 6
 
 _lib = None
 
@@ -66,6 +66,7 @@ def load_library(path=LIB_PATH):
         "bidiag_apply_p": (cint, [vp, vp, cint, i64, vp, i64]),
         "bidiag_sync": (cint, [vp]),
         "bidiag_last_exec_ms": (cint, [vp, P(ctypes.c_float)]),
+        "bidiag_trace": (cint, [vp, P(i64), i64, P(i64)]),
         "bidiag_last_error": (ctypes.c_char_p, [vp]),
         "bidiag_result_free": (cint, [vp]),
         "bidiag_destroy": (cint, [vp]),
@@ -220,6 +221,16 @@ class Handle:
 
     def last_exec_ms(self):
         return bidiag_last_exec_ms(self.h)
+
+    def trace(self):
+        """Per-task trace of the last traced reduction: (ntasks x 4) int64 [start ns, end ns, SM, op]."""
+        lib = load_library()
+        cnt = ctypes.c_int64()
+        _check(self.h, lib.bidiag_trace(self.h, None, 0, ctypes.byref(cnt)))
+        out = np.zeros((cnt.value, 4), dtype=np.int64)
+        _check(self.h, lib.bidiag_trace(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cnt.value,
+                                        ctypes.byref(cnt)))
+        return out
 
     def close(self):
         if self.h:

@@ -54,6 +54,9 @@ struct bidiag_ctx {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool timed = false;
   std::set<bidiag_result*> live;   // results made on this handle and not yet freed
+  int tracing = 0;
+  int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
+  int64_t trace_cap = 0, trace_len = 0;
 };
 
 struct bidiag_result {
@@ -133,6 +136,17 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t
   prm.ib = ib;
   prm.w = w;
   prm.wait_ns = h->wait_ns;
+  prm.trace = nullptr;
+  if (timed && h->tracing) {
+    if (h->trace_cap < ntasks) {
+      if (h->d_trace) CK(h, cudaFree(h->d_trace));
+      h->d_trace = nullptr;
+      CK(h, cudaMalloc(&h->d_trace, sizeof(int64_t) * 4 * (size_t)ntasks));
+      h->trace_cap = ntasks;
+    }
+    prm.trace = h->d_trace;
+    h->trace_len = ntasks;
+  }
   CK(h, cudaMemsetAsync(pd.d_done, 0, sizeof(int) * (size_t)pd.nflags, h->stream));
   CK(h, cudaMemsetAsync(h->d_ctrl, 0, sizeof(int), h->stream));
   const int grid = std::min<int64_t>((int64_t)h->nsm * per_sm, ntasks);
@@ -359,6 +373,9 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
     case BIDIAG_OPT_TIMING:
       h->timing = value != 0;
       return BIDIAG_OK;
+    case BIDIAG_OPT_TRACE:
+      h->tracing = value != 0;
+      return BIDIAG_OK;
     default:
       return -2;
   }
@@ -418,7 +435,7 @@ int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_
     e = cudaMemsetAsync(r->tiles2, 0, (size_t)r->q * r->q * tile_elems * sizeof(double), h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
   }
-  const bool timed = h->timing != 0;
+  const bool timed = h->timing != 0 || h->tracing != 0;
   if (timed && !h->ev[0]) {
     e = cudaEventCreate(&h->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
@@ -557,6 +574,16 @@ int bidiag_last_exec_ms(bidiag_handle h, float* ms) {
   return BIDIAG_OK;
 }
 
+int bidiag_trace(bidiag_handle h, int64_t* out, int64_t cap, int64_t* count) {
+  if (!h) return -1;
+  if (!count) return -4;
+  *count = h->trace_len;
+  if (!h->d_trace || !h->trace_len) return fail(h, BIDIAG_ERR_UNSUPPORTED, "no traced reduction");
+  if (out && cap >= h->trace_len)
+    CK(h, cudaMemcpy(out, h->d_trace, sizeof(int64_t) * 4 * (size_t)h->trace_len, cudaMemcpyDeviceToHost));
+  return BIDIAG_OK;
+}
+
 const char* bidiag_last_error(bidiag_handle h) { return h ? h->err.c_str() : "null handle"; }
 
 int bidiag_result_free(bidiag_result_t r) {
@@ -583,6 +610,7 @@ int bidiag_destroy(bidiag_handle h) {
   cudaStreamSynchronize(h->stream);
   h->cache.clear();
   if (h->d_ctrl) cudaFree(h->d_ctrl);
+  if (h->d_trace) cudaFree(h->d_trace);
   if (h->ev[0]) cudaEventDestroy(h->ev[0]);
   if (h->ev[1]) cudaEventDestroy(h->ev[1]);
   delete h;

@@ -50,40 +50,55 @@ __device__ __forceinline__ uint64_t gtime() {
 }
 
 __host__ __device__ inline int odd_ld(int rows) { return rows | 1; }
+// Leading dimension of a row-major shared buffer with n columns: even, with ld/2 odd, so that the
+// 16-byte pairs of consecutive rows read by consecutive lanes fall in distinct bank groups.
+__host__ __device__ inline int rm_ld(int n) {
+  int l = n + (n & 1);
+  if (((l >> 1) & 1) == 0) l += 2;
+  return l;
+}
 
-// Shared-memory layout (offsets in doubles), identical on host and device.
+constexpr int kPanelChunk = 16;     // column chunk of the trailing update inside a panel task
+
+// Shared-memory layout (offsets in doubles, all even), identical on host and device.
 struct Layout {
-  int lp;                    // leading dimension of tile-column buffers
-  int P, Cs, Cp, Rt, Tb, G, W, W2, tau, red, total;
+  int lp, lv, lc;            // col-major panel ld; row-major V ld; row-major C / W ld
+  int P, V, Cs, Ct, Rt, Tb, G, W, W2, tau, red, total;
 };
+__host__ __device__ inline int even_up(int x) { return x + (x & 1); }
 __host__ __device__ inline Layout layout_panel(int nb, int ib) {
   Layout L{};
   L.lp = odd_ld(nb);
+  L.lv = rm_ld(ib);
+  L.lc = rm_ld(kPanelChunk);
   int o = 0;
-  L.P = o;  o += L.lp * ib;
-  L.Cs = o; o += L.lp * kChunk;
-  L.Rt = o; o += ib * (ib > kChunk ? ib : kChunk);
-  L.Tb = o; o += ib * ib;
-  L.G = o;  o += ib * ib;
-  L.W = o;  o += ib * kChunk;
-  L.W2 = o; o += ib * kChunk;
-  L.tau = o; o += ib;
+  L.P = o;   o = even_up(o + L.lp * ib);
+  L.V = o;   o = even_up(o + nb * L.lv);
+  L.Cs = o;  o = even_up(o + nb * L.lc);
+  L.Ct = o;  o = even_up(o + ib * L.lc);
+  L.Rt = o;  o = even_up(o + ib * ib);
+  L.Tb = o;  o = even_up(o + ib * ib);
+  L.G = o;   o = even_up(o + ib * ib);
+  L.W = o;   o = even_up(o + ib * L.lc);
+  L.W2 = o;  o = even_up(o + ib * L.lc);
+  L.tau = o; o = even_up(o + ib);
   L.red = o; o += 32;
-  L.Cp = -1;
   L.total = o;
   return L;
 }
 __host__ __device__ inline Layout layout_update(int nb, int ib, int w) {
   Layout L{};
   L.lp = odd_ld(nb);
+  L.lv = rm_ld(ib);
+  L.lc = rm_ld(w);
   int o = 0;
-  L.Cp = o; o += L.lp * w;
-  L.Cs = o; o += L.lp * w;
-  L.P = o;  o += L.lp * ib;   // V block
-  L.Tb = o; o += ib * ib;
-  L.W = o;  o += ib * w;
-  L.W2 = o; o += ib * w;
-  L.Rt = L.G = L.tau = L.red = -1;
+  L.Cs = o;  o = even_up(o + nb * L.lc);
+  L.Ct = o;  o = even_up(o + ib * L.lc);
+  L.V = o;   o = even_up(o + nb * L.lv);
+  L.Tb = o;  o = even_up(o + ib * ib);
+  L.W = o;   o = even_up(o + ib * L.lc);
+  L.W2 = o;  o = even_up(o + ib * L.lc);
+  L.P = L.Rt = L.G = L.tau = L.red = -1;
   L.total = o;
   return L;
 }
@@ -92,32 +107,50 @@ __device__ __forceinline__ int toff(int r, int c, int nb, int tr) { return tr ? 
 
 enum Mask : int { M_NONE = 0, M_UPPER = 1, M_UNITLOWER = 2 };
 
-// s[r + c*lds] = oriented X(r0 + r, c0 + c); M_UPPER zeroes entries below the diagonal, M_UNITLOWER
-// gives the unit lower trapezoid (1 on, 0 above the diagonal).  Coalesced in both orientations.
-__device__ void load_block(double* s, int lds, const double* g, int nb, int tr, int r0, int c0, int rows, int cols,
-                           int mask) {
-  const int n = rows * cols;
-  for (int o = threadIdx.x; o < n; o += kThreads) {
-    int r, c;
-    if (!tr) { r = o % rows; c = o / rows; } else { c = o % cols; r = o / cols; }
-    const int R = r0 + r, C = c0 + c;
-    double v;
-    if (mask == M_UPPER && R > C) v = 0.0;
-    else if (mask == M_UNITLOWER && R <= C) v = (R == C) ? 1.0 : 0.0;
-    else v = ldg(g + toff(R, C, nb, tr));
-    s[r + c * lds] = v;
+__device__ __forceinline__ double masked_ld(const double* g, int R, int C, int nb, int tr, int mask) {
+  if (mask == M_UPPER && R > C) return 0.0;
+  if (mask == M_UNITLOWER && R <= C) return (R == C) ? 1.0 : 0.0;
+  return ldg(g + toff(R, C, nb, tr));
+}
+
+// Shared element (r, c) at s[r * rs + c * cs] <- oriented X(r0 + r, c0 + c).  M_UPPER zeroes entries
+// below the diagonal, M_UNITLOWER gives the unit lower trapezoid.  Lanes run along the contiguous
+// direction of global memory (rows for tr = 0, columns for tr = 1), several loads in flight.
+__device__ void load_tile(double* s, int rs, int cs, const double* g, int nb, int tr, int r0, int c0, int rows,
+                          int cols, int mask) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!tr) {
+    for (int c = warp; c < cols; c += kWarps) {
+#pragma unroll 4
+      for (int r = lane; r < rows; r += 32) s[r * rs + c * cs] = masked_ld(g, r0 + r, c0 + c, nb, tr, mask);
+    }
+  } else {
+#pragma unroll 4
+    for (int r = warp; r < rows; r += kWarps) {
+      for (int c = lane; c < cols; c += 32) s[r * rs + c * cs] = masked_ld(g, r0 + r, c0 + c, nb, tr, mask);
+    }
   }
 }
-// Writes s back to oriented X(r0 + r, c0 + c); M_UPPER writes only entries on or above the diagonal.
-__device__ void store_block(const double* s, int lds, double* g, int nb, int tr, int r0, int c0, int rows, int cols,
-                            int mask) {
-  const int n = rows * cols;
-  for (int o = threadIdx.x; o < n; o += kThreads) {
-    int r, c;
-    if (!tr) { r = o % rows; c = o / rows; } else { c = o % cols; r = o / cols; }
-    const int R = r0 + r, C = c0 + c;
-    if (mask == M_UPPER && R > C) continue;
-    stg(g + toff(R, C, nb, tr), s[r + c * lds]);
+// Oriented X(r0 + r, c0 + c) <- s[r * rs + c * cs]; M_UPPER writes only entries on or above the diagonal.
+__device__ void store_tile(const double* s, int rs, int cs, double* g, int nb, int tr, int r0, int c0, int rows,
+                           int cols, int mask) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!tr) {
+    for (int c = warp; c < cols; c += kWarps) {
+#pragma unroll 4
+      for (int r = lane; r < rows; r += 32) {
+        if (mask == M_UPPER && r0 + r > c0 + c) continue;
+        stg(g + toff(r0 + r, c0 + c, nb, tr), s[r * rs + c * cs]);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int r = warp; r < rows; r += kWarps) {
+      for (int c = lane; c < cols; c += 32) {
+        if (mask == M_UPPER && r0 + r > c0 + c) continue;
+        stg(g + toff(r0 + r, c0 + c, nb, tr), s[r * rs + c * cs]);
+      }
+    }
   }
 }
 
@@ -232,43 +265,109 @@ __device__ void build_t(int mode, const double* P, int lp, int rows, int kb, int
   }
 }
 
-// W = op(T) (Ctop + V^T C); Ctop -= W; C -= V W.  V: vrows x kb, C: vrows x ncols, Ctop: kb x ncols or
-// null.  op(T) = T^T applies Q^T (reflectors in increasing order), op(T) = T applies Q.
-__device__ void apply_block(const double* V, int lv, int vrows, int kb, const double* Tb, int ldt, bool notrans,
-                            double* Ctop, int lct, double* C, int lc, int ncols, double* W, double* W2) {
-  for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
-    const int a = o % kb, c = o / kb;
-    double s = Ctop ? Ctop[a + c * lct] : 0.0;
-    const double* v = V + a * lv;
-    const double* cc = C + c * lc;
-    for (int r = 0; r < vrows; ++r) s += v[r] * cc[r];
-    W[o] = s;
+// Block reflector application on row-major shared operands:
+//   W = op(T) (Ct + V^T C),  Ct -= W,  C -= V W
+// V: vrows x kb (ld lv), C: vrows x ncols, Ct: kb x ncols or null, W/W2: kb x ncols (ld lc); T is kb x kb
+// column-major (ld kb).  op(T) = T^T applies Q^T (reflectors in increasing order), op(T) = T applies Q.
+// Register-blocked: phase 1 gives each thread 1 column x 4 reflectors, phase 3 1 row x 8 columns, so
+// that each DFMA needs about half a shared load.
+__device__ void apply_rm(const double* V, int lv, int vrows, int kb, const double* Tb, bool notrans, double* Ct,
+                         double* C, int lc, int ncols, double* W, double* W2) {
+  // phase 1
+  if ((kb & 3) == 0) {
+    const int nunits = ncols * (kb >> 2);
+    for (int u = threadIdx.x; u < nunits; u += kThreads) {
+      const int c = u % ncols, a0 = (u / ncols) << 2;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      if (Ct) {
+        s0 = Ct[a0 * lc + c]; s1 = Ct[(a0 + 1) * lc + c]; s2 = Ct[(a0 + 2) * lc + c]; s3 = Ct[(a0 + 3) * lc + c];
+      }
+      const double* vp = V + a0;
+      const double* cp = C + c;
+#pragma unroll 4
+      for (int r = 0; r < vrows; ++r) {
+        const double2 v01 = *reinterpret_cast<const double2*>(vp + r * lv);
+        const double2 v23 = *reinterpret_cast<const double2*>(vp + r * lv + 2);
+        const double x = cp[r * lc];
+        s0 = fma(v01.x, x, s0);
+        s1 = fma(v01.y, x, s1);
+        s2 = fma(v23.x, x, s2);
+        s3 = fma(v23.y, x, s3);
+      }
+      W[a0 * lc + c] = s0;
+      W[(a0 + 1) * lc + c] = s1;
+      W[(a0 + 2) * lc + c] = s2;
+      W[(a0 + 3) * lc + c] = s3;
+    }
+  } else {
+    for (int u = threadIdx.x; u < ncols * kb; u += kThreads) {
+      const int c = u % ncols, a = u / ncols;
+      double s = Ct ? Ct[a * lc + c] : 0.0;
+      for (int r = 0; r < vrows; ++r) s = fma(V[r * lv + a], C[r * lc + c], s);
+      W[a * lc + c] = s;
+    }
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
-    const int a = o % kb, c = o / kb;
+  // phase 2: W2 = op(T) W, then Ct -= W2
+  for (int u = threadIdx.x; u < ncols * kb; u += kThreads) {
+    const int c = u % ncols, a = u / ncols;
     double s = 0.0;
     if (!notrans) {
-      for (int t = 0; t <= a; ++t) s += Tb[t + a * ldt] * W[t + c * kb];
+      for (int t = 0; t <= a; ++t) s = fma(Tb[t + a * kb], W[t * lc + c], s);
     } else {
-      for (int t = a; t < kb; ++t) s += Tb[a + t * ldt] * W[t + c * kb];
+      for (int t = a; t < kb; ++t) s = fma(Tb[a + t * kb], W[t * lc + c], s);
     }
-    W2[o] = s;
+    W2[a * lc + c] = s;
+    if (Ct) Ct[a * lc + c] -= s;
   }
   __syncthreads();
-  if (Ctop) {
-    for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
-      const int a = o % kb, c = o / kb;
-      Ctop[a + c * lct] -= W2[o];
+  // phase 3: C -= V W2
+  if ((ncols & 7) == 0 && (kb & 1) == 0) {
+    const int nunits = vrows * (ncols >> 3);
+    for (int u = threadIdx.x; u < nunits; u += kThreads) {
+      const int r = u % vrows, c0 = (u / vrows) << 3;
+      double2* cp = reinterpret_cast<double2*>(C + r * lc + c0);
+      double2 a0 = cp[0], a1 = cp[1], a2 = cp[2], a3 = cp[3];
+      const double* vp = V + r * lv;
+#pragma unroll 2
+      for (int a = 0; a < kb; a += 2) {
+        const double2 v = *reinterpret_cast<const double2*>(vp + a);
+        const double2* w0 = reinterpret_cast<const double2*>(W2 + a * lc + c0);
+        const double2* w1 = reinterpret_cast<const double2*>(W2 + (a + 1) * lc + c0);
+        const double2 x0 = w0[0], x1 = w0[1], x2 = w0[2], x3 = w0[3];
+        const double2 y0 = w1[0], y1 = w1[1], y2 = w1[2], y3 = w1[3];
+        a0.x = fma(-v.x, x0.x, a0.x); a0.y = fma(-v.x, x0.y, a0.y);
+        a1.x = fma(-v.x, x1.x, a1.x); a1.y = fma(-v.x, x1.y, a1.y);
+        a2.x = fma(-v.x, x2.x, a2.x); a2.y = fma(-v.x, x2.y, a2.y);
+        a3.x = fma(-v.x, x3.x, a3.x); a3.y = fma(-v.x, x3.y, a3.y);
+        a0.x = fma(-v.y, y0.x, a0.x); a0.y = fma(-v.y, y0.y, a0.y);
+        a1.x = fma(-v.y, y1.x, a1.x); a1.y = fma(-v.y, y1.y, a1.y);
+        a2.x = fma(-v.y, y2.x, a2.x); a2.y = fma(-v.y, y2.y, a2.y);
+        a3.x = fma(-v.y, y3.x, a3.x); a3.y = fma(-v.y, y3.y, a3.y);
+      }
+      cp[0] = a0; cp[1] = a1; cp[2] = a2; cp[3] = a3;
+    }
+  } else {
+    for (int u = threadIdx.x; u < vrows * ncols; u += kThreads) {
+      const int r = u % vrows, c = u / vrows;
+      double s = C[r * lc + c];
+      for (int a = 0; a < kb; ++a) s = fma(-V[r * lv + a], W2[a * lc + c], s);
+      C[r * lc + c] = s;
     }
   }
-  for (int o = threadIdx.x; o < vrows * ncols; o += kThreads) {
-    const int r = o % vrows, c = o / vrows;
-    double s = 0.0;
-    for (int a = 0; a < kb; ++a) s += V[r + a * lv] * W2[a + c * kb];
-    C[r + c * lc] -= s;
-  }
   __syncthreads();
+}
+
+// Row-major V (rows x kb, ld lv) from the column-major factored panel P; GE panels get their unit
+// lower trapezoid (1 on, 0 above the diagonal), TS/TT panels are copied as they are.
+__device__ void panel_to_v(const double* P, int lp, double* V, int lv, int rows, int kb, bool unit_lower) {
+  for (int r = threadIdx.x; r < rows; r += kThreads) {
+    for (int a = 0; a < kb; ++a) {
+      double v = P[r + a * lp];
+      if (unit_lower && r <= a) v = (r == a) ? 1.0 : 0.0;
+      V[r * lv + a] = v;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -276,29 +375,24 @@ __device__ void apply_block(const double* V, int lv, int vrows, int kb, const do
 // ---------------------------------------------------------------------------------------------
 __device__ void task_geqrt(double* sm, double* X, int tr, double* Tg, int nb, int ib) {
   const Layout L = layout_panel(nb, ib);
-  double *P = sm + L.P, *Cs = sm + L.Cs, *Tb = sm + L.Tb, *G = sm + L.G, *W = sm + L.W, *W2 = sm + L.W2;
-  double *tau = sm + L.tau, *red = sm + L.red;
-  const int lp = L.lp;
+  double *P = sm + L.P, *V = sm + L.V, *Cs = sm + L.Cs, *Tb = sm + L.Tb, *G = sm + L.G, *W = sm + L.W;
+  double *W2 = sm + L.W2, *tau = sm + L.tau, *red = sm + L.red;
   for (int c0 = 0; c0 < nb; c0 += ib) {
     const int kb = ib, rows = nb - c0;
-    load_block(P, lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
+    load_tile(P, 1, L.lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
     __syncthreads();
-    factor_panel(PM_GE, P, lp, rows, kb, nullptr, 0, 0, tau, red);
-    build_t(PM_GE, P, lp, rows, kb, 0, tau, Tb, kb, G);
-    store_block(P, lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
+    factor_panel(PM_GE, P, L.lp, rows, kb, nullptr, 0, 0, tau, red);
+    build_t(PM_GE, P, L.lp, rows, kb, 0, tau, Tb, kb, G);
+    store_tile(P, 1, L.lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
     for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
+    panel_to_v(P, L.lp, V, L.lv, rows, kb, true);
     __syncthreads();
-    for (int o = threadIdx.x; o < rows * kb; o += kThreads) {   // materialize the unit lower trapezoid
-      const int r = o % rows, a = o / rows;
-      if (r <= a) P[r + a * lp] = (r == a) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int cc = c0 + kb; cc < nb; cc += kChunk) {
-      const int ncols = min(kChunk, nb - cc);
-      load_block(Cs, lp, X, nb, tr, c0, cc, rows, ncols, M_NONE);
+    for (int cc = c0 + kb; cc < nb; cc += kPanelChunk) {
+      const int ncols = min(kPanelChunk, nb - cc);
+      load_tile(Cs, L.lc, 1, X, nb, tr, c0, cc, rows, ncols, M_NONE);
       __syncthreads();
-      apply_block(P, lp, rows, kb, Tb, kb, false, nullptr, 0, Cs, lp, ncols, W, W2);
-      store_block(Cs, lp, X, nb, tr, c0, cc, rows, ncols, M_NONE);
+      apply_rm(V, L.lv, rows, kb, Tb, false, nullptr, Cs, L.lc, ncols, W, W2);
+      store_tile(Cs, L.lc, 1, X, nb, tr, c0, cc, rows, ncols, M_NONE);
       __syncthreads();
     }
   }
@@ -307,73 +401,72 @@ __device__ void task_geqrt(double* sm, double* X, int tr, double* Tg, int nb, in
 // TSQRT (tt = false) / TTQRT (tt = true): eliminate tile X under the triangle of pivot tile A.
 __device__ void task_tsqrt(double* sm, double* X, double* A, int tr, double* Tg, int nb, int ib, bool tt) {
   const Layout L = layout_panel(nb, ib);
-  double *P = sm + L.P, *Cs = sm + L.Cs, *Rt = sm + L.Rt, *Tb = sm + L.Tb, *G = sm + L.G, *W = sm + L.W;
-  double *W2 = sm + L.W2, *tau = sm + L.tau, *red = sm + L.red;
-  const int lp = L.lp;
+  double *P = sm + L.P, *V = sm + L.V, *Cs = sm + L.Cs, *Ct = sm + L.Ct, *Rt = sm + L.Rt, *Tb = sm + L.Tb;
+  double *G = sm + L.G, *W = sm + L.W, *W2 = sm + L.W2, *tau = sm + L.tau, *red = sm + L.red;
   const int mode = tt ? PM_TT : PM_TS;
   for (int c0 = 0; c0 < nb; c0 += ib) {
     const int kb = ib;
     const int vrows = tt ? c0 + kb : nb;
-    load_block(Rt, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
-    load_block(P, lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+    load_tile(Rt, 1, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
+    load_tile(P, 1, L.lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
     __syncthreads();
-    factor_panel(mode, P, lp, vrows, kb, Rt, kb, c0, tau, red);
-    build_t(mode, P, lp, vrows, kb, c0, tau, Tb, kb, G);
-    store_block(Rt, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
-    store_block(P, lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+    factor_panel(mode, P, L.lp, vrows, kb, Rt, kb, c0, tau, red);
+    build_t(mode, P, L.lp, vrows, kb, c0, tau, Tb, kb, G);
+    store_tile(Rt, 1, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
+    store_tile(P, 1, L.lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
     for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
+    panel_to_v(P, L.lp, V, L.lv, vrows, kb, false);
     __syncthreads();
-    for (int cc = c0 + kb; cc < nb; cc += kChunk) {
-      const int ncols = min(kChunk, nb - cc);
-      load_block(Rt, kb, A, nb, tr, c0, cc, kb, ncols, M_NONE);
-      load_block(Cs, lp, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
+    for (int cc = c0 + kb; cc < nb; cc += kPanelChunk) {
+      const int ncols = min(kPanelChunk, nb - cc);
+      load_tile(Ct, L.lc, 1, A, nb, tr, c0, cc, kb, ncols, M_NONE);
+      load_tile(Cs, L.lc, 1, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
       __syncthreads();
-      apply_block(P, lp, vrows, kb, Tb, kb, false, Rt, kb, Cs, lp, ncols, W, W2);
-      store_block(Rt, kb, A, nb, tr, c0, cc, kb, ncols, M_NONE);
-      store_block(Cs, lp, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
+      apply_rm(V, L.lv, vrows, kb, Tb, false, Ct, Cs, L.lc, ncols, W, W2);
+      store_tile(Ct, L.lc, 1, A, nb, tr, c0, cc, kb, ncols, M_NONE);
+      store_tile(Cs, L.lc, 1, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
       __syncthreads();
     }
   }
 }
 
-// UNMQR / TSMQR / TTMQR on one column strip [s*w, s*w + ncols) of the C tiles (oriented).
+// UNMQR / TSMQR / TTMQR on one column strip [s*w, s*w + ncols) of the C tiles (oriented).  The strip
+// of the bottom tile C stays in shared memory; the top tile Cp is touched kb rows at a time (block b
+// of the reflectors only updates rows b*ib .. b*ib + ib - 1 of it).
 __device__ void task_update(double* sm, int type, const double* X, double* Cp, double* C, int tr, bool notrans,
                             const double* Tg, int nb, int ib, int w, int s) {
   const Layout L = layout_update(nb, ib, w);
-  double *Cps = sm + L.Cp, *Cs = sm + L.Cs, *V = sm + L.P, *Tb = sm + L.Tb, *W = sm + L.W, *W2 = sm + L.W2;
-  const int lp = L.lp;
+  double *Cs = sm + L.Cs, *Ct = sm + L.Ct, *V = sm + L.V, *Tb = sm + L.Tb, *W = sm + L.W, *W2 = sm + L.W2;
   const int col0 = s * w;
   const int ncols = min(w, nb - col0);
-  load_block(Cs, lp, C, nb, tr, 0, col0, nb, ncols, M_NONE);
-  if (type != UNMQR) load_block(Cps, lp, Cp, nb, tr, 0, col0, nb, ncols, M_NONE);
+  load_tile(Cs, L.lc, 1, C, nb, tr, 0, col0, nb, ncols, M_NONE);
   const int nblk = nb / ib;
   for (int bb = 0; bb < nblk; ++bb) {
     const int b = notrans ? nblk - 1 - bb : bb;
     const int c0 = b * ib, kb = ib;
     int vrows;
-    double *Ctop, *Cb;
+    double* Cb;
+    double* Ctop = nullptr;
     if (type == UNMQR) {
       vrows = nb - c0;
-      load_block(V, lp, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
-      Ctop = nullptr;
-      Cb = Cs + c0;
-    } else if (type == TSMQR) {
-      vrows = nb;
-      load_block(V, lp, X, nb, tr, 0, c0, vrows, kb, M_NONE);
-      Ctop = Cps + c0;
-      Cb = Cs;
+      load_tile(V, L.lv, 1, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+      Cb = Cs + c0 * L.lc;
     } else {
-      vrows = c0 + kb;
-      load_block(V, lp, X, nb, tr, 0, c0, vrows, kb, M_UPPER);
-      Ctop = Cps + c0;
+      vrows = (type == TSMQR) ? nb : c0 + kb;
+      load_tile(V, L.lv, 1, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER);
+      load_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
+      Ctop = Ct;
       Cb = Cs;
     }
     for (int o = threadIdx.x; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
     __syncthreads();
-    apply_block(V, lp, vrows, kb, Tb, kb, notrans, Ctop, lp, Cb, lp, ncols, W, W2);
+    apply_rm(V, L.lv, vrows, kb, Tb, notrans, Ctop, Cb, L.lc, ncols, W, W2);
+    if (Ctop) {
+      store_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
+      __syncthreads();
+    }
   }
-  store_block(Cs, lp, C, nb, tr, 0, col0, nb, ncols, M_NONE);
-  if (type != UNMQR) store_block(Cps, lp, Cp, nb, tr, 0, col0, nb, ncols, M_NONE);
+  store_tile(Cs, L.lc, 1, C, nb, tr, 0, col0, nb, ncols, M_NONE);
 }
 
 __device__ void task_copy(const double* src, double* dst, int nb, bool diag) {
@@ -395,7 +488,7 @@ __device__ __forceinline__ double* tile_ptr(const ExecParams& prm, int32_t ref, 
 // wait (bounded) until the sub-tasks they depend on are done, run them and publish completion.
 // Taking tasks in queue order makes the scheme deadlock-free whatever the number of resident CTAs.
 __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   __shared__ int s_idx;
   __shared__ int s_abort;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -438,6 +531,8 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     __syncthreads();
     if (s_abort) break;
 
+    uint64_t t_start = 0;
+    if (prm.trace && threadIdx.x == 0) t_start = gtime();
     const int type = t.op & 15;
     const int tr = (t.op >> 4) & 1;
     const bool notrans = (t.op >> 5) & 1;
@@ -482,6 +577,15 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     if (threadIdx.x == 0) {
       __threadfence();
       st_release(prm.done + idx, 1);
+      if (prm.trace) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        int64_t* rec = prm.trace + 4 * (size_t)idx;
+        rec[0] = (int64_t)t_start;
+        rec[1] = (int64_t)gtime();
+        rec[2] = smid;
+        rec[3] = t.op;
+      }
     }
   }
 }

@@ -9,7 +9,6 @@ namespace bd {
 
 constexpr int kThreads = 256;       // threads of every executor CTA
 constexpr int kMaxNb = 256;
-constexpr int kChunk = 32;          // column chunk of the trailing update inside a panel task
 
 // Error word layout written by the executor: err[0] = code (0 ok, 1 wait ran out, 2 bad task),
 // err[1] = queue position of the failing task, err[2] = dependency it waited for.
@@ -29,6 +28,7 @@ struct ExecParams {
   int32_t npanels;
   int nb, ib, w;        // tile size, inner blocking, strip width
   uint64_t wait_ns;
+  int64_t* trace;       // optional: 4 int64 per task (start ns, end ns, SM id, op), queue order
 };
 
 // Shared memory (bytes) the executor needs for (nb, ib, w).
