@@ -152,7 +152,7 @@ def cpu_sample(path, w, tree, seconds, max_tasks=None):
     A = np.load(path, mmap_mode="r")
     variant = {"bidiag": T.BIDIAG, "rbidiag": T.RBIDIAG}[w["variant"]]
     treec = {"flatts": T.FLATTS, "flattt": T.FLATTT, "greedy": T.GREEDY, "auto": T.AUTO}[tree]
-    st = OB.new_state(np.asarray(A), w["nb"], w["ib"], treec, variant, resources=w.get("resources", 152))
+    st = OB.new_state(np.asarray(A), w["nb"], w["ib"], treec, variant, resources=w["resources"])
     units = 0
     done = 0
     t0 = time.perf_counter()
@@ -174,7 +174,7 @@ def run_cpu_sample_subprocess(A_host_np, w, tree, seconds, max_tasks=None):
         np.save(path, A_host_np)
         env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
         cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", path, "--workload", w["name"],
-               "--tree", tree, "--cpu-seconds", str(seconds)]
+               "--tree", tree, "--cpu-seconds", str(seconds), "--auto-resources", str(w["resources"])]
         if max_tasks:
             cmd += ["--cpu-max-tasks", str(max_tasks)]
         out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
@@ -196,11 +196,14 @@ def main():
     ap.add_argument("--cpu-sample", default=None)
     ap.add_argument("--cpu-seconds", type=float, default=CPU_SAMPLE_SECONDS)
     ap.add_argument("--cpu-max-tasks", type=int, default=None)
+    ap.add_argument("--auto-resources", type=int, default=None,
+                    help="R of the Auto tree (default: SMs * 32 / nb, as the library chooses)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload], name=args.workload)
     if args.workload == "square512" and args.tree == "auto":
         args.tree = "flatts"
 
+    w["resources"] = args.auto_resources
     if args.cpu_sample:
         r = cpu_sample(args.cpu_sample, w, args.tree, args.cpu_seconds, args.cpu_max_tasks)
         print(json.dumps(r))
@@ -212,10 +215,12 @@ def main():
 
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
+    if w["resources"] is None:
+        w["resources"] = max(1, torch.cuda.get_device_properties(local).multi_processor_count * 32 // w["nb"])
     m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
     flops = metric_flops(m, n)
     config = {"workload": w["desc"] + f", tree={args.tree}", "m": m, "n": n, "nb": nb, "ib": ib,
-              "tree": args.tree, "variant": w["variant"],
+              "tree": args.tree, "variant": w["variant"], "auto_resources": w["resources"],
               "l2": f"input {m * n * 8 / 2**20:.0f} MiB > 129 MB L2 (no flush needed)" if m * n * 8 > 129e6
               else "input smaller than L2"}
     base = {"metric": "GE2BND TFLOP/s (4mn^2 - 4n^3/3 flops)", "unit": "TFLOP/s", "higher_is_better": True,
@@ -252,6 +257,7 @@ def main():
     A = make_input(w, rank, device)
     h = G.Handle(device=local)
     h.set_option(G.OPT_TIMING, 1)
+    h.set_option(G.OPT_AUTO_RESOURCES, w["resources"])
     stream = h.stream
 
     def step():

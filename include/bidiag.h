@@ -51,7 +51,8 @@ enum {
 /* Options for bidiag_set_option. */
 enum {
   BIDIAG_OPT_WAIT_LIMIT_NS = 1,   /* bound of every device-side dependency wait, ns (default 2e10) */
-  BIDIAG_OPT_AUTO_RESOURCES = 2,  /* "nbcores" R of the Auto tree (default: the device's SM count) */
+  BIDIAG_OPT_AUTO_RESOURCES = 2,  /* "nbcores" R of the Auto tree (default: SMs * w / nb, the number of
+                                     tile updates that run at once when each spreads over nb / w SMs) */
   BIDIAG_OPT_DEBUG_UNSET_DEP = 3, /* 1: the next bidiag_band adds to its first task a dependency on a
                                      flag nothing sets, so that its wait runs out (failure-path test) */
   BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16 or 32, default 32) */
@@ -212,6 +213,17 @@ int bidiag_plan_eliminations(int64_t p, int64_t q, int tree, int variant, int64_
  * Table 1 units (GEQRT 4, UNMQR 6, TSQRT 6, TSMQR 12, TTQRT 2, TTMQR 6, COPY 0) in *cp when cp != NULL. */
 int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resources,
                       int32_t* tasks, int32_t* level, int64_t cap, int64_t* count, int64_t* cp);
+
+/* The device program the executor runs for a reduction (host-only, for validation): *count sub-tasks
+ * of 8 int32 in queue order (op word: type | orientation << 4 | Q-instead-of-Q^T << 5 | strip << 8 |
+ * inner block << 16 | panel kind << 24; V/panel tile, pivot/top tile, C tile references (buffer << 28 |
+ * tile index); T slot; first and one-past-last dependency; flags) and *ndeps dependency entries
+ * (queue positions).  Sub-task types: 1, 3, 5 = update strips (UNMQR, TSMQR, TTMQR), 6 = COPY,
+ * 7 = factor one inner block of a panel, 8 = apply it to a later column block of the panel.
+ * *strip_w receives the update strip width.  Arrays are filled when their capacities suffice. */
+int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
+                        int strip_w, int32_t* program, int64_t cap, int64_t* count, int32_t* deps,
+                        int64_t dcap, int64_t* ndeps, int32_t* strip_w_used);
 
 #ifdef __cplusplus
 }

@@ -72,6 +72,8 @@ def load_library(path=LIB_PATH):
         "bidiag_destroy": (cint, [vp]),
         "bidiag_plan_eliminations": (cint, [i64, i64, cint, cint, i64, P(i32), i64, P(i64)]),
         "bidiag_plan_tasks": (cint, [i64, i64, cint, cint, i64, P(i32), P(i32), i64, P(i64), P(i64)]),
+        "bidiag_plan_program": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), i64, P(i64), P(i32),
+                                       i64, P(i64), P(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -165,6 +167,22 @@ def bidiag_plan_tasks(p, q, tree, variant, resources=1):
     _check(None, lib.bidiag_plan_tasks(p, q, tree, variant, resources, tasks.ctypes.data_as(I32),
                                        lv.ctypes.data_as(I32), cnt.value, ctypes.byref(cnt), ctypes.byref(cp)))
     return tasks[:cnt.value], lv[:cnt.value], cp.value
+
+
+def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
+    """Device program of a reduction: (sub-tasks (count x 8) int32, dependency array, strip width)."""
+    lib = load_library()
+    cnt, nd = ctypes.c_int64(), ctypes.c_int64()
+    w = ctypes.c_int32()
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    _check(None, lib.bidiag_plan_program(m, n, nb, ib, tree, variant, resources, strip_w, None, 0, ctypes.byref(cnt),
+                                         None, 0, ctypes.byref(nd), ctypes.byref(w)))
+    prog = np.zeros((max(cnt.value, 1), 8), dtype=np.int32)
+    deps = np.zeros(max(nd.value, 1), dtype=np.int32)
+    _check(None, lib.bidiag_plan_program(m, n, nb, ib, tree, variant, resources, strip_w, prog.ctypes.data_as(I32),
+                                         cnt.value, ctypes.byref(cnt), deps.ctypes.data_as(I32), nd.value,
+                                         ctypes.byref(nd), ctypes.byref(w)))
+    return prog[:cnt.value], deps[:nd.value], w.value
 
 
 # ---- torch-facing wrappers ---------------------------------------------------------------------

@@ -110,7 +110,13 @@ int upload_program(bidiag_handle h, PlanDev& pd, const std::vector<bd::DevTask>&
   return BIDIAG_OK;
 }
 
-int64_t resources_of(bidiag_handle h) { return h->auto_res > 0 ? h->auto_res : h->nsm; }
+// Resources R of the Auto tree (Sec. 5 "nbcores"): the number of workers that each take one tile
+// task.  A tile update is spread over nb / w SMs (one column strip each), so the default is
+// SMs * w / nb; BIDIAG_OPT_AUTO_RESOURCES overrides it.
+int64_t resources_of(bidiag_handle h, int nb, int w) {
+  if (h->auto_res > 0) return h->auto_res;
+  return std::max<int64_t>(1, (int64_t)h->nsm * w / nb);
+}
 
 // Executor launch of a program held in pd with the given buffers.
 int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t n0, double* b1, int64_t n1, double* b2,
@@ -157,20 +163,14 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t
 }
 
 int choose_strip(bidiag_handle h, int nb, int ib, int* w) {
-  int cand[2] = {h->strip_w, 16};
-  for (int c : cand) {
-    const int ww = std::min(c, nb);
-    if (bd::exec_smem_bytes(nb, ib, ww) <= h->smem_optin) {
-      *w = ww;
-      return BIDIAG_OK;
-    }
-  }
+  *w = bd::choose_strip_width(nb, ib, h->strip_w, h->smem_optin);
+  if (*w) return BIDIAG_OK;
   return fail(h, BIDIAG_ERR_UNSUPPORTED, "tile size / inner blocking need more shared memory than the device has");
 }
 
 int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int w,
              std::shared_ptr<PlanDev>* out) {
-  const int64_t R = resources_of(h);
+  const int64_t R = resources_of(h, nb, w);
   const bool debug = h->debug_unset != 0;
   PlanKey key{m, n, nb, ib, tree, variant, R, w};
   if (!debug) {
@@ -662,6 +662,33 @@ int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resou
     }
   } catch (...) {
     return BIDIAG_ERR_NOMEM;
+  }
+  return BIDIAG_OK;
+}
+
+int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources, int strip_w,
+                        int32_t* program, int64_t cap, int64_t* count, int32_t* deps, int64_t dcap, int64_t* ndeps,
+                        int32_t* strip_w_used) {
+  if (m < 1 || n < 1 || m < n) return -1;
+  if (nb < 1 || nb > bd::kMaxNb) return -3;
+  if (ib < 1 || nb % ib) return -4;
+  if (tree < 0 || tree > 3) return -5;
+  if (variant < 0 || variant > 1) return -6;
+  if (!count || !ndeps) return -9;
+  int w = std::max(ib, (strip_w / ib) * ib);
+  w = std::min(w, nb);
+  try {
+    bd::Plan pl;
+    bd::build_plan(pl, m, n, nb, ib, tree, variant, resources, w);
+    *count = (int64_t)pl.dev.size();
+    *ndeps = (int64_t)pl.deps.size();
+    if (strip_w_used) *strip_w_used = pl.strip_w;
+    if (program && cap >= *count) std::memcpy(program, pl.dev.data(), pl.dev.size() * sizeof(bd::DevTask));
+    if (deps && dcap >= *ndeps) std::memcpy(deps, pl.deps.data(), pl.deps.size() * sizeof(int32_t));
+  } catch (const std::bad_alloc&) {
+    return BIDIAG_ERR_NOMEM;
+  } catch (...) {
+    return BIDIAG_ERR_UNSUPPORTED;
   }
   return BIDIAG_OK;
 }

@@ -58,8 +58,6 @@ __host__ __device__ inline int rm_ld(int n) {
   return l;
 }
 
-constexpr int kPanelChunk = 16;     // column chunk of the trailing update inside a panel task
-
 // Shared-memory layout (offsets in doubles, all even), identical on host and device.
 struct Layout {
   int lp, lv, lc;            // col-major panel ld; row-major V ld; row-major C / W ld
@@ -69,20 +67,15 @@ __host__ __device__ inline int even_up(int x) { return x + (x & 1); }
 __host__ __device__ inline Layout layout_panel(int nb, int ib) {
   Layout L{};
   L.lp = odd_ld(nb);
-  L.lv = rm_ld(ib);
-  L.lc = rm_ld(kPanelChunk);
+  L.lv = L.lc = 0;
   int o = 0;
   L.P = o;   o = even_up(o + L.lp * ib);
-  L.V = o;   o = even_up(o + nb * L.lv);
-  L.Cs = o;  o = even_up(o + nb * L.lc);
-  L.Ct = o;  o = even_up(o + ib * L.lc);
   L.Rt = o;  o = even_up(o + ib * ib);
   L.Tb = o;  o = even_up(o + ib * ib);
   L.G = o;   o = even_up(o + ib * ib);
-  L.W = o;   o = even_up(o + ib * L.lc);
-  L.W2 = o;  o = even_up(o + ib * L.lc);
   L.tau = o; o = even_up(o + ib);
   L.red = o; o += 32;
+  L.V = L.Cs = L.Ct = L.W = L.W2 = -1;
   L.total = o;
   return L;
 }
@@ -358,91 +351,54 @@ __device__ void apply_rm(const double* V, int lv, int vrows, int kb, const doubl
   __syncthreads();
 }
 
-// Row-major V (rows x kb, ld lv) from the column-major factored panel P; GE panels get their unit
-// lower trapezoid (1 on, 0 above the diagonal), TS/TT panels are copied as they are.
-__device__ void panel_to_v(const double* P, int lp, double* V, int lv, int rows, int kb, bool unit_lower) {
-  for (int r = threadIdx.x; r < rows; r += kThreads) {
-    for (int a = 0; a < kb; ++a) {
-      double v = P[r + a * lp];
-      if (unit_lower && r <= a) v = (r == a) ? 1.0 : 0.0;
-      V[r * lv + a] = v;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
-// Panel tasks
+// Panel factor sub-task PF(b): factors inner block b (columns b*ib .. b*ib + ib - 1) of a panel task
+// and writes its reflectors in place and its T block.  GE: rows b*ib .. nb-1 of tile X.  TS: the
+// triangle of pivot tile A's diagonal block b over all rows of X.  TT: the same triangle over the upper
+// part of X (rows 0 .. b*ib + ib - 1).  The later column blocks are updated by PU sub-tasks.
 // ---------------------------------------------------------------------------------------------
-__device__ void task_geqrt(double* sm, double* X, int tr, double* Tg, int nb, int ib) {
+__device__ void task_panel_factor(double* sm, int kind, double* X, double* A, int tr, double* Tg, int nb, int ib,
+                                  int b) {
   const Layout L = layout_panel(nb, ib);
-  double *P = sm + L.P, *V = sm + L.V, *Cs = sm + L.Cs, *Tb = sm + L.Tb, *G = sm + L.G, *W = sm + L.W;
-  double *W2 = sm + L.W2, *tau = sm + L.tau, *red = sm + L.red;
-  for (int c0 = 0; c0 < nb; c0 += ib) {
-    const int kb = ib, rows = nb - c0;
+  double *P = sm + L.P, *Rt = sm + L.Rt, *Tb = sm + L.Tb, *G = sm + L.G, *tau = sm + L.tau, *red = sm + L.red;
+  const int c0 = b * ib, kb = ib;
+  if (kind == PM_GE) {
+    const int rows = nb - c0;
     load_tile(P, 1, L.lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
     __syncthreads();
     factor_panel(PM_GE, P, L.lp, rows, kb, nullptr, 0, 0, tau, red);
     build_t(PM_GE, P, L.lp, rows, kb, 0, tau, Tb, kb, G);
     store_tile(P, 1, L.lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
-    for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
-    panel_to_v(P, L.lp, V, L.lv, rows, kb, true);
-    __syncthreads();
-    for (int cc = c0 + kb; cc < nb; cc += kPanelChunk) {
-      const int ncols = min(kPanelChunk, nb - cc);
-      load_tile(Cs, L.lc, 1, X, nb, tr, c0, cc, rows, ncols, M_NONE);
-      __syncthreads();
-      apply_rm(V, L.lv, rows, kb, Tb, false, nullptr, Cs, L.lc, ncols, W, W2);
-      store_tile(Cs, L.lc, 1, X, nb, tr, c0, cc, rows, ncols, M_NONE);
-      __syncthreads();
-    }
-  }
-}
-
-// TSQRT (tt = false) / TTQRT (tt = true): eliminate tile X under the triangle of pivot tile A.
-__device__ void task_tsqrt(double* sm, double* X, double* A, int tr, double* Tg, int nb, int ib, bool tt) {
-  const Layout L = layout_panel(nb, ib);
-  double *P = sm + L.P, *V = sm + L.V, *Cs = sm + L.Cs, *Ct = sm + L.Ct, *Rt = sm + L.Rt, *Tb = sm + L.Tb;
-  double *G = sm + L.G, *W = sm + L.W, *W2 = sm + L.W2, *tau = sm + L.tau, *red = sm + L.red;
-  const int mode = tt ? PM_TT : PM_TS;
-  for (int c0 = 0; c0 < nb; c0 += ib) {
-    const int kb = ib;
+  } else {
+    const bool tt = kind == PM_TT;
     const int vrows = tt ? c0 + kb : nb;
     load_tile(Rt, 1, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
     load_tile(P, 1, L.lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
     __syncthreads();
-    factor_panel(mode, P, L.lp, vrows, kb, Rt, kb, c0, tau, red);
-    build_t(mode, P, L.lp, vrows, kb, c0, tau, Tb, kb, G);
+    factor_panel(kind, P, L.lp, vrows, kb, Rt, kb, c0, tau, red);
+    build_t(kind, P, L.lp, vrows, kb, c0, tau, Tb, kb, G);
     store_tile(Rt, 1, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
     store_tile(P, 1, L.lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
-    for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
-    panel_to_v(P, L.lp, V, L.lv, vrows, kb, false);
-    __syncthreads();
-    for (int cc = c0 + kb; cc < nb; cc += kPanelChunk) {
-      const int ncols = min(kPanelChunk, nb - cc);
-      load_tile(Ct, L.lc, 1, A, nb, tr, c0, cc, kb, ncols, M_NONE);
-      load_tile(Cs, L.lc, 1, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
-      __syncthreads();
-      apply_rm(V, L.lv, vrows, kb, Tb, false, Ct, Cs, L.lc, ncols, W, W2);
-      store_tile(Ct, L.lc, 1, A, nb, tr, c0, cc, kb, ncols, M_NONE);
-      store_tile(Cs, L.lc, 1, X, nb, tr, 0, cc, vrows, ncols, M_NONE);
-      __syncthreads();
-    }
   }
+  for (int o = threadIdx.x; o < kb * kb; o += kThreads) stg(Tg + (size_t)c0 * ib + o, Tb[o]);
 }
 
-// UNMQR / TSMQR / TTMQR on one column strip [s*w, s*w + ncols) of the C tiles (oriented).  The strip
-// of the bottom tile C stays in shared memory; the top tile Cp is touched kb rows at a time (block b
-// of the reflectors only updates rows b*ib .. b*ib + ib - 1 of it).
+// Applies reflector blocks [blk0, blk1) of V tile X (UNMQR: GEQRT reflectors; TSMQR: TSQRT reflectors
+// over [Cp; C]; TTMQR: TTQRT reflectors) to columns [col0, col0 + ncols) of the C tiles (oriented), in
+// increasing block order for Q^T and decreasing for Q.  Only the rows the blocks touch are loaded and
+// written: rows blk0*ib .. nb-1 of C (UNMQR), all rows of C (TSMQR), rows 0 .. blk1*ib - 1 of C
+// (TTMQR), and rows b*ib .. b*ib + ib - 1 of Cp for each block b.  The C rows stay in shared memory.
+// With blk0 = b, blk1 = b + 1 and C = X this is the PU(b, s) sub-task of a panel.
 __device__ void task_update(double* sm, int type, const double* X, double* Cp, double* C, int tr, bool notrans,
-                            const double* Tg, int nb, int ib, int w, int s) {
+                            const double* Tg, int nb, int ib, int w, int blk0, int blk1, int col0, int ncols) {
   const Layout L = layout_update(nb, ib, w);
   double *Cs = sm + L.Cs, *Ct = sm + L.Ct, *V = sm + L.V, *Tb = sm + L.Tb, *W = sm + L.W, *W2 = sm + L.W2;
-  const int col0 = s * w;
-  const int ncols = min(w, nb - col0);
-  load_tile(Cs, L.lc, 1, C, nb, tr, 0, col0, nb, ncols, M_NONE);
-  const int nblk = nb / ib;
-  for (int bb = 0; bb < nblk; ++bb) {
-    const int b = notrans ? nblk - 1 - bb : bb;
+  const int row_lo = (type == UNMQR) ? blk0 * ib : 0;
+  const int row_hi = (type == TTMQR) ? blk1 * ib : nb;
+  load_tile(Cs + row_lo * L.lc, L.lc, 1, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
+  const int nbk = blk1 - blk0;
+  for (int bb = 0; bb < nbk; ++bb) {
+    const int b = notrans ? blk1 - 1 - bb : blk0 + bb;
     const int c0 = b * ib, kb = ib;
     int vrows;
     double* Cb;
@@ -466,7 +422,7 @@ __device__ void task_update(double* sm, int type, const double* X, double* Cp, d
       __syncthreads();
     }
   }
-  store_tile(Cs, L.lc, 1, C, nb, tr, 0, col0, nb, ncols, M_NONE);
+  store_tile(Cs + row_lo * L.lc, L.lc, 1, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
 }
 
 __device__ void task_copy(const double* src, double* dst, int nb, bool diag) {
@@ -536,18 +492,28 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     const int type = t.op & 15;
     const int tr = (t.op >> 4) & 1;
     const bool notrans = (t.op >> 5) & 1;
-    const int strip = (t.op >> 8) & 0xffff;
+    const int strip = (t.op >> 8) & 0xff;
+    const int blk = (t.op >> 16) & 0xff;
+    const int kind = (t.op >> 24) & 3;
+    const int nblk = prm.nb / prm.ib;
     bool ok = true;
     double* X = tile_ptr(prm, t.x, ok);
     double* Tg = (t.tslot >= 0 && t.tslot < prm.npanels) ? prm.T + (size_t)t.tslot * prm.ib * prm.nb : nullptr;
     switch (type) {
-      case GEQRT:
-        if (ok && Tg) task_geqrt(sm, X, tr, Tg, prm.nb, prm.ib); else ok = false;
+      case PF: {
+        double* A = (kind == PM_GE) ? nullptr : tile_ptr(prm, t.a, ok);
+        if (ok && Tg && blk < nblk && kind <= PM_TT) task_panel_factor(sm, kind, X, A, tr, Tg, prm.nb, prm.ib, blk);
+        else ok = false;
         break;
-      case TSQRT:
-      case TTQRT: {
-        double* A = tile_ptr(prm, t.a, ok);
-        if (ok && Tg) task_tsqrt(sm, X, A, tr, Tg, prm.nb, prm.ib, type == TTQRT); else ok = false;
+      }
+      case PU: {
+        double* A = (kind == PM_GE) ? nullptr : tile_ptr(prm, t.a, ok);
+        const int utype = kind == PM_GE ? UNMQR : (kind == PM_TS ? TSMQR : TTMQR);
+        if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT)
+          task_update(sm, utype, X, A, X, tr, false, Tg, prm.nb, prm.ib, prm.w, blk, blk + 1, strip * prm.ib,
+                      prm.ib);
+        else
+          ok = false;
         break;
       }
       case UNMQR:
@@ -555,8 +521,10 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       case TTMQR: {
         double* A = (type == UNMQR) ? nullptr : tile_ptr(prm, t.a, ok);
         double* C = tile_ptr(prm, t.c, ok);
-        if (ok && Tg && strip * prm.w < prm.nb)
-          task_update(sm, type, X, A, C, tr, notrans, Tg, prm.nb, prm.ib, prm.w, strip);
+        const int col0 = strip * prm.w;
+        if (ok && Tg && col0 < prm.nb)
+          task_update(sm, type, X, A, C, tr, notrans, Tg, prm.nb, prm.ib, prm.w, 0, nblk, col0,
+                      min(prm.w, prm.nb - col0));
         else
           ok = false;
         break;
@@ -635,6 +603,16 @@ __global__ void extract_kernel(const double* __restrict__ tiles, int64_t rows_t,
 size_t exec_smem_bytes(int nb, int ib, int w) {
   const Layout a = layout_panel(nb, ib), b = layout_update(nb, ib, w);
   return sizeof(double) * (size_t)(a.total > b.total ? a.total : b.total);
+}
+
+int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit) {
+  for (int want = preferred; want >= 1; want /= 2) {
+    int w = want < ib ? ib : (want / ib) * ib;
+    if (w > nb) w = nb;
+    if (exec_smem_bytes(nb, ib, w) <= smem_limit) return w;
+    if (w == ib) break;
+  }
+  return 0;
 }
 
 cudaError_t exec_set_smem(size_t smem) {

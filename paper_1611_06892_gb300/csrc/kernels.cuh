@@ -33,6 +33,9 @@ struct ExecParams {
 
 // Shared memory (bytes) the executor needs for (nb, ib, w).
 size_t exec_smem_bytes(int nb, int ib, int w);
+// Column-strip width of the update sub-tasks: a multiple of ib, at most nb, as close to `preferred`
+// as the shared-memory limit allows; 0 if even w = ib does not fit.
+int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit);
 
 cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st);
 cudaError_t exec_set_smem(size_t smem);

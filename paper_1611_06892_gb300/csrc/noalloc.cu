@@ -8,6 +8,7 @@
 // up the array's device address with cudaGetSymbolAddress (with that device current) and keeps it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <mutex>
 #include <new>
@@ -67,16 +68,15 @@ extern "C" int bidiag_band_noalloc(int64_t m, int64_t n, const double* d_A, int6
   if (e != cudaSuccess) return BIDIAG_ERR_CUDA;
   if (dev >= kMaxDevices) return BIDIAG_ERR_UNSUPPORTED;
 
-  int w = nb < 32 ? nb : 32;
-  if (bd::exec_smem_bytes(nb, ib, w) > (size_t)optin - 64) w = nb < 16 ? nb : 16;
+  const int w = bd::choose_strip_width(nb, ib, 32, (size_t)optin - 64);
+  if (!w) return BIDIAG_ERR_UNSUPPORTED;
   const size_t smem = bd::exec_smem_bytes(nb, ib, w);
-  if (smem > (size_t)optin - 64) return BIDIAG_ERR_UNSUPPORTED;
 
   // The task program is planned on the host (host memory only).
   bd::Plan pl;
   try {
     const char* env = std::getenv("BIDIAG_AUTO_RES");
-    const int64_t R = env && std::atoll(env) > 0 ? std::atoll(env) : nsm;
+    const int64_t R = env && std::atoll(env) > 0 ? std::atoll(env) : std::max<int64_t>(1, (int64_t)nsm * w / nb);
     bd::build_plan(pl, m, n, nb, ib, tree, variant, R, w);
   } catch (const std::bad_alloc&) {
     return BIDIAG_ERR_NOMEM;

@@ -363,12 +363,101 @@ void make_dag(const std::vector<Task>& tasks, int p, int q, int variant, std::ve
 }
 
 // ---------------------------------------------------------------------------------------------
-// Device program: every update task is split into `nstrips` column strips of its C tiles (columns
-// in the step's orientation); panel and COPY tasks are one sub-task each.  A strip of an update
-// depends only on the same strip of a preceding update of the same orientation; any other
-// dependency is on every sub-task of the predecessor.  Sub-tasks are ordered by decreasing bottom
-// level (longest weighted path to the end), which is a topological order since weights are > 0.
+// Device program.
+//  * A panel task (GEQRT / TSQRT / TTQRT) becomes, for each inner block b of ib reflectors, a factor
+//    sub-task PF(b) on column block b, followed by update sub-tasks PU(b, s) that apply block b to the
+//    later column blocks s of the panel (and of the pivot's top rows for TS / TT).  Block b + 1 can be
+//    factored as soon as PU(b, b + 1) is done (look-ahead inside the tile), and consecutive eliminations
+//    into the same pivot overlap block by block.
+//  * An update task (UNMQR / TSMQR / TTMQR) becomes one sub-task per column strip of w columns (w a
+//    multiple of ib) of its C tiles.
+// Dependencies come from the data each sub-task reads and writes, tracked per ib x ib block of every
+// tile (a diagonal block is split into its strict upper part, diagonal and strict lower part) and per
+// T block: read-after-write, write-after-write and write-after-read.  An update strip depends on the
+// last sub-task of its panel task for the reflectors it applies (the panel's sub-tasks are chained, and
+// a factored region is never written again).  Sub-tasks are queued by decreasing bottom level (longest
+// weighted path to the end), a topological order since every weight is positive.
 // ---------------------------------------------------------------------------------------------
+namespace {
+
+struct Items {
+  int p = 0, q = 0, nblk = 0;
+  int64_t per_tile = 0, tbase = 0;
+  int64_t tile(int buf, int x, int y) const { return (((int64_t)buf * q + y) * p + x) * per_tile; }
+  int64_t blk(int buf, int x, int y, int bi, int bj) const { return tile(buf, x, y) + (int64_t)bi * nblk + bj; }
+  int64_t dsu(int buf, int x, int y, int b) const { return tile(buf, x, y) + (int64_t)nblk * nblk + 2 * b; }
+  int64_t dsl(int buf, int x, int y, int b) const { return dsu(buf, x, y, b) + 1; }
+  int64_t t(int slot, int b) const { return tbase + (int64_t)slot * nblk + b; }
+  int64_t size(int npanels) const { return tbase + (int64_t)npanels * nblk; }
+};
+
+// Item sets of an oriented tile (oa, ob) of buffer `buf` in a step of orientation lq.
+struct OTile {
+  const Items* it;
+  int buf, x, y;
+  bool lq;
+  OTile(const Items* i, int b, int oa, int ob, bool l) : it(i), buf(b), x(l ? ob : oa), y(l ? oa : ob), lq(l) {}
+  void full(std::vector<int64_t>& v, int br, int bc) const {
+    if (br != bc) {
+      v.push_back(lq ? it->blk(buf, x, y, bc, br) : it->blk(buf, x, y, br, bc));
+    } else {
+      v.push_back(it->blk(buf, x, y, br, br));
+      v.push_back(it->dsu(buf, x, y, br));
+      v.push_back(it->dsl(buf, x, y, br));
+    }
+  }
+  void up(std::vector<int64_t>& v, int b) const {   // oriented diagonal + strict upper of block (b, b)
+    v.push_back(it->blk(buf, x, y, b, b));
+    v.push_back(lq ? it->dsl(buf, x, y, b) : it->dsu(buf, x, y, b));
+  }
+  void lo(std::vector<int64_t>& v, int b) const {   // oriented strict lower of block (b, b)
+    v.push_back(lq ? it->dsu(buf, x, y, b) : it->dsl(buf, x, y, b));
+  }
+};
+
+enum PanelKind : int { PK_GE = 0, PK_TS = 1, PK_TT = 2 };
+
+struct SubDag {
+  std::vector<int32_t> last_w;
+  std::vector<std::vector<int32_t>> readers;
+  std::vector<DevTask> sub;
+  std::vector<int64_t> weight;
+  std::vector<std::vector<int32_t>> deps;
+  std::vector<int32_t> tmp;
+
+  explicit SubDag(int64_t nitems) : last_w(nitems, -1), readers(nitems) {}
+
+  int32_t add(const DevTask& d, int64_t w, const std::vector<int64_t>& rd, const std::vector<int64_t>& wr,
+              int32_t extra_dep) {
+    const int32_t me = (int32_t)sub.size();
+    tmp.clear();
+    for (int64_t i : rd)
+      if (last_w[i] >= 0) tmp.push_back(last_w[i]);
+    for (int64_t i : wr) {
+      if (last_w[i] >= 0) tmp.push_back(last_w[i]);
+      for (int32_t r : readers[i]) tmp.push_back(r);
+    }
+    if (extra_dep >= 0) tmp.push_back(extra_dep);
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    for (int64_t i : rd) readers[i].push_back(me);
+    for (int64_t i : wr) {
+      last_w[i] = me;
+      readers[i].clear();
+    }
+    sub.push_back(d);
+    weight.push_back(w > 0 ? w : 1);
+    deps.push_back(tmp);
+    return me;
+  }
+};
+
+inline int32_t make_op(int type, bool tr, bool notrans, int strip, int blk, int kind) {
+  return type | ((tr ? 1 : 0) << 4) | ((notrans ? 1 : 0) << 5) | (strip << 8) | (blk << 16) | (kind << 24);
+}
+
+}  // namespace
+
 void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t R, int strip_w) {
   pl.m = m;
   pl.n = n;
@@ -381,21 +470,18 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
   pl.q = (int)((n + nb - 1) / nb);
   pl.strip_w = std::min(strip_w, nb);
   pl.nstrips = (nb + pl.strip_w - 1) / pl.strip_w;
-  const int p = pl.p, q = pl.q, S = pl.nstrips;
+  if (pl.strip_w % ib) throw std::invalid_argument("strip width must be a multiple of ib");
+  const int p = pl.p, q = pl.q, S = pl.nstrips, w = pl.strip_w, nblk = nb / ib;
+  if (S > 255 || nblk > 255) throw std::invalid_argument("too many strips or inner blocks");
   pl.elims = make_eliminations(p, q, tree, variant, R);
   pl.tasks = make_tasks(p, q, tree, variant, R);
-  std::vector<std::vector<int32_t>> preds;
-  make_dag(pl.tasks, p, q, variant, &preds, &pl.level, &pl.critical_path);
+  make_dag(pl.tasks, p, q, variant, nullptr, &pl.level, &pl.critical_path);
   const size_t nt = pl.tasks.size();
 
-  // T slots and owners
+  // T slots and the panel task whose reflectors each update applies
   pl.tslot.assign(nt, -1);
   pl.owner.assign(nt, -1);
   pl.npanels = 0;
-  for (size_t x = 0; x < nt; ++x) {
-    const int ty = pl.tasks[x].type;
-    if (ty == GEQRT || ty == TSQRT || ty == TTQRT) pl.tslot[x] = pl.npanels++;
-  }
   {
     std::vector<int32_t> lastp((size_t)3 * 3 * (q + 1) * (p + 1), -1);
     auto key = [&](int ptype, int phase, int k, int i) {
@@ -403,6 +489,7 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
     };
     for (size_t x = 0; x < nt; ++x) {
       const Task& t = pl.tasks[x];
+      if (t.type == GEQRT || t.type == TSQRT || t.type == TTQRT) pl.tslot[x] = pl.npanels++;
       if (t.type == GEQRT) lastp[key(0, t.phase, t.k, t.i)] = (int32_t)x;
       if (t.type == TSQRT) lastp[key(1, t.phase, t.k, t.i)] = (int32_t)x;
       if (t.type == TTQRT) lastp[key(2, t.phase, t.k, t.i)] = (int32_t)x;
@@ -412,81 +499,133 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
     }
   }
 
-  // sub-tasks in program order
-  auto is_update = [](int ty) { return ty == UNMQR || ty == TSMQR || ty == TTMQR; };
-  std::vector<int32_t> first(nt + 1, 0);
-  for (size_t x = 0; x < nt; ++x) first[x + 1] = first[x] + (is_update(pl.tasks[x].type) ? S : 1);
-  const int32_t nsub = first[nt];
-  std::vector<DevTask> sub(nsub);
-  std::vector<int64_t> wsub(nsub);
-  std::vector<std::vector<int32_t>> sdeps(nsub);
-  auto tref = [&](int buf, int a, int b, bool lq) {
-    // actual tile of oriented (a, b)
-    const int x = lq ? b : a, y = lq ? a : b;
+  Items it;
+  it.p = p;
+  it.q = q;
+  it.nblk = nblk;
+  it.per_tile = (int64_t)nblk * nblk + 2 * nblk;
+  it.tbase = 2 * (int64_t)q * p * it.per_tile;
+  SubDag g(it.size(pl.npanels));
+  std::vector<int32_t> panel_last(nt, -1);   // last sub-task of each panel task
+  std::vector<int64_t> rd, wr;
+  const int64_t ib2 = (int64_t)ib * ib;
+
+  auto tref = [&](int buf, int oa, int ob, bool lq) {
+    const int x = lq ? ob : oa, y = lq ? oa : ob;
     const int rows = buf == 0 ? p : q;
     return tile_ref(buf, (int64_t)y * rows + x);
   };
+
   for (size_t x = 0; x < nt; ++x) {
     const Task& t = pl.tasks[x];
     const int buf = (variant == V_RBIDIAG && t.phase != PH_PQR) ? 1 : 0;
     const bool lq = t.phase == PH_LQ;
-    DevTask d{};
-    d.op = t.type | ((lq ? 1 : 0) << 4);
-    d.x = d.a = d.c = -1;
-    d.tslot = -1;
-    d.flags = 0;
-    switch (t.type) {
-      case GEQRT: d.x = tref(buf, t.i, t.k, lq); d.tslot = pl.tslot[x]; break;
-      case TSQRT:
-      case TTQRT:
-        d.x = tref(buf, t.i, t.k, lq);
-        d.a = tref(buf, t.piv, t.k, lq);
-        d.tslot = pl.tslot[x];
-        break;
-      case UNMQR:
-        d.x = tref(buf, t.i, t.k, lq);
-        d.c = tref(buf, t.i, t.j, lq);
-        d.tslot = pl.tslot[pl.owner[x]];
-        break;
-      case TSMQR:
-      case TTMQR:
-        d.x = tref(buf, t.i, t.k, lq);
-        d.a = tref(buf, t.piv, t.j, lq);
-        d.c = tref(buf, t.i, t.j, lq);
-        d.tslot = pl.tslot[pl.owner[x]];
-        break;
-      case COPY:
-        d.x = tile_ref(0, (int64_t)t.j * p + t.i);
-        d.c = tile_ref(1, (int64_t)t.j * q + t.i);
-        d.flags = t.i == t.j ? 1 : 0;
-        break;
-    }
-    const int ns = first[x + 1] - first[x];
-    for (int s = 0; s < ns; ++s) {
-      DevTask e = d;
-      e.op |= (s << 8);
-      sub[first[x] + s] = e;
-      wsub[first[x] + s] = is_update(t.type) ? kWeight[t.type] : (t.type == COPY ? 1 : (int64_t)kWeight[t.type] * S);
-    }
-    for (int32_t pd : preds[x]) {
-      if (pd == (int32_t)x) continue;
-      const Task& u = pl.tasks[pd];
-      const bool strip_wise = is_update(t.type) && is_update(u.type) && (u.phase == PH_LQ) == lq &&
-                              ((variant == V_RBIDIAG && u.phase != PH_PQR) ? 1 : 0) == buf;
-      for (int s = 0; s < ns; ++s) {
-        if (strip_wise) {
-          sdeps[first[x] + s].push_back(first[pd] + s);
+    if (t.type == GEQRT || t.type == TSQRT || t.type == TTQRT) {
+      const int kind = t.type == GEQRT ? PK_GE : (t.type == TSQRT ? PK_TS : PK_TT);
+      const OTile X(&it, buf, t.i, t.k, lq);
+      const OTile A(&it, buf, kind == PK_GE ? t.i : t.piv, t.k, lq);
+      const int slot = pl.tslot[x];
+      DevTask d{};
+      d.x = tref(buf, t.i, t.k, lq);
+      d.a = kind == PK_GE ? -1 : tref(buf, t.piv, t.k, lq);
+      d.c = -1;
+      d.tslot = slot;
+      int32_t last = -1;
+      for (int b = 0; b < nblk; ++b) {
+        // PF(b)
+        rd.clear();
+        wr.clear();
+        if (kind == PK_GE) {
+          X.full(wr, b, b);
+          for (int br = b + 1; br < nblk; ++br) X.full(wr, br, b);
+        } else if (kind == PK_TS) {
+          A.up(wr, b);
+          for (int br = 0; br < nblk; ++br) X.full(wr, br, b);
         } else {
-          for (int32_t y = first[pd]; y < first[pd + 1]; ++y) sdeps[first[x] + s].push_back(y);
+          A.up(wr, b);
+          for (int br = 0; br < b; ++br) X.full(wr, br, b);
+          X.up(wr, b);
+        }
+        wr.push_back(it.t(slot, b));
+        const int64_t rows = kind == PK_GE ? nb - (int64_t)b * ib : (kind == PK_TS ? nb : (int64_t)(b + 1) * ib);
+        d.op = make_op(PF, lq, false, 0, b, kind);
+        last = g.add(d, 3 * ib2 * rows * 4, rd, wr, -1);
+        // PU(b, s)
+        for (int s = b + 1; s < nblk; ++s) {
+          rd.clear();
+          wr.clear();
+          if (kind == PK_GE) {
+            X.lo(rd, b);
+            for (int br = b + 1; br < nblk; ++br) X.full(rd, br, b);
+            for (int br = b; br < nblk; ++br) X.full(wr, br, s);
+          } else if (kind == PK_TS) {
+            for (int br = 0; br < nblk; ++br) X.full(rd, br, b);
+            A.full(wr, b, s);
+            for (int br = 0; br < nblk; ++br) X.full(wr, br, s);
+          } else {
+            for (int br = 0; br < b; ++br) X.full(rd, br, b);
+            X.up(rd, b);
+            A.full(wr, b, s);
+            for (int br = 0; br <= b; ++br) X.full(wr, br, s);
+          }
+          rd.push_back(it.t(slot, b));
+          d.op = make_op(PU, lq, false, s, b, kind);
+          last = g.add(d, 4 * ib2 * rows, rd, wr, -1);
         }
       }
+      panel_last[x] = last;
+    } else if (t.type == UNMQR || t.type == TSMQR || t.type == TTMQR) {
+      const int owner = pl.owner[x];
+      DevTask d{};
+      d.x = tref(buf, t.i, t.k, lq);
+      d.a = t.type == UNMQR ? -1 : tref(buf, t.piv, t.j, lq);
+      d.c = tref(buf, t.i, t.j, lq);
+      d.tslot = pl.tslot[owner];
+      const OTile C(&it, buf, t.i, t.j, lq);
+      const OTile Cp(&it, buf, t.type == UNMQR ? t.i : t.piv, t.j, lq);
+      const int64_t per_strip = (t.type == TSMQR ? 4 : 2) * (int64_t)nb * nb * w;
+      for (int s = 0; s < S; ++s) {
+        rd.clear();
+        wr.clear();
+        const int cb0 = s * (w / ib), cb1 = std::min(nblk, (s + 1) * (w / ib));
+        for (int cb = cb0; cb < cb1; ++cb) {
+          for (int br = 0; br < nblk; ++br) {
+            C.full(wr, br, cb);
+            if (t.type != UNMQR) Cp.full(wr, br, cb);
+          }
+        }
+        d.op = make_op(t.type, lq, false, s, 0, 0);
+        g.add(d, per_strip, rd, wr, panel_last[owner]);
+      }
+    } else {   // COPY(i, j): R part of A's tile (i, j) into the second phase's tile (i, j)
+      DevTask d{};
+      d.x = tile_ref(0, (int64_t)t.j * p + t.i);
+      d.a = -1;
+      d.c = tile_ref(1, (int64_t)t.j * q + t.i);
+      d.tslot = -1;
+      d.flags = t.i == t.j ? 1 : 0;
+      d.op = make_op(COPY, false, false, 0, 0, 0);
+      rd.clear();
+      wr.clear();
+      const OTile src(&it, 0, t.i, t.j, false), dst(&it, 1, t.i, t.j, false);
+      for (int br = 0; br < nblk; ++br) {
+        for (int bc = 0; bc < nblk; ++bc) {
+          dst.full(wr, br, bc);
+          if (t.i < t.j) src.full(rd, br, bc);
+          else if (br < bc) src.full(rd, br, bc);
+          else if (br == bc) src.up(rd, br);
+        }
+      }
+      g.add(d, (int64_t)nb * nb, rd, wr, -1);
     }
   }
-  // bottom levels (program order is topological: deps point backwards)
+
+  // bottom levels (sub-task numbering is a topological order: dependencies point backwards)
+  const int32_t nsub = (int32_t)g.sub.size();
   std::vector<int64_t> bottom(nsub, 0);
   for (int32_t y = nsub - 1; y >= 0; --y) {
-    bottom[y] += wsub[y];
-    for (int32_t d : sdeps[y]) bottom[d] = std::max(bottom[d], bottom[y]);
+    bottom[y] += g.weight[y];
+    for (int32_t dd : g.deps[y]) bottom[dd] = std::max(bottom[dd], bottom[y]);
   }
   std::vector<int32_t> order(nsub);
   for (int32_t y = 0; y < nsub; ++y) order[y] = y;
@@ -496,11 +635,11 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
   pl.dev.resize(nsub);
   pl.deps.clear();
   for (int32_t y = 0; y < nsub; ++y) {
-    DevTask e = sub[order[y]];
+    DevTask e = g.sub[order[y]];
     e.dep_begin = (int32_t)pl.deps.size();
-    for (int32_t d : sdeps[order[y]]) {
-      if (pos[d] >= y) throw std::logic_error("priority order is not topological");
-      pl.deps.push_back(pos[d]);
+    for (int32_t dd : g.deps[order[y]]) {
+      if (pos[dd] >= y) throw std::logic_error("priority order is not topological");
+      pl.deps.push_back(pos[dd]);
     }
     e.dep_end = (int32_t)pl.deps.size();
     pl.dev[y] = e;

@@ -7,6 +7,9 @@
 namespace bd {
 
 enum TaskType : int { GEQRT = 0, UNMQR = 1, TSQRT = 2, TSMQR = 3, TTQRT = 4, TTMQR = 5, COPY = 6 };
+// Device-only sub-task types: factor one inner block of a panel (PF), apply it to a later column block
+// of the panel (PU).  Their op word carries the panel kind (0 GE, 1 TS, 2 TT) in bits 24-25.
+enum SubType : int { PF = 7, PU = 8 };
 enum Phase : int { PH_QR = 0, PH_LQ = 1, PH_PQR = 2 };
 enum Tree : int { FLATTS = 0, FLATTT = 1, GREEDY = 2, AUTO = 3 };
 enum Variant : int { V_BIDIAG = 0, V_RBIDIAG = 1 };
@@ -22,7 +25,7 @@ struct Elim {
 // One unit of work of the persistent executor (32 bytes).  Tile references pack a buffer id in the
 // top 4 bits and the tile index (column-major tile grid of that buffer) in the low 28 bits.
 struct DevTask {
-  int32_t op;        // type | tr << 4 | notrans << 5 | strip << 8
+  int32_t op;        // type | tr << 4 | notrans << 5 | strip << 8 | block << 16 | kind << 24
   int32_t x;         // reflector / panel tile (COPY: source tile)
   int32_t a;         // pivot tile (TS/TT panels) or top C tile (TSMQR/TTMQR)
   int32_t c;         // C tile of UNMQR / bottom C tile of TSMQR, TTMQR (COPY: destination tile)

@@ -1,0 +1,125 @@
+"""Full-size GPU checks at the bench's workloads (8192^2 square BiDiag, 65536 x 1024 tall R-BiDiag), in
+the launch configuration bench.py times.
+
+At these sizes the oracle cannot run the whole reduction, so the checks are properties that hold at
+any size (band structure, orthogonal invariance of the Frobenius norm, singular values of B equal to
+those of A, A P X = Q B X through the library's own apply_q / apply_p, orthogonality of Q) plus one
+sampled output the oracle computes exactly: the first diagonal block of B, which only depends on the
+panel tasks of the first tile column (Sec. 3.4: QR(1) factors that column before anything else).
+"""
+import numpy as np
+import pytest
+
+import paper_1611_06892_gb300 as G
+from oracle import bidiag as OB
+from oracle import trees as T
+from paper_1611_06892_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def dense_band(torch, ab, n, nb):
+    """Dense n x n B from the (nb+1) x n band on the device."""
+    B = torch.zeros((n, n), dtype=torch.float64, device=ab.device)
+    j = torch.arange(n, device=ab.device)
+    for d in range(nb + 1):
+        i = j + d - nb
+        ok = i >= 0
+        B[i[ok], j[ok]] = ab[d, ok]
+    return B
+
+
+def run(torch, A, nb, ib, tree, variant, resources):
+    h = G.Handle()
+    h.set_option(G.OPT_AUTO_RESOURCES, resources)
+    res = h.band(A, nb, ib, tree, variant)
+    h.sync()
+    return h, res
+
+
+def check_properties(torch, h, res, A, nb, s_ref, tol_sv, via_gram=False):
+    m, n = A.shape
+    ab = res.band()
+    # rows above B's first row are exact zeros
+    d = torch.arange(nb + 1, device=ab.device)[:, None]
+    j = torch.arange(n, device=ab.device)[None, :]
+    assert torch.all(ab[(j + d - nb) < 0] == 0)
+    B = dense_band(torch, ab, n, nb)
+    nA = torch.linalg.norm(A).item()
+    assert abs(torch.linalg.norm(B).item() - nA) <= 1e-12 * nA * max(m, n) ** 0.5
+    if via_gram:
+        # eigenvalues of B^T B against s^2 (absolute tolerance on the squares; cheaper than an SVD)
+        lam = torch.linalg.eigvalsh(B.t() @ B).flip(0)
+        assert (lam - s_ref ** 2).abs().max().item() <= tol_sv
+    else:
+        sb = torch.linalg.svdvals(B)
+        assert (sb - s_ref).abs().max().item() <= tol_sv
+    # A (P X) = Q [B X; 0]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    X = torch.randn((n, 4), dtype=torch.float64, device="cuda", generator=gen)
+    PXt = torch.empty((n, 4), dtype=torch.float64, device="cuda").t()   # 4 x n, column-major
+    PXt.copy_(X.t())
+    res.apply_p(PXt, 1)                                  # X^T P^T = (P X)^T
+    h.sync()
+    y1 = A @ PXt.t()
+    Y = torch.zeros((4, m), dtype=torch.float64, device="cuda").t()       # m x 4, column-major
+    Y[:n] = B @ X
+    res.apply_q(Y, 0)
+    h.sync()
+    err = torch.linalg.norm(y1 - Y).item() / (nA * torch.linalg.norm(X).item())
+    assert err <= 30 * max(m, n) * EPS, err
+    # Q^T Q X = X
+    Z = Y.clone()
+    res.apply_q(Z, 1)
+    h.sync()
+    Z2 = Z.clone()
+    res.apply_q(Z2, 0)
+    h.sync()
+    assert torch.linalg.norm(Z2 - Y).item() <= 30 * m * EPS * torch.linalg.norm(Y).item()
+
+
+@pytest.mark.parametrize("tree", ("auto", "flatts"))
+def test_square_8192(torch_mod, tree):
+    torch = torch_mod
+    m = n = 8192
+    nb, ib = 256, 32
+    s = inputs.geometric_sv(n)
+    A = inputs.torch_prescribed_singular_values(m, n, s, 2, 3)
+    R = max(1, torch.cuda.get_device_properties(0).multi_processor_count * 32 // nb)
+    h, res = run(torch, A, nb, ib, tree, "bidiag", R)
+    s_ref = torch.as_tensor(np.sort(s)[::-1].copy(), device="cuda")
+    check_properties(torch, h, res, A, nb, s_ref, 30 * n * EPS, via_gram=True)
+    # sampled output: the first diagonal block of B from the oracle's column-0 panel tasks
+    tasks = T.task_list(m // nb, n // nb, G.TREES[tree], T.BIDIAG, R)
+    col0 = [(x, t) for x, t in enumerate(tasks)
+            if t[1] == T.QR and t[2] == 0 and t[0] in (T.GEQRT, T.TSQRT, T.TTQRT)]
+    A0 = A[:, :nb].cpu().numpy()
+    st = OB.new_state(np.zeros((m, nb)), nb, ib, G.TREES[tree], T.BIDIAG, resources=R)
+    st["A"].M[...] = A0
+    OB.run_tasks(st, col0)
+    R00 = np.triu(st["A"].M[:nb, :nb])
+    B00 = np.triu(dense_band(torch, res.band(), n, nb)[:nb, :nb].cpu().numpy())
+    assert np.abs(B00 - R00).max() <= 1e-12 * torch.linalg.norm(A).item()
+    res.free()
+    h.close()
+
+
+@pytest.mark.parametrize("tree", ("greedy", "auto"))
+def test_tall_65536x1024_rbidiag(torch_mod, tree):
+    torch = torch_mod
+    m, n, nb, ib = 65536, 1024, 256, 32
+    A = inputs.torch_gaussian(m, n, 4)
+    R = max(1, torch.cuda.get_device_properties(0).multi_processor_count * 32 // nb)
+    h, res = run(torch, A, nb, ib, tree, "rbidiag", R)
+    s_ref = torch.linalg.svdvals(A)
+    check_properties(torch, h, res, A, nb, s_ref, 30 * m * EPS * s_ref[0].item())
+    res.free()
+    h.close()
