@@ -108,10 +108,45 @@ __device__ __forceinline__ double masked_ld(const double* g, int R, int C, int n
 
 // Shared element (r, c) at s[r * rs + c * cs] <- oriented X(r0 + r, c0 + c).  M_UPPER zeroes entries
 // below the diagonal, M_UNITLOWER gives the unit lower trapezoid.  Lanes run along the contiguous
-// direction of global memory (rows for tr = 0, columns for tr = 1), several loads in flight.
+// direction of global memory (rows for tr = 0, columns for tr = 1).  Blocks of at most 256 x 32 (every
+// block the sub-tasks move) issue all of a thread's loads (up to 32) before the first shared store, so
+// that one L2 latency covers the whole block.
 __device__ void load_tile(double* s, int rs, int cs, const double* g, int nb, int tr, int r0, int c0, int rows,
                           int cols, int mask) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (rows <= 256 && cols <= 32) {
+    double v[32];
+    if (!tr) {   // c = warp + 8 kc, r = lane + 32 kr
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+#pragma unroll
+        for (int kr = 0; kr < 8; ++kr) {
+          const int c = warp + 8 * kc, r = lane + 32 * kr;
+          v[kc * 8 + kr] = (c < cols && r < rows) ? masked_ld(g, r0 + r, c0 + c, nb, tr, mask) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+#pragma unroll
+        for (int kr = 0; kr < 8; ++kr) {
+          const int c = warp + 8 * kc, r = lane + 32 * kr;
+          if (c < cols && r < rows) s[r * rs + c * cs] = v[kc * 8 + kr];
+        }
+      }
+    } else {     // r = warp + 8 kr, c = lane
+#pragma unroll
+      for (int kr = 0; kr < 32; ++kr) {
+        const int r = warp + 8 * kr;
+        v[kr] = (lane < cols && r < rows) ? masked_ld(g, r0 + r, c0 + lane, nb, tr, mask) : 0.0;
+      }
+#pragma unroll
+      for (int kr = 0; kr < 32; ++kr) {
+        const int r = warp + 8 * kr;
+        if (lane < cols && r < rows) s[r * rs + lane * cs] = v[kr];
+      }
+    }
+    return;
+  }
   if (!tr) {
     for (int c = warp; c < cols; c += kWarps) {
 #pragma unroll 4
@@ -301,17 +336,35 @@ __device__ void apply_rm(const double* V, int lv, int vrows, int kb, const doubl
     }
   }
   __syncthreads();
-  // phase 2: W2 = op(T) W, then Ct -= W2
-  for (int u = threadIdx.x; u < ncols * kb; u += kThreads) {
-    const int c = u % ncols, a = u / ncols;
-    double s = 0.0;
-    if (!notrans) {
-      for (int t = 0; t <= a; ++t) s = fma(Tb[t + a * kb], W[t * lc + c], s);
-    } else {
-      for (int t = a; t < kb; ++t) s = fma(Tb[a + t * kb], W[t * lc + c], s);
+  // phase 2: W2 = op(T) W, then Ct -= W2.  For kb = 32 and ncols = 32 each thread takes the rows
+  // g, 31 - g, g + 8, 23 - g of one column (g = warp), so that every thread does 66 FMAs.
+  if (kb == 32 && ncols == 32) {
+    const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int arow[4] = {g, 31 - g, g + 8, 23 - g};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = arow[q];
+      double s = 0.0;
+      if (!notrans) {
+        for (int t = 0; t <= a; ++t) s = fma(Tb[t + a * kb], W[t * lc + c], s);
+      } else {
+        for (int t = a; t < kb; ++t) s = fma(Tb[a + t * kb], W[t * lc + c], s);
+      }
+      W2[a * lc + c] = s;
+      if (Ct) Ct[a * lc + c] -= s;
     }
-    W2[a * lc + c] = s;
-    if (Ct) Ct[a * lc + c] -= s;
+  } else {
+    for (int u = threadIdx.x; u < ncols * kb; u += kThreads) {
+      const int c = u % ncols, a = u / ncols;
+      double s = 0.0;
+      if (!notrans) {
+        for (int t = 0; t <= a; ++t) s = fma(Tb[t + a * kb], W[t * lc + c], s);
+      } else {
+        for (int t = a; t < kb; ++t) s = fma(Tb[a + t * kb], W[t * lc + c], s);
+      }
+      W2[a * lc + c] = s;
+      if (Ct) Ct[a * lc + c] -= s;
+    }
   }
   __syncthreads();
   // phase 3: C -= V W2
