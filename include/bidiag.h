@@ -34,8 +34,10 @@ typedef struct bidiag_result* bidiag_result_t;
 
 /* Reduction trees: Sec. 3.3 (FlatTS, FlatTT, Greedy) and Sec. 5 (Auto). */
 enum { BIDIAG_FLATTS = 0, BIDIAG_FLATTT = 1, BIDIAG_GREEDY = 2, BIDIAG_AUTO = 3 };
-/* Variants: Sec. 3.4 (BiDiag) and Sec. 3.5 (R-BiDiag = QR(p,q) then BiDiag of the top square). */
-enum { BIDIAG_BIDIAG = 0, BIDIAG_RBIDIAG = 1 };
+/* Variants: Sec. 3.4 (BiDiag) and Sec. 3.5 (R-BiDiag = QR(p,q) then BiDiag of the top square).
+ * BIDIAG_AUTO_VARIANT picks the one with the shorter critical path (Sec. 4.3.3, the delta_s switch;
+ * see bidiag_plan_choose_variant); the result records the variant used. */
+enum { BIDIAG_BIDIAG = 0, BIDIAG_RBIDIAG = 1, BIDIAG_AUTO_VARIANT = 2 };
 /* Status codes. */
 enum {
   BIDIAG_OK = 0,
@@ -57,7 +59,9 @@ enum {
                                      flag nothing sets, so that its wait runs out (failure-path test) */
   BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16 or 32, default 32) */
   BIDIAG_OPT_TIMING = 5,          /* 1: time the executor launch of each bidiag_band with CUDA events */
-  BIDIAG_OPT_TRACE = 6            /* 1: record a per-task trace of each bidiag_band (see bidiag_trace) */
+  BIDIAG_OPT_TRACE = 6,           /* 1: record a per-task trace of each bidiag_band (see bidiag_trace) */
+  BIDIAG_OPT_F32_UPDATES = 7      /* FP32 storage: 0 = updates as three TF32 tensor-core products (default),
+                                     1 = updates by FP32 FMA on the CUDA cores (FP32-exact products) */
 };
 
 /* Task type codes of the canonical task list (GELQT etc. are the same codes in LQ phases). */
@@ -69,25 +73,26 @@ enum { BIDIAG_PH_QR = 0, BIDIAG_PH_LQ = 1, BIDIAG_PH_PQR = 2 };
 /*
  * Reflector store of a result (Sec. 3.6 "Memory usage": R-BiDiag keeps its pre-QR reflectors apart).
  * All pointers are device pointers owned by the result.
- *  tiles   : p*q tiles of nb*nb doubles, tile (a, b) at tiles + (b*p + a)*nb*nb, column-major inside
+ *  tiles   : p*q tiles of nb*nb elements, tile (a, b) at tiles + (b*p + a)*nb*nb, column-major inside
  *            with leading dimension nb, zero padded beyond m / n.  After the reduction it holds the
  *            Householder vectors of every tile kernel in the positions they eliminated (GEQRT/GELQT:
  *            strict lower/upper triangle; TSQRT: the whole eliminated tile; TTQRT: the upper/lower
  *            triangle of the eliminated tile) and, for BiDiag, the band entries.
  *  tiles2  : R-BiDiag only (else NULL): q*q tiles, same layout, holding the second phase.
- *  T       : one block of ib*nb doubles per panel task (tslot order): the ib x ib upper-triangular T
+ *  T       : one block of ib*nb elements per panel task (tslot order): the ib x ib upper-triangular T
  *            factors of the compact WY form of each group of ib reflectors side by side
  *            (block b at T + slot*ib*nb + b*ib*ib, column-major, ld ib); tau_j = diag(T).
  *  tslot   : host array, one entry per canonical task: its T slot for a panel task, -1 otherwise.
  */
 typedef struct bidiag_reflectors {
-  const double* tiles;
-  const double* tiles2;
-  const double* T;
+  const void* tiles;           /* double or float elements, see elem_bytes */
+  const void* tiles2;
+  const void* T;
   const int32_t* tslot;
   int64_t ntasks;
   int64_t m, n;
   int32_t nb, ib, p, q, npanels, variant;
+  int32_t elem_bytes;          /* 8: tiles and T in FP64; 4: in FP32 (bidiag_band_f32) */
 } bidiag_reflectors;
 
 /* Creates a handle bound to CUDA device `device` and stream `cuda_stream` (a cudaStream_t; NULL =
@@ -103,12 +108,23 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value);
  * band form with tile size nb, inner blocking ib (Sec. 6.2: internal blocking of the TS/TT kernels),
  * tree and variant.  Preconditions (else -i): m >= 1 (-2), 1 <= n (-3), d_A != NULL (-4), lda >= m
  * (-5), 1 <= nb <= 256 (-6), 1 <= ib <= min(nb, 64) and nb % ib == 0 (-7), tree in 0..3 (-8), variant
- * in 0..1 (-9), out != NULL (-10).  m < n returns BIDIAG_ERR_UNSUPPORTED (Sec. 3.6: the transposed
+ * in 0..2 (-9), out != NULL (-10).  m < n returns BIDIAG_ERR_UNSUPPORTED (Sec. 3.6: the transposed
  * problem).  *out receives a new result object (free with bidiag_result_free) that owns the band, the
  * reflector store and the canonical task list.  The call enqueues the work and returns.
  */
 int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_t lda,
                 int nb, int ib, int tree, int variant, bidiag_result_t* out);
+
+/*
+ * Split-precision form of bidiag_band: FP32 storage (d_A, the tiles, T factors and band are float);
+ * the trailing updates run on the tensor cores as three TF32 products (hi*hi + hi*lo + lo*hi, each
+ * operand split into a TF32 part and a TF32 remainder) accumulated in FP32, while the reflector norms,
+ * beta, tau (the T diagonal) and the scaling of the reflector vectors are computed in FP64.  Arguments,
+ * errors and ownership as bidiag_band; read the band with bidiag_result_band_f32 and apply Q, P with
+ * bidiag_apply_q_f32 / bidiag_apply_p_f32.  Sec. 3.6: the method holds for single precision.
+ */
+int bidiag_band_f32(bidiag_handle h, int64_t m, int64_t n, const float* d_A, int64_t lda,
+                    int nb, int ib, int tree, int variant, bidiag_result_t* out);
 
 /*
  * Same reduction for host buffers: copies h_A (column-major, lda) to the device, reduces it, copies the
@@ -153,6 +169,10 @@ int bidiag_band_noalloc(int64_t m, int64_t n, const double* d_A, int64_t lda, in
  * entry outside the band is an exact zero by construction. */
 int bidiag_result_band(bidiag_result_t r, const double** ab, int64_t* ldab, int64_t* n, int* nb);
 
+/* Band of an FP32 result (bidiag_band_f32), same layout as bidiag_result_band; BIDIAG_ERR_UNSUPPORTED
+ * for an FP64 result (and bidiag_result_band returns it for an FP32 result). */
+int bidiag_result_band_f32(bidiag_result_t r, const float** ab, int64_t* ldab, int64_t* n, int* nb);
+
 /* Canonical task list (host memory owned by the result): ntasks records of 6 int32
  * (type, phase, k, i, piv, j) in program order, oriented coordinates (an LQ step's oriented tile (a,b)
  * is tile (b,a)); -1 where a field is unused.  COPY(i, j) copies tile (i, j)'s R into the second
@@ -171,6 +191,13 @@ int bidiag_apply_q(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols,
  * trans = 0: C <- C P, trans = 1: C <- C P^T.  Errors: -3 trans, -4 nrows < 0, -5 d_C, -6 ldc. */
 int bidiag_apply_p(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, double* d_C,
                    int64_t ldc);
+
+/* FP32 forms of bidiag_apply_q / bidiag_apply_p for results of bidiag_band_f32 (float C, same layout
+ * and errors; -2 when the result's precision does not match). */
+int bidiag_apply_q_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols, float* d_C,
+                       int64_t ldc);
+int bidiag_apply_p_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, float* d_C,
+                       int64_t ldc);
 
 /* Waits for the handle's stream and returns the device-side status of the work enqueued since the
  * last call: BIDIAG_OK, BIDIAG_ERR_TIMEOUT (a dependency wait ran out; the context stays usable) or
@@ -213,6 +240,14 @@ int bidiag_plan_eliminations(int64_t p, int64_t q, int tree, int variant, int64_
  * Table 1 units (GEQRT 4, UNMQR 6, TSQRT 6, TSMQR 12, TTQRT 2, TTMQR 6, COPY 0) in *cp when cp != NULL. */
 int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resources,
                       int32_t* tasks, int32_t* level, int64_t cap, int64_t* count, int64_t* cp);
+
+/* BiDiag or R-BiDiag for a p x q tile matrix, whichever has the shorter critical path in the task-DAG
+ * model (Table 1 weights, unbounded resources; Sec. 4.3.3 shows the switch ratio delta_s = p/q
+ * oscillates in [5, 8], e.g. 5.67 for q = 100).  The Auto tree is compared through Greedy.  Ties keep
+ * BiDiag.  *variant receives BIDIAG_BIDIAG or BIDIAG_RBIDIAG; the two critical paths are returned when
+ * the pointers are not NULL.  Errors: -1 (p, q), -3 (tree), -5 (variant NULL). */
+int bidiag_plan_choose_variant(int64_t p, int64_t q, int tree, int64_t resources, int* variant,
+                               int64_t* cp_bidiag, int64_t* cp_rbidiag);
 
 /* The device program the executor runs for a reduction (host-only, for validation): *count sub-tasks
  * of 8 int32 in queue order (op word: type | orientation << 4 | Q-instead-of-Q^T << 5 | strip << 8 |

@@ -20,11 +20,12 @@ LIB_PATH = os.path.join(_HERE, "libbidiag.so")
 
 FLATTS, FLATTT, GREEDY, AUTO = 0, 1, 2, 3
 TREES = {"flatts": FLATTS, "flattt": FLATTT, "greedy": GREEDY, "auto": AUTO}
-BIDIAG, RBIDIAG = 0, 1
-VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG}
+BIDIAG, RBIDIAG, AUTO_VARIANT = 0, 1, 2
+VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG, "auto": AUTO_VARIANT}
 OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = 0, 1, 2, 3, 4, 5
 NOALLOC_SCRATCH_BYTES = 8 << 20
 OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING, OPT_TRACE = 1, 2, 3, 4, 5, 6
+OPT_F32_UPDATES = 7
 
 _lib = None
 
@@ -40,7 +41,7 @@ class Reflectors(ctypes.Structure):
                 ("tslot", ctypes.POINTER(ctypes.c_int32)), ("ntasks", ctypes.c_int64),
                 ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
                 ("p", ctypes.c_int32), ("q", ctypes.c_int32), ("npanels", ctypes.c_int32),
-                ("variant", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("elem_bytes", ctypes.c_int32)]
 
 
 def load_library(path=LIB_PATH):
@@ -58,6 +59,10 @@ def load_library(path=LIB_PATH):
         "bidiag_set_option": (cint, [vp, cint, i64]),
         "bidiag_band": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, P(vp)]),
         "bidiag_band_host": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, P(vp)]),
+        "bidiag_band_f32": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, P(vp)]),
+        "bidiag_result_band_f32": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
+        "bidiag_apply_q_f32": (cint, [vp, vp, cint, i64, vp, i64]),
+        "bidiag_apply_p_f32": (cint, [vp, vp, cint, i64, vp, i64]),
         "bidiag_band_noalloc": (cint, [i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, vp]),
         "bidiag_result_band": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
         "bidiag_result_tasks": (cint, [vp, P(P(i32)), P(i64)]),
@@ -72,6 +77,7 @@ def load_library(path=LIB_PATH):
         "bidiag_destroy": (cint, [vp]),
         "bidiag_plan_eliminations": (cint, [i64, i64, cint, cint, i64, P(i32), i64, P(i64)]),
         "bidiag_plan_tasks": (cint, [i64, i64, cint, cint, i64, P(i32), P(i32), i64, P(i64), P(i64)]),
+        "bidiag_plan_choose_variant": (cint, [i64, i64, cint, i64, P(cint), P(i64), P(i64)]),
         "bidiag_plan_program": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), i64, P(i64), P(i32),
                                        i64, P(i64), P(i32)]),
     }
@@ -106,6 +112,12 @@ def bidiag_band(h, m, n, d_A, lda, nb, ib, tree, variant):
     return r
 
 
+def bidiag_band_f32(h, m, n, d_A, lda, nb, ib, tree, variant):
+    r = ctypes.c_void_p()
+    _check(h, load_library().bidiag_band_f32(h, m, n, d_A, lda, nb, ib, tree, variant, ctypes.byref(r)))
+    return r
+
+
 def bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab, keep=False):
     r = ctypes.c_void_p()
     _check(h, load_library().bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab,
@@ -134,6 +146,14 @@ def bidiag_apply_q(h, r, trans, ncols, d_C, ldc):
 
 def bidiag_apply_p(h, r, trans, nrows, d_C, ldc):
     _check(h, load_library().bidiag_apply_p(h, r, trans, nrows, d_C, ldc))
+
+
+def bidiag_apply_q_f32(h, r, trans, ncols, d_C, ldc):
+    _check(h, load_library().bidiag_apply_q_f32(h, r, trans, ncols, d_C, ldc))
+
+
+def bidiag_apply_p_f32(h, r, trans, nrows, d_C, ldc):
+    _check(h, load_library().bidiag_apply_p_f32(h, r, trans, nrows, d_C, ldc))
 
 
 def bidiag_result_free(r):
@@ -169,6 +189,15 @@ def bidiag_plan_tasks(p, q, tree, variant, resources=1):
     return tasks[:cnt.value], lv[:cnt.value], cp.value
 
 
+def bidiag_plan_choose_variant(p, q, tree, resources=1):
+    """(variant, critical path of BiDiag, critical path of R-BiDiag) for a p x q tile matrix."""
+    v = ctypes.c_int()
+    cb, cr = ctypes.c_int64(), ctypes.c_int64()
+    _check(None, load_library().bidiag_plan_choose_variant(p, q, tree, resources, ctypes.byref(v), ctypes.byref(cb),
+                                                          ctypes.byref(cr)))
+    return v.value, cb.value, cr.value
+
+
 def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
     """Device program of a reduction: (sub-tasks (count x 8) int32, dependency array, strip width)."""
     lib = load_library()
@@ -189,22 +218,22 @@ def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
 class _CudaArray:
     """Zero-copy view of library-owned device memory for torch.as_tensor."""
 
-    def __init__(self, ptr, shape, strides_elems):
+    def __init__(self, ptr, shape, strides_elems, esize=8):
         self.__cuda_array_interface__ = {
-            "shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False), "version": 3,
-            "strides": tuple(8 * s for s in strides_elems)}
+            "shape": tuple(shape), "typestr": "<f8" if esize == 8 else "<f4", "data": (int(ptr), False),
+            "version": 3, "strides": tuple(esize * s for s in strides_elems)}
 
 
-def _device_view(ptr, shape, strides):
+def _device_view(ptr, shape, strides, esize=8):
     import torch
-    return torch.as_tensor(_CudaArray(ptr, shape, strides), device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, shape, strides, esize), device="cuda")
 
 
 def _colmajor(A):
-    """Column-major FP64 CUDA tensor (copy only if needed) and its leading dimension."""
+    """Column-major FP64 / FP32 CUDA tensor (copy only if needed) and its leading dimension."""
     import torch
-    if A.dtype != torch.float64 or not A.is_cuda:
-        raise TypeError("A must be a float64 CUDA tensor")
+    if A.dtype not in (torch.float64, torch.float32) or not A.is_cuda:
+        raise TypeError("A must be a float64 or float32 CUDA tensor")
     m, n = A.shape
     if A.stride(0) == 1 and (A.stride(1) >= max(1, m) or n == 1):
         return A, max(A.stride(1), m)
@@ -229,9 +258,11 @@ class Handle:
     def band(self, A, nb, ib, tree="greedy", variant="bidiag"):
         tree = TREES[tree] if isinstance(tree, str) else tree
         variant = VARIANTS[variant] if isinstance(variant, str) else variant
+        import torch
         Ac, lda = _colmajor(A)
         m, n = A.shape
-        r = bidiag_band(self.h, m, n, ctypes.c_void_p(Ac.data_ptr()), lda, nb, ib, tree, variant)
+        fn = bidiag_band_f32 if A.dtype == torch.float32 else bidiag_band
+        r = fn(self.h, m, n, ctypes.c_void_p(Ac.data_ptr()), lda, nb, ib, tree, variant)
         return Result(self, r, keep=Ac)
 
     def sync(self):
@@ -270,20 +301,21 @@ class Result:
         self.r = r
         self._keep = keep
         lib = load_library()
+        desc = Reflectors()
+        _check(handle.h, lib.bidiag_result_reflectors(r, ctypes.byref(desc)))
+        self.desc = desc
+        self.esize = desc.elem_bytes
         ab = ctypes.c_void_p()
         ldab = ctypes.c_int64()
         n = ctypes.c_int64()
         nb = ctypes.c_int()
-        _check(handle.h, lib.bidiag_result_band(r, ctypes.byref(ab), ctypes.byref(ldab), ctypes.byref(n),
-                                                ctypes.byref(nb)))
+        getter = lib.bidiag_result_band if self.esize == 8 else lib.bidiag_result_band_f32
+        _check(handle.h, getter(r, ctypes.byref(ab), ctypes.byref(ldab), ctypes.byref(n), ctypes.byref(nb)))
         self.ab_ptr, self.ldab, self.n, self.nb = ab.value, ldab.value, n.value, nb.value
-        desc = Reflectors()
-        _check(handle.h, lib.bidiag_result_reflectors(r, ctypes.byref(desc)))
-        self.desc = desc
 
     def band(self):
         """Copy of B in LAPACK upper-band storage, shape (nb + 1, n)."""
-        return _device_view(self.ab_ptr, (self.nb + 1, self.n), (1, self.ldab)).clone()
+        return _device_view(self.ab_ptr, (self.nb + 1, self.n), (1, self.ldab), self.esize).clone()
 
     def tasks(self):
         lib = load_library()
@@ -301,12 +333,12 @@ class Result:
         rows = d.q if second else d.p
         cols = d.q
         nb = d.nb
-        t = _device_view(ptr, (cols * rows * nb * nb,), (1,)).clone()
+        t = _device_view(ptr, (cols * rows * nb * nb,), (1,), self.esize).clone()
         return t.view(cols, rows, nb, nb).permute(1, 0, 3, 2)   # [a, b, r, c]
 
     def T(self):
         d = self.desc
-        return _device_view(d.T, (max(d.npanels, 1), d.ib, d.nb), (d.ib * d.nb, 1, d.ib)).clone()
+        return _device_view(d.T, (max(d.npanels, 1), d.ib, d.nb), (d.ib * d.nb, 1, d.ib), self.esize).clone()
 
     def tslot(self):
         d = self.desc
@@ -314,14 +346,16 @@ class Result:
 
     def apply_q(self, C, trans):
         Cc, ldc = _colmajor(C)
-        bidiag_apply_q(self.handle.h, self.r, trans, C.shape[1], ctypes.c_void_p(Cc.data_ptr()), ldc)
+        fn = bidiag_apply_q if self.esize == 8 else bidiag_apply_q_f32
+        fn(self.handle.h, self.r, trans, C.shape[1], ctypes.c_void_p(Cc.data_ptr()), ldc)
         if Cc.data_ptr() != C.data_ptr():
             C.copy_(Cc)
         return C
 
     def apply_p(self, C, trans):
         Cc, ldc = _colmajor(C)
-        bidiag_apply_p(self.handle.h, self.r, trans, C.shape[0], ctypes.c_void_p(Cc.data_ptr()), ldc)
+        fn = bidiag_apply_p if self.esize == 8 else bidiag_apply_p_f32
+        fn(self.handle.h, self.r, trans, C.shape[0], ctypes.c_void_p(Cc.data_ptr()), ldc)
         if Cc.data_ptr() != C.data_ptr():
             C.copy_(Cc)
         return C

@@ -55,6 +55,7 @@ struct bidiag_ctx {
   bool timed = false;
   std::set<bidiag_result*> live;   // results made on this handle and not yet freed
   int tracing = 0;
+  int f32_simt = 0;                // FP32 storage: updates by FFMA instead of 3xTF32 tensor-core products
   int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
   int64_t trace_cap = 0, trace_len = 0;
 };
@@ -64,10 +65,11 @@ struct bidiag_result {
   std::shared_ptr<PlanDev> pd;
   int64_t m = 0, n = 0;
   int nb = 0, ib = 0, tree = 0, variant = 0, p = 0, q = 0;
-  double* tiles = nullptr;
-  double* tiles2 = nullptr;
-  double* T = nullptr;
-  double* ab = nullptr;
+  int esize = 8;                  // 8: FP64 storage, 4: FP32 storage (split-precision updates)
+  void* tiles = nullptr;
+  void* tiles2 = nullptr;
+  void* T = nullptr;
+  void* ab = nullptr;
   int64_t ldab = 0;
 };
 
@@ -119,12 +121,12 @@ int64_t resources_of(bidiag_handle h, int nb, int w) {
 }
 
 // Executor launch of a program held in pd with the given buffers.
-int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t n0, double* b1, int64_t n1, double* b2,
-             int64_t n2, double* T, int npanels, int nb, int ib, int w, bool timed = false) {
+int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n0, void* b1, int64_t n1, void* b2,
+             int64_t n2, void* T, int npanels, int nb, int ib, int w, int esize, bool timed = false) {
   if (ntasks == 0) return BIDIAG_OK;
-  const size_t smem = bd::exec_smem_bytes(nb, ib, w);
-  CK(h, bd::exec_set_smem(smem));
-  const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem));
+  const size_t smem = bd::exec_smem_bytes(nb, ib, w, esize);
+  CK(h, bd::exec_set_smem(smem, esize));
+  const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem, esize));
   bd::ExecParams prm{};
   prm.tasks = pd.d_tasks;
   prm.deps = pd.d_deps;
@@ -142,6 +144,8 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t
   prm.ib = ib;
   prm.w = w;
   prm.wait_ns = h->wait_ns;
+  prm.esize = esize;
+  prm.f32_simt = h->f32_simt;
   prm.trace = nullptr;
   if (timed && h->tracing) {
     if (h->trace_cap < ntasks) {
@@ -162,8 +166,8 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, double* b0, int64_t
   return BIDIAG_OK;
 }
 
-int choose_strip(bidiag_handle h, int nb, int ib, int* w) {
-  *w = bd::choose_strip_width(nb, ib, h->strip_w, h->smem_optin);
+int choose_strip(bidiag_handle h, int nb, int ib, int esize, int* w) {
+  *w = bd::choose_strip_width(nb, ib, h->strip_w, h->smem_optin, esize);
   if (*w) return BIDIAG_OK;
   return fail(h, BIDIAG_ERR_UNSUPPORTED, "tile size / inner blocking need more shared memory than the device has");
 }
@@ -238,7 +242,8 @@ void free_result_buffers(bidiag_result* r) {
 }
 
 // Replays the panel tasks of one side (QR side: left = true; LQ side: left = false) on a tiled copy of C.
-int apply_side(bidiag_handle h, bidiag_result_t r, bool left, int trans, int64_t other, double* C, int64_t ldc) {
+template <typename E>
+int apply_side(bidiag_handle h, bidiag_result_t r, bool left, int trans, int64_t other, E* C, int64_t ldc) {
   const bd::Plan& pl = r->pd->plan;
   const int nb = r->nb, ib = r->ib;
   const int64_t crow = left ? r->m : other, ccol = left ? other : r->n;
@@ -246,7 +251,7 @@ int apply_side(bidiag_handle h, bidiag_result_t r, bool left, int trans, int64_t
   const int64_t rows_t = (crow + nb - 1) / nb, cols_t = (ccol + nb - 1) / nb;
   const int64_t nblk = left ? cols_t : rows_t;   // independent tile columns of the oriented C
   int w = 0;
-  int rc = choose_strip(h, nb, ib, &w);
+  int rc = choose_strip(h, nb, ib, (int)sizeof(E), &w);
   if (rc) return rc;
   const int S = (nb + w - 1) / w;
   // panel tasks of this side, in application order
@@ -308,17 +313,106 @@ int apply_side(bidiag_handle h, bidiag_result_t r, bool left, int trans, int64_t
   PlanDev prog;
   rc = upload_program(h, prog, dev, deps, 1);
   if (rc) return rc;
-  double* Ct = nullptr;
+  E* Ct = nullptr;
   rc = dev_alloc(h, &Ct, (size_t)rows_t * cols_t * nb * nb);
   if (rc) return rc;
   CK(h, bd::launch_pack(C, ldc, crow, ccol, nb, Ct, rows_t, cols_t, h->stream));
   rc = run_exec(h, prog, (int)dev.size(), r->tiles, (int64_t)r->p * r->q, r->tiles2,
-                r->tiles2 ? (int64_t)r->q * r->q : 0, Ct, rows_t * cols_t, r->T, pl.npanels, nb, ib, w);
+                r->tiles2 ? (int64_t)r->q * r->q : 0, Ct, rows_t * cols_t, r->T, pl.npanels, nb, ib, w,
+                (int)sizeof(E));
   if (rc) return rc;
   CK(h, bd::launch_unpack(Ct, rows_t, nb, crow, ccol, C, ldc, h->stream));
   CK(h, cudaFreeAsync(Ct, h->stream));
   // the program buffers are freed by ~PlanDev; wait for the stream so that they outlive the launch
   CK(h, cudaStreamSynchronize(h->stream));
+  return BIDIAG_OK;
+}
+
+template <typename E>
+int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, int nb, int ib, int tree,
+              int variant, bidiag_result_t* out) {
+  if (!h) return -1;
+  if (m < 1) return fail(h, -2, "m < 1");
+  if (n < 1) return fail(h, -3, "n < 1");
+  if (!d_A) return fail(h, -4, "A is NULL");
+  if (lda < m) return fail(h, -5, "lda < m");
+  if (nb < 1 || nb > bd::kMaxNb) return fail(h, -6, "nb out of range");
+  if (ib < 1 || ib > std::min(nb, 64) || nb % ib) return fail(h, -7, "ib out of range or does not divide nb");
+  if (tree < 0 || tree > 3) return fail(h, -8, "unknown tree");
+  if (variant < 0 || variant > 2) return fail(h, -9, "unknown variant");
+  if (!out) return fail(h, -10, "out is NULL");
+  *out = nullptr;
+  if (m < n) return fail(h, BIDIAG_ERR_UNSUPPORTED, "m < n: reduce the transpose");
+  CK(h, cudaSetDevice(h->device));
+  int w = 0;
+  int rc = choose_strip(h, nb, ib, (int)sizeof(E), &w);
+  if (rc) return rc;
+  if (variant == BIDIAG_AUTO_VARIANT) {
+    try {
+      variant = bd::choose_variant((int)((m + nb - 1) / nb), (int)((n + nb - 1) / nb), tree, resources_of(h, nb, w),
+                                   nullptr, nullptr);
+    } catch (...) {
+      return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while choosing the variant");
+    }
+  }
+  std::shared_ptr<PlanDev> pd;
+  rc = get_plan(h, m, n, nb, ib, tree, variant, w, &pd);
+  if (rc) return rc;
+  bidiag_result* r = new (std::nothrow) bidiag_result();
+  if (!r) return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed");
+  r->h = h;
+  r->pd = pd;
+  r->m = m;
+  r->n = n;
+  r->nb = nb;
+  r->ib = ib;
+  r->tree = tree;
+  r->variant = variant;
+  r->p = pd->plan.p;
+  r->q = pd->plan.q;
+  r->ldab = nb + 1;
+  r->esize = (int)sizeof(E);
+  const size_t tile_elems = (size_t)nb * nb;
+  E *tiles = nullptr, *tiles2 = nullptr, *Tst = nullptr, *ab = nullptr;
+  rc = dev_alloc(h, &tiles, (size_t)r->p * r->q * tile_elems);
+  if (!rc && variant == BIDIAG_RBIDIAG) rc = dev_alloc(h, &tiles2, (size_t)r->q * r->q * tile_elems);
+  if (!rc) rc = dev_alloc(h, &Tst, (size_t)std::max(1, pd->plan.npanels) * ib * nb);
+  if (!rc) rc = dev_alloc(h, &ab, (size_t)(nb + 1) * n);
+  r->tiles = tiles;
+  r->tiles2 = tiles2;
+  r->T = Tst;
+  r->ab = ab;
+  if (rc) {
+    free_result_buffers(r);
+    delete r;
+    return rc;
+  }
+  auto bail = [&](int code) {
+    free_result_buffers(r);
+    delete r;
+    return code;
+  };
+  cudaError_t e = bd::launch_pack(d_A, lda, m, n, nb, tiles, r->p, r->q, h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "pack"));
+  if (r->tiles2) {
+    e = cudaMemsetAsync(r->tiles2, 0, (size_t)r->q * r->q * tile_elems * sizeof(E), h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+  }
+  const bool timed = h->timing != 0 || h->tracing != 0;
+  if (timed && !h->ev[0]) {
+    e = cudaEventCreate(&h->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
+  }
+  rc = run_exec(h, *pd, (int)pd->plan.dev.size(), r->tiles, (int64_t)r->p * r->q, r->tiles2,
+                r->tiles2 ? (int64_t)r->q * r->q : 0, nullptr, 0, r->T, pd->plan.npanels, nb, ib, w, (int)sizeof(E),
+                timed);
+  h->timed = timed;
+  if (rc) return bail(rc);
+  e = bd::launch_extract(tiles2 ? tiles2 : tiles, tiles2 ? r->q : r->p, nb, n, ab, r->ldab, h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "extract"));
+  h->live.insert(r);
+  *out = r;
   return BIDIAG_OK;
 }
 
@@ -376,6 +470,10 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
     case BIDIAG_OPT_TRACE:
       h->tracing = value != 0;
       return BIDIAG_OK;
+    case BIDIAG_OPT_F32_UPDATES:
+      if (value != 0 && value != 1) return -3;
+      h->f32_simt = (int)value;
+      return BIDIAG_OK;
     default:
       return -2;
   }
@@ -383,73 +481,12 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
 
 int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_t lda, int nb, int ib, int tree,
                 int variant, bidiag_result_t* out) {
-  if (!h) return -1;
-  if (m < 1) return fail(h, -2, "m < 1");
-  if (n < 1) return fail(h, -3, "n < 1");
-  if (!d_A) return fail(h, -4, "A is NULL");
-  if (lda < m) return fail(h, -5, "lda < m");
-  if (nb < 1 || nb > bd::kMaxNb) return fail(h, -6, "nb out of range");
-  if (ib < 1 || ib > std::min(nb, 64) || nb % ib) return fail(h, -7, "ib out of range or does not divide nb");
-  if (tree < 0 || tree > 3) return fail(h, -8, "unknown tree");
-  if (variant < 0 || variant > 1) return fail(h, -9, "unknown variant");
-  if (!out) return fail(h, -10, "out is NULL");
-  *out = nullptr;
-  if (m < n) return fail(h, BIDIAG_ERR_UNSUPPORTED, "m < n: reduce the transpose");
-  CK(h, cudaSetDevice(h->device));
-  int w = 0;
-  int rc = choose_strip(h, nb, ib, &w);
-  if (rc) return rc;
-  std::shared_ptr<PlanDev> pd;
-  rc = get_plan(h, m, n, nb, ib, tree, variant, w, &pd);
-  if (rc) return rc;
-  bidiag_result* r = new (std::nothrow) bidiag_result();
-  if (!r) return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed");
-  r->h = h;
-  r->pd = pd;
-  r->m = m;
-  r->n = n;
-  r->nb = nb;
-  r->ib = ib;
-  r->tree = tree;
-  r->variant = variant;
-  r->p = pd->plan.p;
-  r->q = pd->plan.q;
-  r->ldab = nb + 1;
-  const size_t tile_elems = (size_t)nb * nb;
-  if ((rc = dev_alloc(h, &r->tiles, (size_t)r->p * r->q * tile_elems)) ||
-      (variant == BIDIAG_RBIDIAG && (rc = dev_alloc(h, &r->tiles2, (size_t)r->q * r->q * tile_elems))) ||
-      (rc = dev_alloc(h, &r->T, (size_t)std::max(1, pd->plan.npanels) * ib * nb)) ||
-      (rc = dev_alloc(h, &r->ab, (size_t)(nb + 1) * n))) {
-    free_result_buffers(r);
-    delete r;
-    return rc;
-  }
-  auto bail = [&](int code) {
-    free_result_buffers(r);
-    delete r;
-    return code;
-  };
-  cudaError_t e = bd::launch_pack(d_A, lda, m, n, nb, r->tiles, r->p, r->q, h->stream);
-  if (e != cudaSuccess) return bail(cuda_fail(h, e, "pack"));
-  if (r->tiles2) {
-    e = cudaMemsetAsync(r->tiles2, 0, (size_t)r->q * r->q * tile_elems * sizeof(double), h->stream);
-    if (e != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
-  }
-  const bool timed = h->timing != 0 || h->tracing != 0;
-  if (timed && !h->ev[0]) {
-    e = cudaEventCreate(&h->ev[0]);
-    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
-    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
-  }
-  rc = run_exec(h, *pd, (int)pd->plan.dev.size(), r->tiles, (int64_t)r->p * r->q, r->tiles2,
-                r->tiles2 ? (int64_t)r->q * r->q : 0, nullptr, 0, r->T, pd->plan.npanels, nb, ib, w, timed);
-  h->timed = timed;
-  if (rc) return bail(rc);
-  e = bd::launch_extract(r->tiles2 ? r->tiles2 : r->tiles, r->tiles2 ? r->q : r->p, nb, n, r->ab, r->ldab, h->stream);
-  if (e != cudaSuccess) return bail(cuda_fail(h, e, "extract"));
-  h->live.insert(r);
-  *out = r;
-  return BIDIAG_OK;
+  return band_impl(h, m, n, d_A, lda, nb, ib, tree, variant, out);
+}
+
+int bidiag_band_f32(bidiag_handle h, int64_t m, int64_t n, const float* d_A, int64_t lda, int nb, int ib, int tree,
+                    int variant, bidiag_result_t* out) {
+  return band_impl(h, m, n, d_A, lda, nb, ib, tree, variant, out);
 }
 
 int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, int64_t lda, int nb, int ib, int tree,
@@ -492,7 +529,18 @@ int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, i
 
 int bidiag_result_band(bidiag_result_t r, const double** ab, int64_t* ldab, int64_t* n, int* nb) {
   if (!r) return -1;
-  if (ab) *ab = r->ab;
+  if (r->esize != 8) return BIDIAG_ERR_UNSUPPORTED;
+  if (ab) *ab = static_cast<const double*>(r->ab);
+  if (ldab) *ldab = r->ldab;
+  if (n) *n = r->n;
+  if (nb) *nb = r->nb;
+  return BIDIAG_OK;
+}
+
+int bidiag_result_band_f32(bidiag_result_t r, const float** ab, int64_t* ldab, int64_t* n, int* nb) {
+  if (!r) return -1;
+  if (r->esize != 4) return BIDIAG_ERR_UNSUPPORTED;
+  if (ab) *ab = static_cast<const float*>(r->ab);
   if (ldab) *ldab = r->ldab;
   if (n) *n = r->n;
   if (nb) *nb = r->nb;
@@ -512,6 +560,7 @@ int bidiag_result_reflectors(bidiag_result_t r, bidiag_reflectors* desc) {
   desc->tiles = r->tiles;
   desc->tiles2 = r->tiles2;
   desc->T = r->T;
+  desc->elem_bytes = r->esize;
   desc->tslot = r->pd->plan.tslot.data();
   desc->ntasks = (int64_t)r->pd->plan.tasks.size();
   desc->m = r->m;
@@ -529,6 +578,20 @@ int bidiag_apply_q(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols,
   if (!h) return -1;
   if (!r) return fail(h, -2, "result is NULL");
   if (r->h != h) return fail(h, -2, "result was made on another handle or its handle was destroyed");
+  if (r->esize != 8) return fail(h, -2, "FP32 result: use bidiag_apply_q_f32");
+  if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
+  if (ncols < 0) return fail(h, -4, "ncols < 0");
+  if (!d_C && ncols > 0) return fail(h, -5, "C is NULL");
+  if (ldc < r->m) return fail(h, -6, "ldc < m");
+  CK(h, cudaSetDevice(h->device));
+  return apply_side(h, r, true, trans, ncols, d_C, ldc);
+}
+
+int bidiag_apply_q_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t ncols, float* d_C, int64_t ldc) {
+  if (!h) return -1;
+  if (!r) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result was made on another handle or its handle was destroyed");
+  if (r->esize != 4) return fail(h, -2, "FP64 result: use bidiag_apply_q");
   if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
   if (ncols < 0) return fail(h, -4, "ncols < 0");
   if (!d_C && ncols > 0) return fail(h, -5, "C is NULL");
@@ -541,6 +604,20 @@ int bidiag_apply_p(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows,
   if (!h) return -1;
   if (!r) return fail(h, -2, "result is NULL");
   if (r->h != h) return fail(h, -2, "result was made on another handle or its handle was destroyed");
+  if (r->esize != 8) return fail(h, -2, "FP32 result: use bidiag_apply_p_f32");
+  if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
+  if (nrows < 0) return fail(h, -4, "nrows < 0");
+  if (!d_C && nrows > 0) return fail(h, -5, "C is NULL");
+  if (ldc < std::max<int64_t>(1, nrows)) return fail(h, -6, "ldc < nrows");
+  CK(h, cudaSetDevice(h->device));
+  return apply_side(h, r, false, trans, nrows, d_C, ldc);
+}
+
+int bidiag_apply_p_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, float* d_C, int64_t ldc) {
+  if (!h) return -1;
+  if (!r) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result was made on another handle or its handle was destroyed");
+  if (r->esize != 4) return fail(h, -2, "FP64 result: use bidiag_apply_p");
   if (trans != 0 && trans != 1) return fail(h, -3, "trans must be 0 or 1");
   if (nrows < 0) return fail(h, -4, "nrows < 0");
   if (!d_C && nrows > 0) return fail(h, -5, "C is NULL");
@@ -660,6 +737,19 @@ int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resou
       dump_tasks(ts, d);
       std::copy(d.begin(), d.end(), tasks);
     }
+  } catch (...) {
+    return BIDIAG_ERR_NOMEM;
+  }
+  return BIDIAG_OK;
+}
+
+int bidiag_plan_choose_variant(int64_t p, int64_t q, int tree, int64_t resources, int* variant, int64_t* cp_bidiag,
+                               int64_t* cp_rbidiag) {
+  if (p < 1 || q < 1 || q > p) return -1;
+  if (tree < 0 || tree > 3) return -3;
+  if (!variant) return -5;
+  try {
+    *variant = bd::choose_variant((int)p, (int)q, tree, resources, cp_bidiag, cp_rbidiag);
   } catch (...) {
     return BIDIAG_ERR_NOMEM;
   }

@@ -22,32 +22,40 @@ struct ExecParams {
   int* done;
   int* head;
   int* err;
-  double* buf[3];       // tile buffers: A tiles, R copy (R-BiDiag), apply target
+  void* buf[3];         // tile buffers (element type by esize): A tiles, R copy (R-BiDiag), apply target
   int64_t ntiles[3];
-  double* T;
+  void* T;
   int32_t npanels;
   int nb, ib, w;        // tile size, inner blocking, strip width
   uint64_t wait_ns;
   int64_t* trace;       // optional: 4 int64 per task (start ns, end ns, SM id, op), queue order
+  int esize;            // 8: FP64 tiles; 4: FP32 tiles (split-precision updates)
+  int f32_simt;         // FP32 tiles only: 1 = updates by FP32 FFMA instead of three TF32 tensor-core products
 };
 
-// Shared memory (bytes) the executor needs for (nb, ib, w).
-size_t exec_smem_bytes(int nb, int ib, int w);
+// Shared memory (bytes) the executor needs for (nb, ib, w) and element size esize (8 or 4).
+size_t exec_smem_bytes(int nb, int ib, int w, int esize);
 // Column-strip width of the update sub-tasks: a multiple of ib, at most nb, as close to `preferred`
 // as the shared-memory limit allows; 0 if even w = ib does not fit.
-int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit);
+int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit, int esize);
 
 cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st);
-cudaError_t exec_set_smem(size_t smem);
-int exec_max_ctas_per_sm(size_t smem);
+cudaError_t exec_set_smem(size_t smem, int esize);
+int exec_max_ctas_per_sm(size_t smem, int esize);
 
 // Column-major (ld) matrix <-> zero-padded tile buffer (grid of rows_t x cols_t tiles of nb x nb).
 cudaError_t launch_pack(const double* A, int64_t lda, int64_t m, int64_t n, int nb, double* tiles, int64_t rows_t,
                         int64_t cols_t, cudaStream_t st);
+cudaError_t launch_pack(const float* A, int64_t lda, int64_t m, int64_t n, int nb, float* tiles, int64_t rows_t,
+                        int64_t cols_t, cudaStream_t st);
 cudaError_t launch_unpack(const double* tiles, int64_t rows_t, int nb, int64_t m, int64_t n, double* A, int64_t lda,
+                          cudaStream_t st);
+cudaError_t launch_unpack(const float* tiles, int64_t rows_t, int nb, int64_t m, int64_t n, float* A, int64_t lda,
                           cudaStream_t st);
 // Band extraction: ab((nb+1) x n, ld ldab) from the tile buffer (grid rows rows_t).
 cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
+                           cudaStream_t st);
+cudaError_t launch_extract(const float* tiles, int64_t rows_t, int nb, int64_t n, float* ab, int64_t ldab,
                            cudaStream_t st);
 
 }  // namespace bd

@@ -68,9 +68,9 @@ extern "C" int bidiag_band_noalloc(int64_t m, int64_t n, const double* d_A, int6
   if (e != cudaSuccess) return BIDIAG_ERR_CUDA;
   if (dev >= kMaxDevices) return BIDIAG_ERR_UNSUPPORTED;
 
-  const int w = bd::choose_strip_width(nb, ib, 32, (size_t)optin - 64);
+  const int w = bd::choose_strip_width(nb, ib, 32, (size_t)optin - 64, 8);
   if (!w) return BIDIAG_ERR_UNSUPPORTED;
-  const size_t smem = bd::exec_smem_bytes(nb, ib, w);
+  const size_t smem = bd::exec_smem_bytes(nb, ib, w, 8);
 
   // The task program is planned on the host (host memory only).
   bd::Plan pl;
@@ -135,8 +135,9 @@ extern "C" int bidiag_band_noalloc(int64_t m, int64_t n, const double* d_A, int6
     prm.w = w;
     const char* wl = std::getenv("BIDIAG_WAIT_LIMIT_NS");
     prm.wait_ns = wl ? std::strtoull(wl, nullptr, 10) : 20000000000ull;
-    if ((e = bd::exec_set_smem(smem)) != cudaSuccess) return cuda_status(e);
-    int per_sm = bd::exec_max_ctas_per_sm(smem);
+    prm.esize = 8;
+    if ((e = bd::exec_set_smem(smem, 8)) != cudaSuccess) return cuda_status(e);
+    int per_sm = bd::exec_max_ctas_per_sm(smem, 8);
     if (per_sm < 1) per_sm = 1;
     const int64_t grid = (int64_t)nsm * per_sm < (int64_t)ntask ? (int64_t)nsm * per_sm : (int64_t)ntask;
     if ((e = bd::launch_exec(prm, (int)grid, smem, st)) != cudaSuccess) return cuda_status(e);

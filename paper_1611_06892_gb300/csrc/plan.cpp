@@ -362,6 +362,16 @@ void make_dag(const std::vector<Task>& tasks, int p, int q, int variant, std::ve
   if (cp) *cp = best;
 }
 
+int choose_variant(int p, int q, int tree, int64_t R, int64_t* cp_bidiag, int64_t* cp_rbidiag) {
+  const int t = tree == AUTO ? GREEDY : tree;
+  int64_t cb = 0, cr = 0;
+  make_dag(make_tasks(p, q, t, V_BIDIAG, R), p, q, V_BIDIAG, nullptr, nullptr, &cb);
+  make_dag(make_tasks(p, q, t, V_RBIDIAG, R), p, q, V_RBIDIAG, nullptr, nullptr, &cr);
+  if (cp_bidiag) *cp_bidiag = cb;
+  if (cp_rbidiag) *cp_rbidiag = cr;
+  return cr < cb ? V_RBIDIAG : V_BIDIAG;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Device program.
 //  * A panel task (GEQRT / TSQRT / TTQRT) becomes, for each inner block b of ib reflectors, a factor

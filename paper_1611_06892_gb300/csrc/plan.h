@@ -59,6 +59,10 @@ std::vector<Task> make_tasks(int p, int q, int tree, int variant, int64_t resour
 // Task DAG: predecessor lists, levels and the Table 1 critical path.
 void make_dag(const std::vector<Task>& tasks, int p, int q, int variant,
               std::vector<std::vector<int32_t>>* preds, std::vector<int32_t>* level, int64_t* cp);
+// Variant with the shorter critical path (Sec. 4.3.3: BiDiag for square-ish, R-BiDiag for tall
+// matrices, switching at p/q = delta_s).  The Auto tree is compared through Greedy, whose critical path
+// the paper studies (Auto's has no meaning without a resource model).  Ties keep BiDiag.
+int choose_variant(int p, int q, int tree, int64_t resources, int64_t* cp_bidiag, int64_t* cp_rbidiag);
 // Full plan for a reduction: tasks, DAG, device sub-tasks ordered by critical-path priority.
 void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
                 int strip_w);

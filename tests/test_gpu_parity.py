@@ -170,7 +170,7 @@ def test_argument_errors(handle, torch_mod):
     assert lib.bidiag_band(handle.h, 10, 8, p, 10, 300, 2, 0, 0, ctypes.byref(r)) == -6
     assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 3, 0, 0, ctypes.byref(r)) == -7
     assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 9, 0, ctypes.byref(r)) == -8
-    assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 0, 2, ctypes.byref(r)) == -9
+    assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 0, 3, ctypes.byref(r)) == -9
     assert lib.bidiag_band(handle.h, 8, 10, p, 10, 4, 2, 0, 0, ctypes.byref(r)) == G.ERR_UNSUPPORTED
     # shared memory limit: nb = 256 with ib = 64 does not fit
     big = to_dev(torch_mod, inputs.gaussian(256, 256, seed=2))
@@ -196,3 +196,13 @@ def test_wait_timeout_is_reported(handle, torch_mod):
     ref = OB.bidiag_band(A_h, 16, 4, T.GREEDY, T.BIDIAG)
     assert np.abs(res.band().cpu().numpy() - ref["ab"]).max() <= 1e-12 * np.linalg.norm(A_h)
     h.close()
+
+
+def test_auto_variant(handle, torch_mod):
+    """variant = auto runs R-BiDiag on a tall matrix and BiDiag on a square one (critical-path switch)."""
+    for (m, n, expect) in ((640, 64, T.RBIDIAG), (96, 96, T.BIDIAG)):
+        A = inputs.gaussian(m, n, seed=m + n)
+        res_g = gpu_reduce(handle, torch_mod, A, 16, 4, "greedy", "auto")
+        assert res_g.desc.variant == expect
+        res_o = OB.bidiag_band(A, 16, 4, T.GREEDY, expect)
+        compare(res_g, res_o, A, 16, 4)

@@ -96,3 +96,18 @@ def test_planner_argument_errors():
     assert lib.bidiag_plan_tasks(4, 3, 7, 0, 1, None, None, 0, ctypes.byref(cnt), None) == -3
     assert lib.bidiag_plan_tasks(4, 3, 0, 5, 1, None, None, 0, ctypes.byref(cnt), None) == -4
     assert lib.bidiag_plan_eliminations(4, 3, 0, 0, 1, None, 0, None) == -8
+
+
+def test_choose_variant_follows_critical_paths():
+    """BIDIAG_AUTO_VARIANT picks the variant with the shorter critical path (Sec. 4.3.3): BiDiag for
+    square matrices, R-BiDiag for tall ones, switching between p = 566 and 568 for q = 100."""
+    for (p, q) in ((1, 1), (5, 5), (9, 4), (13, 3), (17, 2), (40, 40)):
+        for tree in (T.FLATTS, T.FLATTT, T.GREEDY):
+            v, cb, cr = G.bidiag_plan_choose_variant(p, q, tree, 1)
+            assert cb == T.critical_path(p, q, tree, T.BIDIAG)
+            assert cr == T.critical_path(p, q, tree, T.RBIDIAG)
+            assert v == (T.RBIDIAG if cr < cb else T.BIDIAG)
+    assert G.bidiag_plan_choose_variant(32, 32, T.AUTO, 19)[0] == T.BIDIAG
+    assert G.bidiag_plan_choose_variant(256, 4, T.AUTO, 19)[0] == T.RBIDIAG
+    assert G.bidiag_plan_choose_variant(560, 100, T.GREEDY, 1)[0] == T.BIDIAG
+    assert G.bidiag_plan_choose_variant(575, 100, T.GREEDY, 1)[0] == T.RBIDIAG
