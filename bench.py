@@ -45,6 +45,9 @@ WORKLOADS = {
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock/SM (4 flops) x
 # 2070 MHz = 1258.6 GFLOP/s (a DFMA loop measured 1.20 TFLOP/s, cuBLAS DGEMM 1.10, FP64 MMA 1.05).
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+# Split-FP32 form: the updates are three TF32 tensor-core products per useful product.  TF32 dense peak
+# = measured bf16 peak x nominal TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s); one useful flop costs three.
+TF32_RATIO = 1.1 / 2.25
 # DRAM bytes per executor launch from the ncu capture summarised under profiles/ (None until taken
 # for the current kernel).
 EXEC_TRAFFIC_BYTES = None
@@ -191,6 +194,8 @@ def main():
     ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS))
     ap.add_argument("--tree", default="auto", choices=("flatts", "flattt", "greedy", "auto"))
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--precision", default="f64", choices=("f64", "f32"),
+                    help="f32: FP32 storage with 3xTF32 tensor-core updates and FP64 reflector norms")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", default=None)
@@ -219,13 +224,15 @@ def main():
         w["resources"] = max(1, torch.cuda.get_device_properties(local).multi_processor_count * 32 // w["nb"])
     m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
     flops = metric_flops(m, n)
-    config = {"workload": w["desc"] + f", tree={args.tree}", "m": m, "n": n, "nb": nb, "ib": ib,
+    f32 = args.precision == "f32"
+    desc = w["desc"].replace("FP64", "FP32 storage (3xTF32 updates)") if f32 else w["desc"]
+    config = {"workload": desc + f", tree={args.tree}", "m": m, "n": n, "nb": nb, "ib": ib,
               "tree": args.tree, "variant": w["variant"], "auto_resources": w["resources"],
               "l2": f"input {m * n * 8 / 2**20:.0f} MiB > 129 MB L2 (no flush needed)" if m * n * 8 > 129e6
               else "input smaller than L2"}
     base = {"metric": "GE2BND TFLOP/s (4mn^2 - 4n^3/3 flops)", "unit": "TFLOP/s", "higher_is_better": True,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config}
+            "vs_baseline": None, "dtype": "f32" if f32 else "f64", "data": "synthetic", "config": config}
 
     if args.impl == "reference":
         # the plain CPU oracle on bounded samples of the same workload; rank 0 only
@@ -255,6 +262,8 @@ def main():
     G.load_library()
 
     A = make_input(w, rank, device)
+    if f32:
+        A = A.float().t().contiguous().t()
     h = G.Handle(device=local)
     h.set_option(G.OPT_TIMING, 1)
     h.set_option(G.OPT_AUTO_RESOURCES, w["resources"])
@@ -289,7 +298,7 @@ def main():
     A_host.copy_(A)
     ab_host = torch.empty((n, nb + 1), dtype=torch.float64, pin_memory=True).t()
     e2e_t = []
-    for _ in range(args.e2e_steps):
+    for _ in range(0 if f32 else args.e2e_steps):
         barrier(world)
         t0 = time.perf_counter()
         G.bidiag_band_host(h.h, m, n, A_host.data_ptr(), m, nb, ib, G.TREES[args.tree], G.VARIANTS[w["variant"]],
@@ -299,15 +308,26 @@ def main():
 
     exec_mean = statistics.mean(exec_ms)
     achieved = flops / (exec_mean * 1e-3) / 1e9
+    if f32:
+        bf16 = 1926.3
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                bf16 = json.load(fh).get("bf16_tflops", bf16)
+        except OSError:
+            pass
+        peak, bound, unit = bf16 * TF32_RATIO * 1e3 / 3.0, "tensor", "GFLOP/s"
+        peak_src = "measured bf16 x 1.1/2.25 (TF32) / 3 products per useful flop"
+    else:
+        peak, bound, unit = FP64_PEAK_GFLOPS, "alu", "GFLOP/s"
+        peak_src = "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
     line = dict(base, value=value, ms_per_step=ms_per_step,
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (nb + 1) * n * 8},
-                roofline={"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": EXEC_TRAFFIC_BYTES,
-                          "kernel": "exec_kernel (persistent dataflow executor)",
-                          "peak_source": "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"},
+                roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                          "frac": achieved / peak, "traffic": None if f32 else EXEC_TRAFFIC_BYTES,
+                          "kernel": "exec_kernel (persistent dataflow executor)", "peak_source": peak_src},
                 exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
-    if world == 1 and rank == 0 and not args.no_cpu:
+    if world == 1 and rank == 0 and not args.no_cpu and not f32:
         A_np = A.cpu().numpy()
         r = run_cpu_sample_subprocess(A_np, w, args.tree, CPU_SAMPLE_SECONDS)
         line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
