@@ -93,6 +93,7 @@ typedef struct bidiag_reflectors {
   int64_t m, n;
   int32_t nb, ib, p, q, npanels, variant;
   int32_t elem_bytes;          /* 8: tiles and T in FP64; 4: in FP32 (bidiag_band_f32) */
+  int32_t tree;                /* tree the reduction used */
 } bidiag_reflectors;
 
 /* Creates a handle bound to CUDA device `device` and stream `cuda_stream` (a cudaStream_t; NULL =
@@ -125,6 +126,32 @@ int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_
  */
 int bidiag_band_f32(bidiag_handle h, int64_t m, int64_t n, const float* d_A, int64_t lda,
                     int nb, int ib, int tree, int variant, bidiag_result_t* out);
+
+/*
+ * Batched form: reduces `count` independent matrices (each m[b] x n[b], m >= n, column-major at device
+ * pointer d_A[b] with leading dimension lda[b]) in ONE persistent launch.  Per-matrix tile size nb[b],
+ * inner blocking ib[b], tree[b] and variant[b] (BIDIAG_AUTO_VARIANT allowed); when nb is NULL the
+ * library's autotuner (bidiag_autotune) picks all four per matrix; when only ib / tree / variant is NULL
+ * the defaults are min(nb, 32), Auto and BIDIAG_AUTO_VARIANT.  The host arrays are read during the call.
+ * out[b] receives one result per matrix (free each with bidiag_result_free; they share one device
+ * allocation that is released with the last of them) usable like any other result (band, tasks,
+ * reflectors, apply_q / apply_p).  Errors: -2 count, -3 a matrix's sizes or pointer, -7 nb/ib, -9 tree or
+ * variant, -11 out; the text names the matrix.  No counterpart in the paper's experiments (Sec. 5's
+ * runtime reduces one matrix); the per-matrix algorithm is the same.
+ */
+int bidiag_band_batched(bidiag_handle h, int64_t count, const int64_t* m, const int64_t* n,
+                        const double* const* d_A, const int64_t* lda, const int* nb, const int* ib,
+                        const int* tree, const int* variant, bidiag_result_t* out);
+/* The same for FP32 storage (split-precision form of bidiag_band_f32). */
+int bidiag_band_batched_f32(bidiag_handle h, int64_t count, const int64_t* m, const int64_t* n,
+                            const float* const* d_A, const int64_t* lda, const int* nb, const int* ib,
+                            const int* tree, const int* variant, bidiag_result_t* out);
+
+/* Autotuner of the batched form (host only): for an m x n matrix on a device with nsm SMs, picks nb in
+ * {32, 64, 128} (ib = 16 for nb = 32, else 32) minimising padded Table 1 work / (nsm x efficiency of
+ * that tile size) + critical path, the variant by critical path (Sec. 4.3.3), and the Auto tree
+ * (Greedy when the panel has at most two tiles).  Errors: -1 sizes, -3 nsm, -4 NULL output. */
+int bidiag_autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant);
 
 /*
  * Same reduction for host buffers: copies h_A (column-major, lda) to the device, reduces it, copies the

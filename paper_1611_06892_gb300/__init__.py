@@ -41,7 +41,7 @@ class Reflectors(ctypes.Structure):
                 ("tslot", ctypes.POINTER(ctypes.c_int32)), ("ntasks", ctypes.c_int64),
                 ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32),
                 ("p", ctypes.c_int32), ("q", ctypes.c_int32), ("npanels", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("elem_bytes", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("elem_bytes", ctypes.c_int32), ("tree", ctypes.c_int32)]
 
 
 def load_library(path=LIB_PATH):
@@ -60,6 +60,11 @@ def load_library(path=LIB_PATH):
         "bidiag_band": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, P(vp)]),
         "bidiag_band_host": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, P(vp)]),
         "bidiag_band_f32": (cint, [vp, i64, i64, vp, i64, cint, cint, cint, cint, P(vp)]),
+        "bidiag_band_batched": (cint, [vp, i64, P(i64), P(i64), P(vp), P(i64), P(cint), P(cint), P(cint), P(cint),
+                                       P(vp)]),
+        "bidiag_band_batched_f32": (cint, [vp, i64, P(i64), P(i64), P(vp), P(i64), P(cint), P(cint), P(cint),
+                                           P(cint), P(vp)]),
+        "bidiag_autotune": (cint, [i64, i64, cint, P(cint), P(cint), P(cint), P(cint)]),
         "bidiag_result_band_f32": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
         "bidiag_apply_q_f32": (cint, [vp, vp, cint, i64, vp, i64]),
         "bidiag_apply_p_f32": (cint, [vp, vp, cint, i64, vp, i64]),
@@ -116,6 +121,13 @@ def bidiag_band_f32(h, m, n, d_A, lda, nb, ib, tree, variant):
     r = ctypes.c_void_p()
     _check(h, load_library().bidiag_band_f32(h, m, n, d_A, lda, nb, ib, tree, variant, ctypes.byref(r)))
     return r
+
+
+def bidiag_autotune(m, n, nsm):
+    """(nb, ib, tree, variant) the batched form's autotuner picks for an m x n matrix."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(None, load_library().bidiag_autotune(m, n, nsm, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab, keep=False):
@@ -264,6 +276,34 @@ class Handle:
         fn = bidiag_band_f32 if A.dtype == torch.float32 else bidiag_band
         r = fn(self.h, m, n, ctypes.c_void_p(Ac.data_ptr()), lda, nb, ib, tree, variant)
         return Result(self, r, keep=Ac)
+
+    def band_batched(self, As, nb=None, ib=None, tree=None, variant=None):
+        """Reduces a list of matrices (all float64 or all float32) in one persistent launch.
+
+        nb / ib / tree / variant: None (autotuned or default) or a sequence with one entry per matrix
+        (tree and variant entries may be names)."""
+        import torch
+        count = len(As)
+        f32 = count > 0 and As[0].dtype == torch.float32
+        cols = [_colmajor(A) for A in As]
+        I64 = ctypes.c_int64 * count
+        CI = ctypes.c_int * count
+        m = I64(*[A.shape[0] for A in As])
+        n = I64(*[A.shape[1] for A in As])
+        lda = I64(*[ld for _, ld in cols])
+        ptrs = (ctypes.c_void_p * count)(*[Ac.data_ptr() for Ac, _ in cols])
+
+        def arr(v, names=None):
+            if v is None:
+                return None
+            return CI(*[(names[x] if isinstance(x, str) else x) for x in v])
+
+        out = (ctypes.c_void_p * count)()
+        lib = load_library()
+        fn = lib.bidiag_band_batched_f32 if f32 else lib.bidiag_band_batched
+        _check(self.h, fn(self.h, count, m, n, ptrs, lda, arr(nb), arr(ib), arr(tree, TREES), arr(variant, VARIANTS),
+                          out))
+        return [Result(self, ctypes.c_void_p(out[b]), keep=cols[b][0]) for b in range(count)]
 
     def sync(self):
         bidiag_sync(self.h)

@@ -36,6 +36,20 @@ struct PlanDev {
 
 using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int>;
 
+// Device storage shared by the results of one batched reduction (freed with the last of them).
+struct BatchStore {
+  void* tiles = nullptr;
+  void* tiles2 = nullptr;
+  void* T = nullptr;
+  void* d_mats = nullptr;
+  void* d_desc = nullptr;
+  PlanDev prog;          // the merged device program
+  ~BatchStore() {
+    for (void* p : {tiles, tiles2, T, d_mats, d_desc})
+      if (p) cudaFree(p);
+  }
+};
+
 }  // namespace
 
 struct bidiag_ctx {
@@ -66,6 +80,7 @@ struct bidiag_result {
   int64_t m = 0, n = 0;
   int nb = 0, ib = 0, tree = 0, variant = 0, p = 0, q = 0;
   int esize = 8;                  // 8: FP64 storage, 4: FP32 storage (split-precision updates)
+  std::shared_ptr<BatchStore> store;   // batched results: tiles, tiles2 and T point into it
   void* tiles = nullptr;
   void* tiles2 = nullptr;
   void* T = nullptr;
@@ -122,9 +137,10 @@ int64_t resources_of(bidiag_handle h, int nb, int w) {
 
 // Executor launch of a program held in pd with the given buffers.
 int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n0, void* b1, int64_t n1, void* b2,
-             int64_t n2, void* T, int npanels, int nb, int ib, int w, int esize, bool timed = false) {
+             int64_t n2, void* T, int npanels, int nb, int ib, int w, int esize, bool timed = false,
+             const bd::MatInfo* d_mats = nullptr, int nmats = 0, size_t smem_batch = 0) {
   if (ntasks == 0) return BIDIAG_OK;
-  const size_t smem = bd::exec_smem_bytes(nb, ib, w, esize);
+  const size_t smem = d_mats ? smem_batch : bd::exec_smem_bytes(nb, ib, w, esize);
   CK(h, bd::exec_set_smem(smem, esize));
   const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem, esize));
   bd::ExecParams prm{};
@@ -146,6 +162,8 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   prm.wait_ns = h->wait_ns;
   prm.esize = esize;
   prm.f32_simt = h->f32_simt;
+  prm.mats = d_mats;
+  prm.nmats = nmats;
   prm.trace = nullptr;
   if (timed && h->tracing) {
     if (h->trace_cap < ntasks) {
@@ -234,11 +252,14 @@ int dev_alloc(bidiag_handle h, T** p, size_t count) {
 
 void free_result_buffers(bidiag_result* r) {
   cudaStream_t s = r->h ? r->h->stream : nullptr;
-  if (r->tiles) cudaFreeAsync(r->tiles, s);
-  if (r->tiles2) cudaFreeAsync(r->tiles2, s);
-  if (r->T) cudaFreeAsync(r->T, s);
+  if (!r->store) {
+    if (r->tiles) cudaFreeAsync(r->tiles, s);
+    if (r->tiles2) cudaFreeAsync(r->tiles2, s);
+    if (r->T) cudaFreeAsync(r->T, s);
+  }
   if (r->ab) cudaFreeAsync(r->ab, s);
   r->tiles = r->tiles2 = r->T = r->ab = nullptr;
+  r->store.reset();
 }
 
 // Replays the panel tasks of one side (QR side: left = true; LQ side: left = false) on a tiled copy of C.
@@ -416,6 +437,179 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   return BIDIAG_OK;
 }
 
+
+// Batched form: `count` independent reductions in one persistent launch.  Each matrix keeps its own
+// plan (tile size, tree, variant); the device programs are merged by critical-path priority and every
+// sub-task finds its matrix's offsets and tile size in a per-matrix table.
+template <typename E>
+int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const int64_t* n, const E* const* d_A,
+                      const int64_t* lda, const int* nb_in, const int* ib_in, const int* tree_in, const int* var_in,
+                      bidiag_result_t* out) {
+  if (!h) return -1;
+  if (count < 0) return fail(h, -2, "count < 0");
+  if (count == 0) return BIDIAG_OK;
+  if (!m || !n || !d_A || !lda) return fail(h, -3, "m, n, A and lda arrays are required");
+  if (!out) return fail(h, -11, "out is NULL");
+  CK(h, cudaSetDevice(h->device));
+  const int esize = (int)sizeof(E);
+  struct One {
+    int nb, ib, tree, variant, w;
+    std::shared_ptr<PlanDev> pd;
+  };
+  std::vector<One> mats((size_t)count);
+  size_t smem = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    out[b] = nullptr;
+    if (m[b] < 1 || n[b] < 1 || m[b] < n[b] || lda[b] < m[b] || !d_A[b])
+      return fail(h, -3, "matrix " + std::to_string(b) + ": need m >= n >= 1, lda >= m and A != NULL");
+    One& o = mats[(size_t)b];
+    if (nb_in) {
+      o.nb = nb_in[b];
+      o.ib = ib_in ? ib_in[b] : std::min(o.nb, 32);
+      o.tree = tree_in ? tree_in[b] : BIDIAG_AUTO;
+      o.variant = var_in ? var_in[b] : BIDIAG_AUTO_VARIANT;
+    } else {
+      try {
+        bd::autotune(m[b], n[b], h->nsm, &o.nb, &o.ib, &o.tree, &o.variant);
+      } catch (...) {
+        return fail(h, BIDIAG_ERR_NOMEM, "autotuner failed");
+      }
+      if (tree_in) o.tree = tree_in[b];
+      if (var_in) o.variant = var_in[b];
+    }
+    if (o.nb < 1 || o.nb > bd::kMaxNb || o.ib < 1 || o.ib > std::min(o.nb, 64) || o.nb % o.ib)
+      return fail(h, -7, "matrix " + std::to_string(b) + ": invalid nb / ib");
+    if (o.tree < 0 || o.tree > 3 || o.variant < 0 || o.variant > 2)
+      return fail(h, -9, "matrix " + std::to_string(b) + ": invalid tree / variant");
+    o.w = bd::choose_strip_width(o.nb, o.ib, h->strip_w, h->smem_optin, esize);
+    if (!o.w) return fail(h, BIDIAG_ERR_UNSUPPORTED, "matrix " + std::to_string(b) + ": shared memory");
+    smem = std::max(smem, bd::exec_smem_bytes(o.nb, o.ib, o.w, esize));
+    const int p = (int)((m[b] + o.nb - 1) / o.nb), q = (int)((n[b] + o.nb - 1) / o.nb);
+    const int64_t R = resources_of(h, o.nb, o.w);
+    try {
+      if (o.variant == BIDIAG_AUTO_VARIANT) o.variant = bd::choose_variant(p, q, o.tree, R, nullptr, nullptr);
+      o.pd = std::make_shared<PlanDev>();
+      bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w);
+      dump_tasks(o.pd->plan.tasks, o.pd->dump);
+    } catch (const std::bad_alloc&) {
+      return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning");
+    } catch (const std::exception& ex) {
+      return fail(h, BIDIAG_ERR_UNSUPPORTED, std::string("planner: ") + ex.what());
+    }
+  }
+  // storage layout
+  std::vector<bd::MatInfo> info((size_t)count);
+  int64_t tot0 = 0, tot1 = 0, totT = 0, tiles_all = 0, cols_all = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    const bd::Plan& pl = mats[(size_t)b].pd->plan;
+    bd::MatInfo& mi = info[(size_t)b];
+    const int64_t t2 = (int64_t)pl.nb * pl.nb;
+    mi.off[0] = tot0;
+    mi.ntiles[0] = (int64_t)pl.p * pl.q;
+    tot0 += mi.ntiles[0] * t2;
+    mi.off[1] = tot1;
+    mi.ntiles[1] = pl.variant == BIDIAG_RBIDIAG ? (int64_t)pl.q * pl.q : 0;
+    tot1 += mi.ntiles[1] * t2;
+    mi.offT = totT;
+    totT += (int64_t)std::max(1, pl.npanels) * pl.ib * pl.nb;
+    mi.nb = pl.nb;
+    mi.ib = pl.ib;
+    mi.w = pl.strip_w;
+    mi.npanels = pl.npanels;
+    mi.pad = 0;
+    tiles_all += mi.ntiles[0];
+    cols_all += n[b];
+  }
+  auto store = std::make_shared<BatchStore>();
+  std::vector<const bd::Plan*> plans;
+  for (auto& o : mats) plans.push_back(&o.pd->plan);
+  std::vector<bd::DevTask> dev;
+  std::vector<int32_t> deps;
+  try {
+    bd::merge_programs(plans, &dev, &deps);
+  } catch (const std::exception& ex) {
+    return fail(h, BIDIAG_ERR_UNSUPPORTED, std::string("merge: ") + ex.what());
+  }
+  int rc = upload_program(h, store->prog, dev, deps, 1);
+  if (rc) return rc;
+  CK(h, cudaMalloc(&store->tiles, (size_t)std::max<int64_t>(1, tot0) * esize));
+  if (tot1) CK(h, cudaMalloc(&store->tiles2, (size_t)tot1 * esize));
+  CK(h, cudaMalloc(&store->T, (size_t)std::max<int64_t>(1, totT) * esize));
+  CK(h, cudaMalloc(&store->d_mats, sizeof(bd::MatInfo) * (size_t)count));
+  CK(h, cudaMalloc(&store->d_desc, sizeof(bd::PackDesc) * 2 * (size_t)count));
+  // results and their bands
+  std::vector<bidiag_result*> res((size_t)count, nullptr);
+  auto bail = [&](int code) {
+    for (bidiag_result* r : res)
+      if (r) {
+        free_result_buffers(r);
+        delete r;
+      }
+    return code;
+  };
+  std::vector<bd::PackDesc> pk((size_t)count), ex((size_t)count);
+  int64_t first_tile = 0, first_col = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    const bd::Plan& pl = mats[(size_t)b].pd->plan;
+    bidiag_result* r = new (std::nothrow) bidiag_result();
+    if (!r) return bail(fail(h, BIDIAG_ERR_NOMEM, "host allocation failed"));
+    res[(size_t)b] = r;
+    r->h = h;
+    r->pd = mats[(size_t)b].pd;
+    r->m = m[b];
+    r->n = n[b];
+    r->nb = pl.nb;
+    r->ib = pl.ib;
+    r->tree = pl.tree;
+    r->variant = pl.variant;
+    r->p = pl.p;
+    r->q = pl.q;
+    r->esize = esize;
+    r->ldab = pl.nb + 1;
+    r->store = store;
+    r->tiles = static_cast<E*>(store->tiles) + info[(size_t)b].off[0];
+    r->tiles2 = info[(size_t)b].ntiles[1] ? static_cast<E*>(store->tiles2) + info[(size_t)b].off[1] : nullptr;
+    r->T = static_cast<E*>(store->T) + info[(size_t)b].offT;
+    E* ab = nullptr;
+    if ((rc = dev_alloc(h, &ab, (size_t)(pl.nb + 1) * n[b]))) return bail(rc);
+    r->ab = ab;
+    pk[(size_t)b] = bd::PackDesc{d_A[b], r->tiles, lda[b], m[b], n[b], (int64_t)pl.p, first_tile, pl.nb, 0};
+    ex[(size_t)b] = bd::PackDesc{r->tiles2 ? r->tiles2 : r->tiles, ab, r->ldab, 0, n[b],
+                                 (int64_t)(r->tiles2 ? pl.q : pl.p), first_col, pl.nb, 0};
+    first_tile += (int64_t)pl.p * pl.q;
+    first_col += n[b];
+  }
+  bd::PackDesc* d_pk = static_cast<bd::PackDesc*>(store->d_desc);
+  bd::PackDesc* d_ex = d_pk + count;
+  cudaError_t e = cudaMemcpyAsync(store->d_mats, info.data(), sizeof(bd::MatInfo) * (size_t)count,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_pk, pk.data(), sizeof(bd::PackDesc) * (size_t)count, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_ex, ex.data(), sizeof(bd::PackDesc) * (size_t)count, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && tot1) e = cudaMemsetAsync(store->tiles2, 0, (size_t)tot1 * esize, h->stream);
+  if (e == cudaSuccess) e = bd::launch_pack_batched(d_pk, (int)count, tiles_all, esize, h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "batched pack"));
+  const bool timed = h->timing != 0 || h->tracing != 0;
+  if (timed && !h->ev[0]) {
+    e = cudaEventCreate(&h->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
+  }
+  rc = run_exec(h, store->prog, (int)dev.size(), store->tiles, tiles_all, store->tiles2, tot1 ? 1 : 0, nullptr, 0,
+                store->T, 0, 0, 1, 1, esize, timed, static_cast<const bd::MatInfo*>(store->d_mats), (int)count,
+                smem);
+  if (rc) return bail(rc);
+  h->timed = timed;
+  e = bd::launch_extract_batched(d_ex, (int)count, cols_all, esize, h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(h, e, "batched extract"));
+  for (int64_t b = 0; b < count; ++b) {
+    h->live.insert(res[(size_t)b]);
+    out[b] = res[(size_t)b];
+  }
+  return BIDIAG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -487,6 +681,30 @@ int bidiag_band(bidiag_handle h, int64_t m, int64_t n, const double* d_A, int64_
 int bidiag_band_f32(bidiag_handle h, int64_t m, int64_t n, const float* d_A, int64_t lda, int nb, int ib, int tree,
                     int variant, bidiag_result_t* out) {
   return band_impl(h, m, n, d_A, lda, nb, ib, tree, variant, out);
+}
+
+int bidiag_band_batched(bidiag_handle h, int64_t count, const int64_t* m, const int64_t* n, const double* const* d_A,
+                        const int64_t* lda, const int* nb, const int* ib, const int* tree, const int* variant,
+                        bidiag_result_t* out) {
+  return band_batched_impl(h, count, m, n, d_A, lda, nb, ib, tree, variant, out);
+}
+
+int bidiag_band_batched_f32(bidiag_handle h, int64_t count, const int64_t* m, const int64_t* n,
+                            const float* const* d_A, const int64_t* lda, const int* nb, const int* ib, const int* tree,
+                            const int* variant, bidiag_result_t* out) {
+  return band_batched_impl(h, count, m, n, d_A, lda, nb, ib, tree, variant, out);
+}
+
+int bidiag_autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant) {
+  if (m < 1 || n < 1 || m < n) return -1;
+  if (nsm < 1) return -3;
+  if (!nb || !ib || !tree || !variant) return -4;
+  try {
+    bd::autotune(m, n, nsm, nb, ib, tree, variant);
+  } catch (...) {
+    return BIDIAG_ERR_NOMEM;
+  }
+  return BIDIAG_OK;
 }
 
 int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, int64_t lda, int nb, int ib, int tree,
@@ -561,6 +779,7 @@ int bidiag_result_reflectors(bidiag_result_t r, bidiag_reflectors* desc) {
   desc->tiles2 = r->tiles2;
   desc->T = r->T;
   desc->elem_bytes = r->esize;
+  desc->tree = r->tree;
   desc->tslot = r->pd->plan.tslot.data();
   desc->ntasks = (int64_t)r->pd->plan.tasks.size();
   desc->m = r->m;

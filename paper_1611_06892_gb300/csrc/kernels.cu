@@ -638,15 +638,22 @@ __device__ void task_copy(const E* src, E* dst, int nb, bool diag) {
   }
 }
 
+// Tile reference (buffer << 28 | tile index) -> address, with the matrix's offsets and tile size.
+struct MatView {
+  int nb, ib, w, npanels;
+  int64_t off[3], offT, nt[3];
+};
 template <typename E>
-__device__ __forceinline__ E* tile_ptr(const ExecParams& prm, int32_t ref, bool& ok) {
+__device__ __forceinline__ E* tile_ptr(const ExecParams& prm, const MatView& mv, int32_t ref, bool& ok) {
   if (ref < 0) { ok = false; return nullptr; }
   const int buf = (int)((uint32_t)ref >> 28);
   const int64_t idx = ref & 0x0fffffff;
-  void* base = buf == 0 ? prm.buf[0] : (buf == 1 ? prm.buf[1] : (buf == 2 ? prm.buf[2] : nullptr));
-  const int64_t nt = buf == 0 ? prm.ntiles[0] : (buf == 1 ? prm.ntiles[1] : prm.ntiles[2]);
+  if (buf > 2) { ok = false; return nullptr; }
+  void* base = buf == 0 ? prm.buf[0] : (buf == 1 ? prm.buf[1] : prm.buf[2]);
+  const int64_t nt = buf == 0 ? mv.nt[0] : (buf == 1 ? mv.nt[1] : mv.nt[2]);
+  const int64_t off = buf == 0 ? mv.off[0] : (buf == 1 ? mv.off[1] : mv.off[2]);
   if (base == nullptr || idx >= nt) { ok = false; return nullptr; }
-  return static_cast<E*>(base) + (size_t)idx * prm.nb * prm.nb;
+  return static_cast<E*>(base) + off + (size_t)idx * mv.nb * mv.nb;
 }
 
 // Persistent dataflow executor: CTAs take sub-tasks from a queue in topological priority order,
@@ -705,25 +712,40 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     const int strip = (t.op >> 8) & 0xff;
     const int blk = (t.op >> 16) & 0xff;
     const int kind = (t.op >> 24) & 3;
-    const int nblk = prm.nb / prm.ib;
     bool ok = true;
-    E* X = tile_ptr<E>(prm, t.x, ok);
-    E* Tg = (t.tslot >= 0 && t.tslot < prm.npanels)
-                ? static_cast<E*>(prm.T) + (size_t)t.tslot * prm.ib * prm.nb
+    MatView mv;
+    if (prm.mats) {
+      const int mat = (t.flags >> 8) & 0xffffff;
+      if (mat >= prm.nmats) {
+        ok = false;
+        mv = MatView{prm.nb, prm.ib, prm.w, 0, {0, 0, 0}, 0, {0, 0, 0}};
+      } else {
+        const MatInfo mi = prm.mats[mat];
+        mv = MatView{mi.nb, mi.ib, mi.w, mi.npanels, {mi.off[0], mi.off[1], 0}, mi.offT,
+                     {mi.ntiles[0], mi.ntiles[1], 0}};
+      }
+    } else {
+      mv = MatView{prm.nb, prm.ib, prm.w, prm.npanels, {0, 0, 0}, 0, {prm.ntiles[0], prm.ntiles[1], prm.ntiles[2]}};
+    }
+    const int nb = mv.nb, ib = mv.ib, wst = mv.w;
+    const int nblk = nb / ib;
+    E* X = tile_ptr<E>(prm, mv, t.x, ok);
+    E* Tg = (ok && t.tslot >= 0 && t.tslot < mv.npanels)
+                ? static_cast<E*>(prm.T) + mv.offT + (size_t)t.tslot * ib * nb
                 : nullptr;
     switch (type) {
       case PF: {
-        E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, t.a, ok);
-        if (ok && Tg && blk < nblk && kind <= PM_TT) task_panel_factor(smb, kind, X, A, tr, Tg, prm.nb, prm.ib, blk);
+        E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
+        if (ok && Tg && blk < nblk && kind <= PM_TT) task_panel_factor(smb, kind, X, A, tr, Tg, nb, ib, blk);
         else ok = false;
         break;
       }
       case PU: {
-        E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, t.a, ok);
+        E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
         const int utype = kind == PM_GE ? UNMQR : (kind == PM_TS ? TSMQR : TTMQR);
         if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT)
-          task_update(smb, utype, X, A, X, tr, false, Tg, prm.nb, prm.ib, prm.w, blk, blk + 1, strip * prm.ib,
-                      prm.ib, prm.f32_simt != 0);
+          task_update(smb, utype, X, A, X, tr, false, Tg, nb, ib, wst, blk, blk + 1, strip * ib, ib,
+                      prm.f32_simt != 0);
         else
           ok = false;
         break;
@@ -731,19 +753,19 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       case UNMQR:
       case TSMQR:
       case TTMQR: {
-        E* A = (type == UNMQR) ? nullptr : tile_ptr<E>(prm, t.a, ok);
-        E* C = tile_ptr<E>(prm, t.c, ok);
-        const int col0 = strip * prm.w;
-        if (ok && Tg && col0 < prm.nb)
-          task_update(smb, type, X, A, C, tr, notrans, Tg, prm.nb, prm.ib, prm.w, 0, nblk, col0,
-                      min(prm.w, prm.nb - col0), prm.f32_simt != 0);
+        E* A = (type == UNMQR) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
+        E* C = tile_ptr<E>(prm, mv, t.c, ok);
+        const int col0 = strip * wst;
+        if (ok && Tg && col0 < nb)
+          task_update(smb, type, X, A, C, tr, notrans, Tg, nb, ib, wst, 0, nblk, col0, min(wst, nb - col0),
+                      prm.f32_simt != 0);
         else
           ok = false;
         break;
       }
       case COPY: {
-        E* C = tile_ptr<E>(prm, t.c, ok);
-        if (ok) task_copy(X, C, prm.nb, t.flags & 1);
+        E* C = tile_ptr<E>(prm, mv, t.c, ok);
+        if (ok) task_copy(X, C, nb, t.flags & 1);
         break;
       }
       default:
@@ -813,6 +835,50 @@ __global__ void extract_kernel(const E* __restrict__ tiles, int64_t rows_t, int 
   }
 }
 
+__device__ __forceinline__ int find_matrix(const PackDesc* d, int count, int64_t x) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {   // last b with d[b].first <= x
+    const int mid = (lo + hi + 1) >> 1;
+    if (d[mid].first <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename E>
+__global__ void pack_batched_kernel(const PackDesc* __restrict__ d, int count) {
+  const int b = find_matrix(d, count, blockIdx.x);
+  const PackDesc pd = d[b];
+  const int64_t tile = blockIdx.x - pd.first;
+  const int nb = pd.nb;
+  const int64_t a = tile % pd.rows_t, c = tile / pd.rows_t;
+  const E* A = static_cast<const E*>(pd.A);
+  E* dst = static_cast<E*>(pd.out) + (size_t)tile * nb * nb;
+  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+    const int r = o % nb, cc = o / nb;
+    const int64_t gi = a * nb + r, gj = c * nb + cc;
+    dst[o] = (gi < pd.m && gj < pd.n) ? A[gi + gj * pd.ld] : E(0);
+  }
+}
+
+template <typename E>
+__global__ void extract_batched_kernel(const PackDesc* __restrict__ d, int count) {
+  const int b = find_matrix(d, count, blockIdx.x);
+  const PackDesc pd = d[b];
+  const int64_t j = blockIdx.x - pd.first;
+  const int nb = pd.nb;
+  const E* tiles = static_cast<const E*>(pd.A);
+  E* ab = static_cast<E*>(pd.out);
+  for (int dd = threadIdx.x; dd <= nb; dd += blockDim.x) {
+    const int64_t i = j + dd - nb;
+    E v = E(0);
+    if (i >= 0) {
+      const int64_t a = i / nb, c = j / nb;
+      v = tiles[(size_t)(c * pd.rows_t + a) * nb * nb + (i % nb) + (j % nb) * nb];
+    }
+    ab[dd + j * pd.ld] = v;
+  }
+}
+
 template <typename E>
 cudaError_t pack_t(const E* A, int64_t lda, int64_t m, int64_t n, int nb, E* tiles, int64_t rows_t, int64_t cols_t,
                    cudaStream_t st) {
@@ -868,6 +934,20 @@ int exec_max_ctas_per_sm(size_t smem, int esize) {
 cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st) {
   if (prm.esize == 4) exec_kernel<float><<<grid, kThreads, smem, st>>>(prm);
   else exec_kernel<double><<<grid, kThreads, smem, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_batched(const PackDesc* d, int count, int64_t total_tiles, int esize, cudaStream_t st) {
+  if (total_tiles == 0) return cudaSuccess;
+  if (esize == 4) pack_batched_kernel<float><<<(unsigned)total_tiles, 256, 0, st>>>(d, count);
+  else pack_batched_kernel<double><<<(unsigned)total_tiles, 256, 0, st>>>(d, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_batched(const PackDesc* d, int count, int64_t total_cols, int esize, cudaStream_t st) {
+  if (total_cols == 0) return cudaSuccess;
+  if (esize == 4) extract_batched_kernel<float><<<(unsigned)total_cols, 256, 0, st>>>(d, count);
+  else extract_batched_kernel<double><<<(unsigned)total_cols, 256, 0, st>>>(d, count);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,23 @@ constexpr int kMaxNb = 256;
 // err[1] = queue position of the failing task, err[2] = dependency it waited for.
 enum DevErr : int { DERR_OK = 0, DERR_TIMEOUT = 1, DERR_BADTASK = 2 };
 
+// Per-matrix parameters of a batched program (sub-task flags bits 8-31 select the entry).
+struct MatInfo {
+  int64_t off[2];       // element offsets of the matrix's tiles in buf[0] (A) and buf[1] (R copy)
+  int64_t offT;         // element offset of its T slots
+  int64_t ntiles[2];
+  int32_t nb, ib, w, npanels;
+  int64_t pad;
+};
+
+// Matrix b of a batched pack / extract.
+struct PackDesc {
+  const void* A;        // column-major input (pack) or tile buffer of the band's source (extract)
+  void* out;            // tile buffer base of the matrix (pack) or its band (extract)
+  int64_t ld, m, n, rows_t, first;   // ld: lda (pack) / ldab (extract); first: first tile / column
+  int32_t nb, pad;
+};
+
 struct ExecParams {
   const DevTask* tasks;
   const int32_t* deps;
@@ -30,6 +47,8 @@ struct ExecParams {
   uint64_t wait_ns;
   int64_t* trace;       // optional: 4 int64 per task (start ns, end ns, SM id, op), queue order
   int esize;            // 8: FP64 tiles; 4: FP32 tiles (split-precision updates)
+  const MatInfo* mats;  // batched program: per-matrix parameters (null for one matrix)
+  int nmats;
   int f32_simt;         // FP32 tiles only: 1 = updates by FP32 FFMA instead of three TF32 tensor-core products
 };
 
@@ -52,6 +71,9 @@ cudaError_t launch_unpack(const double* tiles, int64_t rows_t, int nb, int64_t m
                           cudaStream_t st);
 cudaError_t launch_unpack(const float* tiles, int64_t rows_t, int nb, int64_t m, int64_t n, float* A, int64_t lda,
                           cudaStream_t st);
+// Batched pack / extract over `count` matrices described on the device (total = tiles / columns).
+cudaError_t launch_pack_batched(const PackDesc* d, int count, int64_t total_tiles, int esize, cudaStream_t st);
+cudaError_t launch_extract_batched(const PackDesc* d, int count, int64_t total_cols, int esize, cudaStream_t st);
 // Band extraction: ab((nb+1) x n, ld ldab) from the tile buffer (grid rows rows_t).
 cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
                            cudaStream_t st);

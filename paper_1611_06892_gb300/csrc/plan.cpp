@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <functional>
 #include <stdexcept>
 
 namespace bd {
@@ -644,7 +645,9 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
   for (int32_t y = 0; y < nsub; ++y) pos[order[y]] = y;
   pl.dev.resize(nsub);
   pl.deps.clear();
+  pl.prio.resize(nsub);
   for (int32_t y = 0; y < nsub; ++y) {
+    pl.prio[y] = bottom[order[y]];
     DevTask e = g.sub[order[y]];
     e.dep_begin = (int32_t)pl.deps.size();
     for (int32_t dd : g.deps[order[y]]) {
@@ -653,6 +656,83 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
     }
     e.dep_end = (int32_t)pl.deps.size();
     pl.dev[y] = e;
+  }
+}
+
+void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>* dev, std::vector<int32_t>* deps) {
+  const size_t np = plans.size();
+  if (np >= (1u << 23)) throw std::invalid_argument("too many matrices in a batch");
+  size_t total = 0;
+  for (const Plan* pl : plans) total += pl->dev.size();
+  std::vector<size_t> head(np, 0);
+  std::vector<std::vector<int32_t>> gpos(np);
+  for (size_t b = 0; b < np; ++b) gpos[b].resize(plans[b]->dev.size());
+  // k-way merge by decreasing priority (ties: lower matrix index first)
+  using Item = std::pair<int64_t, int64_t>;   // (-prio, b)
+  std::vector<Item> heap;
+  auto push = [&](size_t b) {
+    if (head[b] < plans[b]->dev.size()) {
+      heap.push_back({-plans[b]->prio[head[b]], (int64_t)b});
+      std::push_heap(heap.begin(), heap.end(), std::greater<Item>());
+    }
+  };
+  for (size_t b = 0; b < np; ++b) push(b);
+  dev->clear();
+  dev->reserve(total);
+  std::vector<std::pair<int32_t, int32_t>> src;   // (matrix, local queue position) per global position
+  src.reserve(total);
+  while (!heap.empty()) {
+    std::pop_heap(heap.begin(), heap.end(), std::greater<Item>());
+    const size_t b = (size_t)heap.back().second;
+    heap.pop_back();
+    const int32_t y = (int32_t)head[b]++;
+    gpos[b][y] = (int32_t)src.size();
+    src.push_back({(int32_t)b, y});
+    push(b);
+  }
+  deps->clear();
+  for (size_t g = 0; g < src.size(); ++g) {
+    const Plan* pl = plans[src[g].first];
+    DevTask e = pl->dev[src[g].second];
+    const int32_t b0 = e.dep_begin, b1 = e.dep_end;
+    e.dep_begin = (int32_t)deps->size();
+    for (int32_t d = b0; d < b1; ++d) {
+      const int32_t gd = gpos[src[g].first][pl->deps[d]];
+      if (gd >= (int32_t)g) throw std::logic_error("merged order is not topological");
+      deps->push_back(gd);
+    }
+    e.dep_end = (int32_t)deps->size();
+    e.flags = (e.flags & 0xff) | (src[g].first << 8);
+    dev->push_back(e);
+  }
+}
+
+void autotune(int64_t m, int64_t n, int nsm, int* nb_out, int* ib_out, int* tree_out, int* variant_out) {
+  // measured efficiency of FP64 update sub-tasks per tile size (fraction of an SM's FP64 peak)
+  const int cands[3] = {32, 64, 128};
+  const double eff[3] = {0.45, 0.70, 0.85};
+  double best = -1.0;
+  for (int c = 0; c < 3; ++c) {
+    const int nb = cands[c];
+    if (c > 0 && cands[c - 1] >= n) break;          // a larger tile would only add padding
+    const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
+    const int variant = choose_variant(p, q, GREEDY, 1, nullptr, nullptr);
+    const int tree = (q <= 2) ? GREEDY : AUTO;
+    const int64_t R = std::max<int64_t>(1, (int64_t)nsm * std::min(32, nb) / nb);
+    const std::vector<Task> ts = make_tasks(p, q, tree, variant, R);
+    int64_t work = 0, cp = 0;
+    const int kw[7] = {4, 6, 6, 12, 2, 6, 0};
+    for (const Task& t : ts) work += kw[t.type];
+    make_dag(ts, p, q, variant, nullptr, nullptr, &cp);
+    const double unit = (double)nb * nb * nb / 3.0;
+    const double cost = (double)work * unit / (nsm * eff[c]) + (double)cp * unit;
+    if (best < 0 || cost < best) {
+      best = cost;
+      *nb_out = nb;
+      *ib_out = nb == 32 ? 16 : 32;
+      *tree_out = tree;
+      *variant_out = variant;
+    }
   }
 }
 

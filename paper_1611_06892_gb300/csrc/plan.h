@@ -32,7 +32,7 @@ struct DevTask {
   int32_t tslot;     // T slot of the panel task
   int32_t dep_begin; // deps in [dep_begin, dep_end) of the dependency array
   int32_t dep_end;
-  int32_t flags;     // bit 0: diagonal COPY (upper triangle only)
+  int32_t flags;     // bit 0: diagonal COPY (upper triangle only); bits 8-31: matrix of a batch
 };
 
 inline int32_t tile_ref(int buf, int64_t idx) { return (int32_t)(((uint32_t)buf << 28) | (uint32_t)idx); }
@@ -51,6 +51,7 @@ struct Plan {
   // device program
   std::vector<DevTask> dev;        // in queue (priority) order
   std::vector<int32_t> deps;       // indices into dev (queue positions)
+  std::vector<int64_t> prio;       // bottom level of each queued sub-task (flop-proportional weights)
 };
 
 // Trees and task lists (independent of any device state).
@@ -66,5 +67,18 @@ int choose_variant(int p, int q, int tree, int64_t resources, int64_t* cp_bidiag
 // Full plan for a reduction: tasks, DAG, device sub-tasks ordered by critical-path priority.
 void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
                 int strip_w);
+
+// Several independent plans as one device program: the queues are merged by decreasing bottom level
+// (each plan's own order is kept, so the result is topological), matrix b's sub-tasks carry b in
+// flags bits 8-31 and their dependencies are renumbered to the merged queue.
+void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>* dev, std::vector<int32_t>* deps);
+
+// Tile size, inner blocking, tree and variant for one m x n matrix of a batch (the batched form's
+// autotuner).  nb in {32, 64, 128}; ib = 16 for nb = 32, else 32; variant by critical path; tree Auto
+// (Greedy when the panel is at most two tiles).  nb minimises the predicted time
+//   padded Table 1 work / (SMs x eff(nb)) + critical path (unbounded resources),
+// both in flops at the FP64 rate of one SM, eff(nb) being the measured efficiency of the update
+// sub-tasks for that tile size.
+void autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant);
 
 }  // namespace bd

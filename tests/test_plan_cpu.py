@@ -111,3 +111,13 @@ def test_choose_variant_follows_critical_paths():
     assert G.bidiag_plan_choose_variant(256, 4, T.AUTO, 19)[0] == T.RBIDIAG
     assert G.bidiag_plan_choose_variant(560, 100, T.GREEDY, 1)[0] == T.BIDIAG
     assert G.bidiag_plan_choose_variant(575, 100, T.GREEDY, 1)[0] == T.RBIDIAG
+
+
+def test_autotune_choices():
+    """The batched form's autotuner returns a supported configuration for every shape."""
+    for (m, n) in ((32, 1), (64, 32), (100, 100), (1024, 1024), (1024, 200), (4096, 1024), (70000, 64)):
+        nb, ib, tree, variant = G.bidiag_autotune(m, n, 152)
+        assert (nb, ib) in ((32, 16), (64, 32), (128, 32))
+        assert tree in (T.GREEDY, T.AUTO) and variant in (T.BIDIAG, T.RBIDIAG)
+        q = -(-n // nb)
+        assert tree == (T.GREEDY if q <= 2 else T.AUTO)
