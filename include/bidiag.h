@@ -147,10 +147,11 @@ int bidiag_band_batched_f32(bidiag_handle h, int64_t count, const int64_t* m, co
                             const float* const* d_A, const int64_t* lda, const int* nb, const int* ib,
                             const int* tree, const int* variant, bidiag_result_t* out);
 
-/* Autotuner of the batched form (host only): for an m x n matrix on a device with nsm SMs, picks nb in
- * {32, 64, 128} (ib = 16 for nb = 32, else 32) minimising padded Table 1 work / (nsm x efficiency of
- * that tile size) + critical path, the variant by critical path (Sec. 4.3.3), and the Auto tree
- * (Greedy when the panel has at most two tiles).  Errors: -1 sizes, -3 nsm, -4 NULL output. */
+/* Autotuner of the batched form (host only): for an m x n matrix of a batch on a device with nsm SMs,
+ * picks nb in {32, 64, 128} (ib = 16 for nb = 32, else 32) minimising padded Table 1 work / (measured
+ * efficiency of that tile size in batches) + critical path / (nsm / 8), the FlatTS tree (the other
+ * matrices of the batch supply the parallelism) and the variant by critical path (Sec. 4.3.3).
+ * Errors: -1 sizes, -3 nsm, -4 NULL output. */
 int bidiag_autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant);
 
 /*

@@ -52,7 +52,7 @@ def build(verbose=False):
             if log:
                 print(log, file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *[o for o, _ in outs], "-lcudart"]
+    cmd = [_nvcc(), "-shared", *ARCH, "-o", tmp, *[o for o, _ in outs], "-lcudart", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -11,6 +12,7 @@
 #include <set>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -457,45 +459,71 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
     std::shared_ptr<PlanDev> pd;
   };
   std::vector<One> mats((size_t)count);
-  size_t smem = 0;
   for (int64_t b = 0; b < count; ++b) {
     out[b] = nullptr;
     if (m[b] < 1 || n[b] < 1 || m[b] < n[b] || lda[b] < m[b] || !d_A[b])
       return fail(h, -3, "matrix " + std::to_string(b) + ": need m >= n >= 1, lda >= m and A != NULL");
-    One& o = mats[(size_t)b];
-    if (nb_in) {
-      o.nb = nb_in[b];
-      o.ib = ib_in ? ib_in[b] : std::min(o.nb, 32);
-      o.tree = tree_in ? tree_in[b] : BIDIAG_AUTO;
-      o.variant = var_in ? var_in[b] : BIDIAG_AUTO_VARIANT;
-    } else {
-      try {
-        bd::autotune(m[b], n[b], h->nsm, &o.nb, &o.ib, &o.tree, &o.variant);
-      } catch (...) {
-        return fail(h, BIDIAG_ERR_NOMEM, "autotuner failed");
+  }
+  // configuration (autotuned when nb is NULL) and plan of every matrix, in parallel on the host
+  std::vector<int> bad((size_t)count, 0);   // 0 ok, else the error code of that matrix
+  {
+    const unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::atomic<int64_t> next(0);
+    auto worker = [&]() {
+      for (int64_t b = next++; b < count; b = next++) {
+        One& o = mats[(size_t)b];
+        try {
+          if (nb_in) {
+            o.nb = nb_in[b];
+            o.ib = ib_in ? ib_in[b] : std::min(o.nb, 32);
+            o.tree = tree_in ? tree_in[b] : BIDIAG_AUTO;
+            o.variant = var_in ? var_in[b] : BIDIAG_AUTO_VARIANT;
+          } else {
+            bd::autotune(m[b], n[b], h->nsm, &o.nb, &o.ib, &o.tree, &o.variant);
+            if (tree_in) o.tree = tree_in[b];
+            if (var_in) o.variant = var_in[b];
+          }
+          if (o.nb < 1 || o.nb > bd::kMaxNb || o.ib < 1 || o.ib > std::min(o.nb, 64) || o.nb % o.ib) {
+            bad[(size_t)b] = -7;
+            continue;
+          }
+          if (o.tree < 0 || o.tree > 3 || o.variant < 0 || o.variant > 2) {
+            bad[(size_t)b] = -9;
+            continue;
+          }
+          o.w = bd::choose_strip_width(o.nb, o.ib, h->strip_w, h->smem_optin, esize);
+          if (!o.w) {
+            bad[(size_t)b] = BIDIAG_ERR_UNSUPPORTED;
+            continue;
+          }
+          const int p = (int)((m[b] + o.nb - 1) / o.nb), q = (int)((n[b] + o.nb - 1) / o.nb);
+          const int64_t R = resources_of(h, o.nb, o.w);
+          if (o.variant == BIDIAG_AUTO_VARIANT) o.variant = bd::choose_variant(p, q, o.tree, R, nullptr, nullptr);
+          o.pd = std::make_shared<PlanDev>();
+          bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w);
+          dump_tasks(o.pd->plan.tasks, o.pd->dump);
+        } catch (const std::bad_alloc&) {
+          bad[(size_t)b] = BIDIAG_ERR_NOMEM;
+        } catch (...) {
+          bad[(size_t)b] = BIDIAG_ERR_UNSUPPORTED;
+        }
       }
-      if (tree_in) o.tree = tree_in[b];
-      if (var_in) o.variant = var_in[b];
+    };
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nthr && (int64_t)t < count; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+  }
+  size_t smem = 0;
+  for (int64_t b = 0; b < count; ++b) {
+    if (bad[(size_t)b]) {
+      const int code = bad[(size_t)b];
+      const char* what = code == -7 ? "invalid nb / ib" : code == -9 ? "invalid tree / variant"
+                       : code == BIDIAG_ERR_NOMEM ? "host allocation failed" : "unsupported configuration";
+      return fail(h, code, "matrix " + std::to_string(b) + ": " + what);
     }
-    if (o.nb < 1 || o.nb > bd::kMaxNb || o.ib < 1 || o.ib > std::min(o.nb, 64) || o.nb % o.ib)
-      return fail(h, -7, "matrix " + std::to_string(b) + ": invalid nb / ib");
-    if (o.tree < 0 || o.tree > 3 || o.variant < 0 || o.variant > 2)
-      return fail(h, -9, "matrix " + std::to_string(b) + ": invalid tree / variant");
-    o.w = bd::choose_strip_width(o.nb, o.ib, h->strip_w, h->smem_optin, esize);
-    if (!o.w) return fail(h, BIDIAG_ERR_UNSUPPORTED, "matrix " + std::to_string(b) + ": shared memory");
+    const One& o = mats[(size_t)b];
     smem = std::max(smem, bd::exec_smem_bytes(o.nb, o.ib, o.w, esize));
-    const int p = (int)((m[b] + o.nb - 1) / o.nb), q = (int)((n[b] + o.nb - 1) / o.nb);
-    const int64_t R = resources_of(h, o.nb, o.w);
-    try {
-      if (o.variant == BIDIAG_AUTO_VARIANT) o.variant = bd::choose_variant(p, q, o.tree, R, nullptr, nullptr);
-      o.pd = std::make_shared<PlanDev>();
-      bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w);
-      dump_tasks(o.pd->plan.tasks, o.pd->dump);
-    } catch (const std::bad_alloc&) {
-      return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning");
-    } catch (const std::exception& ex) {
-      return fail(h, BIDIAG_ERR_UNSUPPORTED, std::string("planner: ") + ex.what());
-    }
   }
   // storage layout
   std::vector<bd::MatInfo> info((size_t)count);

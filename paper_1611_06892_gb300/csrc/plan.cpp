@@ -708,24 +708,26 @@ void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>*
 }
 
 void autotune(int64_t m, int64_t n, int nsm, int* nb_out, int* ib_out, int* tree_out, int* variant_out) {
-  // measured efficiency of FP64 update sub-tasks per tile size (fraction of an SM's FP64 peak)
+  // Per-tile-size cost in a batch, where the other matrices supply the parallelism: padded Table 1 work
+  // over the measured efficiency of that tile size (512 uneven matrices, m in [64, 1024], on a GB300:
+  // FlatTS batches of nb = 32 / 64 / 128 ran at 0.19 / 0.48 / 0.62 of the FP64 rate the nb = 128 batch
+  // reached), plus the matrix's critical path over the number of SMs it competes with.
   const int cands[3] = {32, 64, 128};
-  const double eff[3] = {0.45, 0.70, 0.85};
+  const double eff[3] = {0.30, 0.75, 1.0};
   double best = -1.0;
   for (int c = 0; c < 3; ++c) {
     const int nb = cands[c];
     if (c > 0 && cands[c - 1] >= n) break;          // a larger tile would only add padding
     const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
-    const int variant = choose_variant(p, q, GREEDY, 1, nullptr, nullptr);
-    const int tree = (q <= 2) ? GREEDY : AUTO;
-    const int64_t R = std::max<int64_t>(1, (int64_t)nsm * std::min(32, nb) / nb);
-    const std::vector<Task> ts = make_tasks(p, q, tree, variant, R);
+    const int variant = choose_variant(p, q, FLATTS, 1, nullptr, nullptr);
+    const int tree = FLATTS;
+    const std::vector<Task> ts = make_tasks(p, q, tree, variant, 1);
     int64_t work = 0, cp = 0;
     const int kw[7] = {4, 6, 6, 12, 2, 6, 0};
     for (const Task& t : ts) work += kw[t.type];
     make_dag(ts, p, q, variant, nullptr, nullptr, &cp);
     const double unit = (double)nb * nb * nb / 3.0;
-    const double cost = (double)work * unit / (nsm * eff[c]) + (double)cp * unit;
+    const double cost = (double)work * unit / eff[c] + (double)cp * unit / std::max(1, nsm / 8);
     if (best < 0 || cost < best) {
       best = cost;
       *nb_out = nb;

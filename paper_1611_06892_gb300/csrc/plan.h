@@ -74,11 +74,10 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
 void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>* dev, std::vector<int32_t>* deps);
 
 // Tile size, inner blocking, tree and variant for one m x n matrix of a batch (the batched form's
-// autotuner).  nb in {32, 64, 128}; ib = 16 for nb = 32, else 32; variant by critical path; tree Auto
-// (Greedy when the panel is at most two tiles).  nb minimises the predicted time
-//   padded Table 1 work / (SMs x eff(nb)) + critical path (unbounded resources),
-// both in flops at the FP64 rate of one SM, eff(nb) being the measured efficiency of the update
-// sub-tasks for that tile size.
+// autotuner).  nb in {32, 64, 128}; ib = 16 for nb = 32, else 32; FlatTS tree (in a batch the other
+// matrices provide the parallelism and the TS kernels are the most efficient); variant by critical
+// path.  nb minimises padded Table 1 work / eff(nb) + critical path / (SMs / 8), eff(nb) being the
+// measured relative efficiency of batches of that tile size.
 void autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant);
 
 }  // namespace bd

@@ -118,6 +118,5 @@ def test_autotune_choices():
     for (m, n) in ((32, 1), (64, 32), (100, 100), (1024, 1024), (1024, 200), (4096, 1024), (70000, 64)):
         nb, ib, tree, variant = G.bidiag_autotune(m, n, 152)
         assert (nb, ib) in ((32, 16), (64, 32), (128, 32))
-        assert tree in (T.GREEDY, T.AUTO) and variant in (T.BIDIAG, T.RBIDIAG)
-        q = -(-n // nb)
-        assert tree == (T.GREEDY if q <= 2 else T.AUTO)
+        assert tree == T.FLATTS and variant in (T.BIDIAG, T.RBIDIAG)
+        assert nb < 2 * max(32, n)          # never more than one size above the matrix's width
