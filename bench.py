@@ -39,6 +39,9 @@ WORKLOADS = {
                       desc="square FP64 512x512 N(0,1), nb=64 ib=16, BiDiag"),
     "tall65536x1024": dict(m=65536, n=1024, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(4,),
                            desc="tall-skinny FP64 65536x1024 N(0,1), nb=256 ib=32, R-BiDiag"),
+    "batched512": dict(m=1024, n=1024, nb=0, ib=0, variant="auto", kind="batch", seeds=(6,),
+                       desc="batch of 512 matrices, m ~ U[64, 1024], n ~ U[32, m], N(0,1), one persistent launch, "
+                            "autotuned nb / ib / tree / variant per matrix"),
     "tall65536x2048": dict(m=65536, n=2048, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(5,),
                            desc="tall-skinny FP64 65536x2048 N(0,1), nb=256 ib=32, R-BiDiag"),
 }
@@ -48,14 +51,35 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 # Split-FP32 form: the updates are three TF32 tensor-core products per useful product.  TF32 dense peak
 # = measured bf16 peak x nominal TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s); one useful flop costs three.
 TF32_RATIO = 1.1 / 2.25
-# DRAM bytes per executor launch from the ncu capture summarised under profiles/ (None until taken
-# for the current kernel).
-EXEC_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one executor launch on the 8192^2 workload, from the ncu capture
+# summarised under profiles/ (to be reset to None whenever the kernel changes).
+EXEC_TRAFFIC_BYTES = 11564153856 + 11562566400
 CPU_SAMPLE_SECONDS = 12.0
+
+
+def tf32_split_peak_gflops():
+    """TF32 tensor peak (measured bf16 burst x 1.1/2.25) over the three products per useful flop."""
+    bf16 = 1926.3
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            bf16 = json.load(fh).get("bf16_tflops", bf16)
+    except OSError:
+        pass
+    return bf16 * TF32_RATIO * 1e3 / 3.0
 
 
 def metric_flops(m, n):
     return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
+
+
+def batch_shapes(seed, count=512):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.integers(64, 1025))
+        out.append((m, int(rng.integers(32, m + 1))))
+    return out
 
 
 def make_input(w, rank, device):
@@ -186,6 +210,173 @@ def run_cpu_sample_subprocess(A_host_np, w, tree, seconds, max_tasks=None):
         return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def cpu_sample_batch(path, seconds):
+    """Times the oracle (single BLAS thread) on the first matrices of the batch with their tuned configs."""
+    import numpy as np
+
+    from oracle import bidiag as OB
+
+    data = np.load(path)
+    flops = 0.0
+    done = 0
+    t0 = time.perf_counter()
+    k = 0
+    while f"A{k}" in data.files:
+        A = data[f"A{k}"]
+        nb, ib, tree, variant = (int(x) for x in data[f"cfg{k}"])
+        OB.bidiag_band(A, nb, ib, tree, variant, resources=1)
+        flops += metric_flops(*A.shape)
+        done += 1
+        k += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    return {"tasks": done, "total_tasks": 512, "flops": flops, "seconds": time.perf_counter() - t0}
+
+
+def reference_batched(args, w, base):
+    """The oracle on the batch: each step reduces the next matrices of the batch (nb = 128, ib = 32,
+    FlatTS, the variant with the shorter critical path) for a bounded time, single BLAS thread."""
+    import numpy as np
+
+    from oracle import trees as OT
+    from paper_1611_06892_gb300 import inputs
+
+    shapes = batch_shapes(w["seeds"][0])
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    res = []
+    k = 0
+    with tempfile.TemporaryDirectory() as td:
+        for _ in range(args.warmup + args.steps):
+            path = os.path.join(td, "batch.npz")
+            sample = {}
+            for j in range(64):
+                m, n = shapes[(k + j) % len(shapes)]
+                p, q = -(-m // 128), -(-n // 128)
+                v = OT.BIDIAG if OT.critical_path(p, q, OT.FLATTS, OT.BIDIAG) <= \
+                    OT.critical_path(p, q, OT.FLATTS, OT.RBIDIAG) else OT.RBIDIAG
+                sample[f"A{j}"] = inputs.gaussian(m, n, seed=w["seeds"][0] + k + j)
+                sample[f"cfg{j}"] = np.array([128, 32, OT.FLATTS, v])
+            np.savez(path, **sample)
+            env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-batch", path,
+                                  "--cpu-seconds", str(per_step)], env=env, capture_output=True, text=True,
+                                 timeout=600, check=True)
+            r = json.loads(out.stdout.strip().splitlines()[-1])
+            k += r["tasks"]
+            res.append(r)
+    timed = res[args.warmup:]
+    val = sum(r["flops"] for r in timed) / sum(r["seconds"] for r in timed) / 1e12
+    sample = (f"{sum(r['tasks'] for r in timed)} of the 512 matrices over {len(timed)} steps "
+              f"(~{per_step:.0f} s each), nb 128, FlatTS, single BLAS thread")
+    line = dict(base, impl="reference", value=val, ms_per_step=1e3 * statistics.mean(r["seconds"] for r in timed),
+                cpu_baseline={"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+                e2e={"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                gpu_launches=0)
+    line["config"] = dict(line["config"], workload=w["desc"] + ", FP64")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args, w, base, config, world, rank, local, device, G, torch):
+    """The batched workload: 512 uneven matrices reduced in one persistent launch per step."""
+    import numpy as np
+
+    f32 = args.precision == "f32"
+    dt = torch.float32 if f32 else torch.float64
+    shapes = batch_shapes(w["seeds"][0] + 1000 * rank)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w["seeds"][0] + 1000 * rank)
+    As = [torch.randn(n, m, dtype=dt, device=device, generator=gen).t() for m, n in shapes]
+    flops = sum(metric_flops(m, n) for m, n in shapes)
+    config = dict(config, workload=w["desc"] + (", FP32 storage (3xTF32 updates)" if f32 else ", FP64"),
+                  count=len(shapes), m="U[64,1024]", n="U[32,m]", nb="autotuned", ib="autotuned",
+                  tree="autotuned (FlatTS)", variant="critical path",
+                  l2="inputs 1.1 GB total > 129 MB L2 (no flush needed)")
+    config.pop("auto_resources", None)
+    h = G.Handle(device=local)
+    h.set_option(G.OPT_TIMING, 1)
+
+    def step():
+        res = h.band_batched(As)
+        h.sync()
+        ms = h.last_exec_ms()
+        for r in res:
+            r.free()
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    stream = h.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    exec_ms = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    el_ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    ms_per_step = el_ms / args.steps
+    value = world * flops / (ms_per_step * 1e-3) / 1e12
+    # end to end: H2D of the 512 inputs from pinned memory, the batched call, D2H of the 512 bands
+    hosts = [torch.empty((A.shape[1], A.shape[0]), dtype=dt, pin_memory=True).t().copy_(A) for A in As]
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        barrier(world)
+        t0 = time.perf_counter()
+        dev = [x.to(device, non_blocking=True) for x in hosts]
+        res = h.band_batched(dev)
+        bands = [r.band().cpu() for r in res]
+        e2e_t.append(time.perf_counter() - t0)
+        d2h = sum(x.numel() * x.element_size() for x in bands)
+        for r in res:
+            r.free()
+        del dev, bands
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device) if e2e_t else None
+    h2d = sum(m * n for m, n in shapes) * (4 if f32 else 8)
+    if not e2e_t:
+        d2h = 0
+    cfgs = [G.bidiag_autotune(m, n, torch.cuda.get_device_properties(local).multi_processor_count) for m, n in shapes]
+    exec_mean = statistics.mean(exec_ms)
+    achieved = flops / (exec_mean * 1e-3) / 1e9
+    if f32:
+        peak, bound, src = tf32_split_peak_gflops(), "tensor", "measured bf16 x 1.1/2.25 (TF32) / 3"
+    else:
+        peak, bound, src = FP64_PEAK_GFLOPS, "alu", "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
+    line = dict(base, config=config, dtype="f32" if f32 else "f64", value=value, ms_per_step=ms_per_step,
+                e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
+                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                          "frac": achieved / peak, "traffic": None,
+                          "kernel": "exec_kernel (persistent dataflow executor, whole batch)", "peak_source": src},
+                exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
+    if world == 1 and rank == 0 and not args.no_cpu and not f32:
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "batch.npz")
+            sample = {}
+            for k in range(8):
+                sample[f"A{k}"] = As[k].double().cpu().numpy()
+                sample[f"cfg{k}"] = np.array(cfgs[k])
+            np.savez(path, **sample)
+            env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+            out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-batch", path,
+                                  "--cpu-seconds", str(CPU_SAMPLE_SECONDS)], env=env, capture_output=True, text=True,
+                                 timeout=600)
+            if out.returncode == 0:
+                r = json.loads(out.stdout.strip().splitlines()[-1])
+                line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
+                                        "kind": "oracle",
+                                        "sample": f"first {r['tasks']} of 512 matrices with their tuned "
+                                                  f"configurations ({r['seconds']:.1f} s), single BLAS thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +392,7 @@ def main():
     ap.add_argument("--cpu-sample", default=None)
     ap.add_argument("--cpu-seconds", type=float, default=CPU_SAMPLE_SECONDS)
     ap.add_argument("--cpu-max-tasks", type=int, default=None)
+    ap.add_argument("--cpu-sample-batch", default=None)
     ap.add_argument("--auto-resources", type=int, default=None,
                     help="R of the Auto tree (default: SMs * 32 / nb, as the library chooses)")
     args = ap.parse_args()
@@ -209,6 +401,9 @@ def main():
         args.tree = "flatts"
 
     w["resources"] = args.auto_resources
+    if args.cpu_sample_batch:
+        print(json.dumps(cpu_sample_batch(args.cpu_sample_batch, args.cpu_seconds)))
+        return 0
     if args.cpu_sample:
         r = cpu_sample(args.cpu_sample, w, args.tree, args.cpu_seconds, args.cpu_max_tasks)
         print(json.dumps(r))
@@ -220,7 +415,7 @@ def main():
 
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
-    if w["resources"] is None:
+    if w["resources"] is None and w["nb"]:
         w["resources"] = max(1, torch.cuda.get_device_properties(local).multi_processor_count * 32 // w["nb"])
     m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
     flops = metric_flops(m, n)
@@ -234,6 +429,10 @@ def main():
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if f32 else "f64", "data": "synthetic", "config": config}
 
+    if args.impl == "reference" and w["kind"] == "batch":
+        if rank != 0:
+            return 0
+        return reference_batched(args, w, base)
     if args.impl == "reference":
         # the plain CPU oracle on bounded samples of the same workload; rank 0 only
         if rank != 0:
@@ -260,6 +459,8 @@ def main():
         from paper_1611_06892_gb300 import build
         build.build()
     G.load_library()
+    if w["kind"] == "batch":
+        return run_batched(args, w, base, config, world, rank, local, device, G, torch)
 
     A = make_input(w, rank, device)
     if f32:
@@ -309,13 +510,7 @@ def main():
     exec_mean = statistics.mean(exec_ms)
     achieved = flops / (exec_mean * 1e-3) / 1e9
     if f32:
-        bf16 = 1926.3
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-                bf16 = json.load(fh).get("bf16_tflops", bf16)
-        except OSError:
-            pass
-        peak, bound, unit = bf16 * TF32_RATIO * 1e3 / 3.0, "tensor", "GFLOP/s"
+        peak, bound, unit = tf32_split_peak_gflops(), "tensor", "GFLOP/s"
         peak_src = "measured bf16 x 1.1/2.25 (TF32) / 3 products per useful flop"
     else:
         peak, bound, unit = FP64_PEAK_GFLOPS, "alu", "GFLOP/s"
@@ -324,7 +519,7 @@ def main():
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (nb + 1) * n * 8},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                          "frac": achieved / peak, "traffic": None if f32 else EXEC_TRAFFIC_BYTES,
+                          "frac": achieved / peak, "traffic": EXEC_TRAFFIC_BYTES if (not f32 and w["name"] == "square8192" and args.tree == "auto") else None,
                           "kernel": "exec_kernel (persistent dataflow executor)", "peak_source": peak_src},
                 exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
