@@ -44,6 +44,9 @@ WORKLOADS = {
                             "autotuned nb / ib / tree / variant per matrix"),
     "tall65536x2048": dict(m=65536, n=2048, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(5,),
                            desc="tall-skinny FP64 65536x2048 N(0,1), nb=256 ib=32, R-BiDiag"),
+    "grad4096x1024": dict(m=4096, n=1024, nb=256, ib=32, variant="bidiag", kind="grad", seeds=(7, 8),
+                          desc="differentiation FP64 4096x1024 N(0,1), nb=256 ib=32, BiDiag: forward reduction "
+                               "+ adjoint (dL/dA from a N(0,1) band gradient W, L = <W, B>)"),
 }
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock/SM (4 flops) x
 # 2070 MHz = 1258.6 GFLOP/s (a DFMA loop measured 1.20 TFLOP/s, cuBLAS DGEMM 1.10, FP64 MMA 1.05).
@@ -277,6 +280,143 @@ def reference_batched(args, w, base):
     return 0
 
 
+def cpu_sample_grad(path, seconds):
+    """The oracle forward + adjoint on the sample matrix of the differentiation workload."""
+    import numpy as np
+
+    from oracle import adjoint as OA
+    from oracle import bidiag as OB
+    from oracle import trees as OT
+
+    data = np.load(path)
+    A, W = data["A"], data["W"]
+    nb, ib = (int(x) for x in data["cfg"])
+    done, t0 = 0, time.perf_counter()
+    while True:
+        res = OB.bidiag_band(A, nb, ib, OT.GREEDY, OT.BIDIAG)
+        OA.band_vjp(res, W)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    m, n = A.shape
+    return {"tasks": done, "flops": done * metric_flops(m, n), "seconds": time.perf_counter() - t0, "m": m, "n": n}
+
+
+def grad_cpu_leg(w, seconds):
+    """Bounded oracle sample for the differentiation workload: the leading 1024 x 256 block with
+    nb = 64 (the same 4:1 shape and 16 x 4 tile grid), forward + adjoint, single BLAS thread."""
+    import numpy as np
+
+    from paper_1611_06892_gb300 import inputs
+    m, n, nb, ib = 1024, 256, 64, 16
+    A = inputs.gaussian(m, n, seed=w["seeds"][0])
+    W = inputs.gaussian(nb + 1, n, seed=w["seeds"][1])
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "grad.npz")
+        np.savez(path, A=A, W=W, cfg=np.array([nb, ib]))
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-grad", path, "--cpu-seconds",
+                              str(seconds)], env=env, capture_output=True, text=True, timeout=900, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    r["sample"] = (f"{r['tasks']} forward + adjoint passes of the oracle on the leading {m} x {n} block "
+                   f"(nb {nb}, ib {ib}, Greedy; {r['seconds']:.1f} s), single BLAS thread")
+    return r
+
+
+def run_grad(args, w, base, config, world, rank, local, device, G, torch):
+    """The differentiation workload: one step = the forward reduction and its adjoint."""
+    f32 = args.precision == "f32"
+    dt = torch.float32 if f32 else torch.float64
+    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
+    from paper_1611_06892_gb300 import inputs
+    A = inputs.torch_gaussian(m, n, w["seeds"][0] + 1000 * rank, device)
+    if f32:
+        A = A.float().t().contiguous().t()
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w["seeds"][1] + 1000 * rank)
+    W = torch.randn((n, nb + 1), dtype=dt, device=device, generator=gen).t()
+    tree = "greedy" if args.tree == "auto" else args.tree
+    config = dict(config, workload=w["desc"].replace("FP64", "FP32 storage (3xTF32 updates)") if f32 else w["desc"],
+                  tree=tree, l2=f"input {m * n * A.element_size() / 2**20:.0f} MiB (the adjoint's working "
+                  "set, 3 copies of A plus partial sums, exceeds the 129 MB L2; no flush)")
+    config.pop("auto_resources", None)
+    h = G.Handle(device=local)
+    h.set_option(G.OPT_TIMING, 1)
+
+    def step():
+        r = h.band(A, nb, ib, tree, w["variant"])
+        h.sync()
+        fms = h.last_exec_ms()
+        Ab = r.backward(W)
+        h.sync()
+        bms = h.last_exec_ms()
+        r.free()
+        del Ab
+        return fms, bms
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(h.stream)
+    ms = [step() for _ in range(args.steps)]
+    e1.record(h.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    el_ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    flops = metric_flops(m, n)
+    ms_per_step = el_ms / args.steps
+    value = world * flops / (ms_per_step * 1e-3) / 1e12
+    # end to end: A from pinned host memory, forward, adjoint, dL/dA back to pinned host memory
+    A_host = torch.empty((n, m), dtype=dt, pin_memory=True).t()
+    A_host.copy_(A)
+    G_host = torch.empty((n, m), dtype=dt, pin_memory=True).t()
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        barrier(world)
+        t0 = time.perf_counter()
+        Ad = A_host.to(device, non_blocking=True)
+        r = h.band(Ad, nb, ib, tree, w["variant"])
+        Ab = r.backward(W)
+        G_host.copy_(Ab, non_blocking=True)
+        h.sync()
+        torch.cuda.current_stream(device).synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        r.free()
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device) if e2e_t else None
+    fwd_ms = statistics.mean(x[0] for x in ms)
+    bwd_ms = statistics.mean(x[1] for x in ms)
+    # the adjoint executor's algorithmic work: every update block is undone on the state and on the
+    # gradient and contributes its partial products (three times the forward's update flops)
+    bwd_flops = 3.0 * flops
+    achieved = bwd_flops / (bwd_ms * 1e-3) / 1e9
+    if f32:
+        peak, bound, src = tf32_split_peak_gflops(), "tensor", "measured bf16 x 1.1/2.25 (TF32) / 3"
+    else:
+        peak, bound, src = FP64_PEAK_GFLOPS, "alu", "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
+    line = dict(base, config=config, dtype="f32" if f32 else "f64", value=value, ms_per_step=ms_per_step,
+                e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
+                     "h2d_bytes_per_step": m * n * A.element_size(), "d2h_bytes_per_step": m * n * A.element_size()},
+                roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                          "frac": achieved / peak, "traffic": None,
+                          "kernel": "exec_kernel adjoint instantiation (reverse sweep), 3 x (4mn^2 - 4n^3/3) flops",
+                          "peak_source": src},
+                forward_exec_ms=fwd_ms, backward_exec_ms=bwd_ms, backward_over_forward=bwd_ms / fwd_ms,
+                gpu_launches=(7 if w["variant"] == "bidiag" else 8) * args.steps, clocks=clocks)
+    if world == 1 and rank == 0 and not args.no_cpu and not f32:
+        r = grad_cpu_leg(w, CPU_SAMPLE_SECONDS)
+        line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
+                                "kind": "oracle", "sample": r["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     """The batched workload: 512 uneven matrices reduced in one persistent launch per step."""
     import numpy as np
@@ -393,6 +533,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=CPU_SAMPLE_SECONDS)
     ap.add_argument("--cpu-max-tasks", type=int, default=None)
     ap.add_argument("--cpu-sample-batch", default=None)
+    ap.add_argument("--cpu-sample-grad", default=None)
     ap.add_argument("--auto-resources", type=int, default=None,
                     help="R of the Auto tree (default: SMs * 32 / nb, as the library chooses)")
     args = ap.parse_args()
@@ -401,6 +542,9 @@ def main():
         args.tree = "flatts"
 
     w["resources"] = args.auto_resources
+    if args.cpu_sample_grad:
+        print(json.dumps(cpu_sample_grad(args.cpu_sample_grad, args.cpu_seconds)))
+        return 0
     if args.cpu_sample_batch:
         print(json.dumps(cpu_sample_batch(args.cpu_sample_batch, args.cpu_seconds)))
         return 0
@@ -433,6 +577,19 @@ def main():
         if rank != 0:
             return 0
         return reference_batched(args, w, base)
+    if args.impl == "reference" and w["kind"] == "grad":
+        if rank != 0:
+            return 0
+        per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+        res = [grad_cpu_leg(w, per_step) for _ in range(args.warmup + args.steps)][args.warmup:]
+        val = sum(r["flops"] for r in res) / sum(r["seconds"] for r in res) / 1e12
+        line = dict(base, impl="reference", value=val, ms_per_step=1e3 * statistics.mean(r["seconds"] for r in res),
+                    cpu_baseline={"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                                  "sample": res[0]["sample"]},
+                    e2e={"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                    gpu_launches=0)
+        print(json.dumps(line), flush=True)
+        return 0
     if args.impl == "reference":
         # the plain CPU oracle on bounded samples of the same workload; rank 0 only
         if rank != 0:
@@ -461,6 +618,8 @@ def main():
     G.load_library()
     if w["kind"] == "batch":
         return run_batched(args, w, base, config, world, rank, local, device, G, torch)
+    if w["kind"] == "grad":
+        return run_grad(args, w, base, config, world, rank, local, device, G, torch)
 
     A = make_input(w, rank, device)
     if f32:

@@ -227,6 +227,30 @@ int bidiag_apply_q_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nc
 int bidiag_apply_p_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, float* d_C,
                        int64_t ldc);
 
+/*
+ * Adjoint (reverse-mode derivative) of a reduction: given dL/dB in band storage (d_abbar, (nb+1) x n,
+ * leading dimension ldab >= nb+1, the layout of bidiag_result_band; entries with row index < 0 are
+ * ignored), writes dL/dA to d_Abar (m x n, column-major, ldabar >= m).  If d_Arec is not NULL it also
+ * receives the reconstruction of A from the band and the reflectors (ldarec >= m), a by-product.
+ * The reduction of Sec. 3.4 / 3.5 is a sequence of Householder steps M <- H(x) M (LQ steps on M^T); the
+ * adjoint walks them backwards over the result's stored reflectors (V tiles and T), undoing each step on
+ * a working copy of the state (H is its own inverse) and applying the chain rule through H and through
+ * the reflector's construction from its pivot column.  The paper has no derivative; this is its exact
+ * reverse mode, with a reflector of tau = 0 (a zero column, where the Householder map switches branch)
+ * held constant.  The result must come from this handle and is not modified; FP64 results only
+ * (FP32 ones: bidiag_band_backward_f32).  Device memory: two copies of the tiled matrix plus partial
+ * sums (about nb^2 + nb ib elements per update strip of the reduction), allocated and freed on the
+ * handle's stream.  Errors: -2 result, -3 d_abbar NULL, -4 ldab, -5 d_Abar NULL, -6 ldabar, -8 ldarec,
+ * BIDIAG_ERR_UNSUPPORTED when nb / ib need more shared memory than a block has (nb = 256 needs
+ * ib <= 32), BIDIAG_ERR_NOMEM, BIDIAG_ERR_CUDA.  Stream-ordered: call bidiag_sync before reading.
+ */
+int bidiag_band_backward(bidiag_handle h, bidiag_result_t r, const double* d_abbar, int64_t ldab,
+                         double* d_Abar, int64_t ldabar, double* d_Arec, int64_t ldarec);
+/* The same for a result with FP32 storage (band_f32 / band_batched_f32); the reflector derivatives
+ * and the Householder-construction step are evaluated in FP64, the updates as in the forward. */
+int bidiag_band_backward_f32(bidiag_handle h, bidiag_result_t r, const float* d_abbar, int64_t ldab,
+                             float* d_Abar, int64_t ldabar, float* d_Arec, int64_t ldarec);
+
 /* Waits for the handle's stream and returns the device-side status of the work enqueued since the
  * last call: BIDIAG_OK, BIDIAG_ERR_TIMEOUT (a dependency wait ran out; the context stays usable) or
  * BIDIAG_ERR_CUDA. */
@@ -287,6 +311,20 @@ int bidiag_plan_choose_variant(int64_t p, int64_t q, int tree, int64_t resources
 int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
                         int strip_w, int32_t* program, int64_t cap, int64_t* count, int32_t* deps,
                         int64_t dcap, int64_t* ndeps, int32_t* strip_w_used);
+
+/* Host-only query of the adjoint program bidiag_band_backward runs for these arguments (same rules as
+ * bidiag_plan_program; strip_w is rounded to a multiple of ib): *count sub-tasks of 8 int32 in queue
+ * order (op, x, a, c, tslot, dep_begin, dep_end, flags; op type 9 = undo a panel block, 10 = undo a
+ * panel-block update, 11 = undo an update strip, 12 = no-op for a COPY; x = reflector tile of the
+ * forward result, a / c = state tiles of the m x n grid, flags = partial slot), fwd[y] = the forward
+ * queue position it undoes, *ndeps dependency indices, *nslot_off slot offsets (the last one is the
+ * total number of elements) and *npinfo = 4 per panel task (first update slot, number of update
+ * slots, first panel-update slot, 0).  Arrays are filled only when their capacity suffices.  Errors as
+ * bidiag_plan_program, -10 for a NULL count pointer. */
+int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
+                         int strip_w, int32_t* program, int32_t* fwd, int64_t cap, int64_t* count,
+                         int32_t* deps, int64_t dcap, int64_t* ndeps, int64_t* slot_off, int64_t scap,
+                         int64_t* nslot_off, int32_t* pinfo, int64_t pcap, int64_t* npinfo);
 
 #ifdef __cplusplus
 }

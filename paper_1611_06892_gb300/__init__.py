@@ -69,6 +69,8 @@ def load_library(path=LIB_PATH):
         "bidiag_apply_q_f32": (cint, [vp, vp, cint, i64, vp, i64]),
         "bidiag_apply_p_f32": (cint, [vp, vp, cint, i64, vp, i64]),
         "bidiag_band_noalloc": (cint, [i64, i64, vp, i64, cint, cint, cint, cint, vp, i64, vp]),
+        "bidiag_band_backward": (cint, [vp, vp, vp, i64, vp, i64, vp, i64]),
+        "bidiag_band_backward_f32": (cint, [vp, vp, vp, i64, vp, i64, vp, i64]),
         "bidiag_result_band": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
         "bidiag_result_tasks": (cint, [vp, P(P(i32)), P(i64)]),
         "bidiag_result_reflectors": (cint, [vp, P(Reflectors)]),
@@ -85,6 +87,8 @@ def load_library(path=LIB_PATH):
         "bidiag_plan_choose_variant": (cint, [i64, i64, cint, i64, P(cint), P(i64), P(i64)]),
         "bidiag_plan_program": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), i64, P(i64), P(i32),
                                        i64, P(i64), P(i32)]),
+        "bidiag_plan_backward": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), P(i32), i64, P(i64),
+                                        P(i32), i64, P(i64), P(i64), i64, P(i64), P(i32), i64, P(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -168,6 +172,14 @@ def bidiag_apply_p_f32(h, r, trans, nrows, d_C, ldc):
     _check(h, load_library().bidiag_apply_p_f32(h, r, trans, nrows, d_C, ldc))
 
 
+def bidiag_band_backward(h, r, d_abbar, ldab, d_Abar, ldabar, d_Arec=None, ldarec=1):
+    _check(h, load_library().bidiag_band_backward(h, r, d_abbar, ldab, d_Abar, ldabar, d_Arec, ldarec))
+
+
+def bidiag_band_backward_f32(h, r, d_abbar, ldab, d_Abar, ldabar, d_Arec=None, ldarec=1):
+    _check(h, load_library().bidiag_band_backward_f32(h, r, d_abbar, ldab, d_Abar, ldabar, d_Arec, ldarec))
+
+
 def bidiag_result_free(r):
     load_library().bidiag_result_free(r)
 
@@ -224,6 +236,29 @@ def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
                                          cnt.value, ctypes.byref(cnt), deps.ctypes.data_as(I32), nd.value,
                                          ctypes.byref(nd), ctypes.byref(w)))
     return prog[:cnt.value], deps[:nd.value], w.value
+
+
+def bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
+    """Adjoint program of a reduction: (sub-tasks (count x 8), forward position of each, dependency
+    array, slot offsets, per-panel slot table (npanels x 4))."""
+    lib = load_library()
+    cnt, nd, ns, npi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    I64 = ctypes.POINTER(ctypes.c_int64)
+    args = (m, n, nb, ib, tree, variant, resources, strip_w)
+    _check(None, lib.bidiag_plan_backward(*args, None, None, 0, ctypes.byref(cnt), None, 0, ctypes.byref(nd), None, 0,
+                                          ctypes.byref(ns), None, 0, ctypes.byref(npi)))
+    prog = np.zeros((max(cnt.value, 1), 8), dtype=np.int32)
+    fwd = np.zeros(max(cnt.value, 1), dtype=np.int32)
+    deps = np.zeros(max(nd.value, 1), dtype=np.int32)
+    slot = np.zeros(max(ns.value, 1), dtype=np.int64)
+    pinfo = np.zeros(max(npi.value, 1), dtype=np.int32)
+    _check(None, lib.bidiag_plan_backward(*args, prog.ctypes.data_as(I32), fwd.ctypes.data_as(I32), cnt.value,
+                                          ctypes.byref(cnt), deps.ctypes.data_as(I32), nd.value, ctypes.byref(nd),
+                                          slot.ctypes.data_as(I64), ns.value, ctypes.byref(ns),
+                                          pinfo.ctypes.data_as(I32), npi.value, ctypes.byref(npi)))
+    return (prog[:cnt.value], fwd[:cnt.value], deps[:nd.value], slot[:ns.value],
+            pinfo[:npi.value].reshape(-1, 4))
 
 
 # ---- torch-facing wrappers ---------------------------------------------------------------------
@@ -399,6 +434,24 @@ class Result:
         if Cc.data_ptr() != C.data_ptr():
             C.copy_(Cc)
         return C
+
+    def backward(self, ab_bar, reconstruct=False):
+        """dL/dA (m x n, column-major tensor) from dL/dB in band storage ((nb + 1) x n); with
+        reconstruct=True also the reconstruction of A from the band and the reflectors."""
+        import torch
+        m = int(self.desc.m)
+        dt = torch.float64 if self.esize == 8 else torch.float32
+        if ab_bar.dtype != dt:
+            raise TypeError("band gradient must have the result's dtype")
+        Gc, ldg = _colmajor(ab_bar)
+        dev = ab_bar.device
+        Abar = torch.empty((self.n, m), dtype=dt, device=dev).t()
+        Arec = torch.empty((self.n, m), dtype=dt, device=dev).t() if reconstruct else None
+        fn = bidiag_band_backward if self.esize == 8 else bidiag_band_backward_f32
+        fn(self.handle.h, self.r, ctypes.c_void_p(Gc.data_ptr()), ldg, ctypes.c_void_p(Abar.data_ptr()), max(m, 1),
+           ctypes.c_void_p(Arec.data_ptr()) if reconstruct else None, max(m, 1))
+        self._grad_keep = Gc     # stream-ordered use: keep the input alive until the next call
+        return (Abar, Arec) if reconstruct else Abar
 
     def free(self):
         if self.r:

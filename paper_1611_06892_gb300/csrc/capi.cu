@@ -22,8 +22,11 @@
 
 namespace {
 
+struct BwdDev;
+
 struct PlanDev {
   bd::Plan plan;
+  std::shared_ptr<BwdDev> bwd;   // adjoint program of this plan, built on first use
   bd::DevTask* d_tasks = nullptr;
   int32_t* d_deps = nullptr;
   int* d_done = nullptr;
@@ -33,6 +36,18 @@ struct PlanDev {
     if (d_tasks) cudaFree(d_tasks);
     if (d_deps) cudaFree(d_deps);
     if (d_done) cudaFree(d_done);
+  }
+};
+
+// Adjoint program (reverse sweep) of a plan and its slot tables on the device.
+struct BwdDev {
+  bd::BwdPlan bp;
+  PlanDev prog;                  // only the device program arrays are used
+  int64_t* d_slot_off = nullptr;
+  int32_t* d_pinfo = nullptr;
+  ~BwdDev() {
+    if (d_slot_off) cudaFree(d_slot_off);
+    if (d_pinfo) cudaFree(d_pinfo);
   }
 };
 
@@ -140,11 +155,13 @@ int64_t resources_of(bidiag_handle h, int nb, int w) {
 // Executor launch of a program held in pd with the given buffers.
 int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n0, void* b1, int64_t n1, void* b2,
              int64_t n2, void* T, int npanels, int nb, int ib, int w, int esize, bool timed = false,
-             const bd::MatInfo* d_mats = nullptr, int nmats = 0, size_t smem_batch = 0) {
+             const bd::MatInfo* d_mats = nullptr, int nmats = 0, size_t smem_batch = 0,
+             const void* const* bx = nullptr, const int64_t* nx = nullptr, const bd::BwdParams* bwd = nullptr) {
   if (ntasks == 0) return BIDIAG_OK;
-  const size_t smem = d_mats ? smem_batch : bd::exec_smem_bytes(nb, ib, w, esize);
-  CK(h, bd::exec_set_smem(smem, esize));
-  const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem, esize));
+  const size_t smem = d_mats ? smem_batch
+                             : (bwd ? bd::bwd_smem_bytes(nb, ib, bwd->hw, esize) : bd::exec_smem_bytes(nb, ib, w, esize));
+  CK(h, bd::exec_set_smem(smem, esize, bwd != nullptr));
+  const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem, esize, bwd != nullptr));
   bd::ExecParams prm{};
   prm.tasks = pd.d_tasks;
   prm.deps = pd.d_deps;
@@ -156,6 +173,11 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   prm.buf[0] = b0; prm.ntiles[0] = n0;
   prm.buf[1] = b1; prm.ntiles[1] = n1;
   prm.buf[2] = b2; prm.ntiles[2] = n2;
+  for (int i = 0; i < 3; ++i) {   // buffers 3..5 (adjoint only)
+    prm.buf[3 + i] = bx ? const_cast<void*>(bx[i]) : nullptr;
+    prm.ntiles[3 + i] = nx ? nx[i] : 0;
+  }
+  if (bwd) prm.bwd = *bwd;
   prm.T = T;
   prm.npanels = npanels;
   prm.nb = nb;
@@ -439,6 +461,112 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   return BIDIAG_OK;
 }
 
+
+// Adjoint of a reduction: dL/dA from dL/dB (band storage) by the reverse sweep over the result's
+// reflectors.  The working state starts as [B; 0] and the gradient as the band gradient, both tiled
+// like A; after the sweep they hold the reconstruction of A and dL/dA.
+template <typename E>
+int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t ldab, E* d_Abar, int64_t ldabar,
+                  E* d_Arec, int64_t ldarec) {
+  if (!h) return -1;
+  if (!r || !r->pd) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result belongs to another handle");
+  if (r->esize != (int)sizeof(E)) return fail(h, -2, "result has the other storage precision");
+  if (!d_abbar) return fail(h, -3, "band gradient is NULL");
+  if (ldab < r->nb + 1) return fail(h, -4, "ldab < nb + 1");
+  if (!d_Abar) return fail(h, -5, "A_bar is NULL");
+  if (ldabar < r->m) return fail(h, -6, "ldabar < m");
+  if (d_Arec && ldarec < r->m) return fail(h, -8, "ldarec < m");
+  CK(h, cudaSetDevice(h->device));
+  const bd::Plan& pl = r->pd->plan;
+  const int nb = r->nb, ib = r->ib, esize = (int)sizeof(E);
+  const int hw = bd::choose_bwd_chunk(nb, ib, pl.strip_w, h->smem_optin, esize);
+  if (!hw) return fail(h, BIDIAG_ERR_UNSUPPORTED, "the adjoint of this tile size / inner blocking needs more shared memory");
+  if (!r->pd->bwd) {
+    auto bw = std::make_shared<BwdDev>();
+    try {
+      bd::build_backward(pl, bw->bp);
+    } catch (const std::bad_alloc&) {
+      return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning the adjoint");
+    } catch (const std::exception& e) {
+      return fail(h, BIDIAG_ERR_UNSUPPORTED, std::string("adjoint planner: ") + e.what());
+    }
+    int rc = upload_program(h, bw->prog, bw->bp.dev, bw->bp.deps, 1);
+    if (rc) return rc;
+    CK(h, cudaMalloc(&bw->d_slot_off, bw->bp.slot_off.size() * sizeof(int64_t)));
+    CK(h, cudaMalloc(&bw->d_pinfo, bw->bp.pinfo.size() * sizeof(int32_t)));
+    CK(h, cudaMemcpy(bw->d_slot_off, bw->bp.slot_off.data(), bw->bp.slot_off.size() * sizeof(int64_t),
+                     cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(bw->d_pinfo, bw->bp.pinfo.data(), bw->bp.pinfo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    r->pd->bwd = bw;
+  }
+  const BwdDev& bw = *r->pd->bwd;
+  // Working state and gradient, tiled like the forward's buffers: S / G mirror the A tiles (p x q);
+  // for R-BiDiag, S2 / G2 mirror the R copy (q x q).  Start: the band lives in the last buffer the
+  // forward wrote (A tiles for BiDiag, the R copy for R-BiDiag); for R-BiDiag the A tiles' state is the
+  // pre-QR's R factor, which the forward leaves in the upper part of its tiles.
+  const bool rb = r->tiles2 != nullptr;
+  const int64_t ntiles = (int64_t)r->p * r->q, ntiles2 = rb ? (int64_t)r->q * r->q : 0;
+  const size_t tile_elems = (size_t)nb * nb;
+  E *S = nullptr, *G = nullptr, *S2 = nullptr, *G2 = nullptr, *part = nullptr, *red = nullptr;
+  int rc = dev_alloc(h, &S, (size_t)ntiles * tile_elems);
+  if (!rc) rc = dev_alloc(h, &G, (size_t)ntiles * tile_elems);
+  if (!rc && rb) rc = dev_alloc(h, &S2, (size_t)ntiles2 * tile_elems);
+  if (!rc && rb) rc = dev_alloc(h, &G2, (size_t)ntiles2 * tile_elems);
+  if (!rc) rc = dev_alloc(h, &part, (size_t)std::max<int64_t>(1, bw.bp.slot_off.back()));
+  if (!rc) rc = dev_alloc(h, &red, (size_t)std::max(1, pl.npanels) * tile_elems);
+  auto release = [&]() {
+    for (E* x : {S, G, S2, G2, part, red})
+      if (x) cudaFreeAsync(x, h->stream);
+  };
+  if (rc) {
+    release();
+    return rc;
+  }
+  cudaError_t e = cudaMemsetAsync(G, 0, (size_t)ntiles * tile_elems * esize, h->stream);
+  if (e == cudaSuccess && !rb) e = cudaMemsetAsync(S, 0, (size_t)ntiles * tile_elems * esize, h->stream);
+  if (e == cudaSuccess && rb) e = cudaMemsetAsync(S2, 0, (size_t)ntiles2 * tile_elems * esize, h->stream);
+  if (e == cudaSuccess && rb) e = cudaMemsetAsync(G2, 0, (size_t)ntiles2 * tile_elems * esize, h->stream);
+  if (e == cudaSuccess && rb) e = bd::launch_r_part(static_cast<const E*>(r->tiles), S, r->p, r->q, nb, h->stream);
+  if (e == cudaSuccess)
+    e = bd::launch_scatter_band(static_cast<const E*>(r->ab), r->ldab, nb, r->n, rb ? S2 : S, rb ? r->q : r->p,
+                                h->stream);
+  if (e == cudaSuccess) e = bd::launch_scatter_band(d_abbar, ldab, nb, r->n, rb ? G2 : G, rb ? r->q : r->p, h->stream);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(h, e, "adjoint set-up");
+  }
+  const bool timed = h->timing != 0;
+  if (timed && !h->ev[0]) {
+    e = cudaEventCreate(&h->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(h, e, "cudaEventCreate");
+    }
+  }
+  bd::BwdParams bp{};
+  bp.part = part;
+  bp.slot_off = bw.d_slot_off;
+  bp.nslots = (int32_t)(bw.bp.slot_off.size() - 1);
+  bp.pinfo = bw.d_pinfo;
+  bp.red = red;
+  bp.hw = hw;
+  const void* bx[3] = {S2, G, G2};
+  const int64_t nx[3] = {ntiles2, ntiles, ntiles2};
+  rc = run_exec(h, bw.prog, (int)bw.bp.dev.size(), r->tiles, ntiles, r->tiles2, ntiles2, S, ntiles, r->T, pl.npanels,
+                nb, ib, pl.strip_w, esize, timed, nullptr, 0, 0, bx, nx, &bp);
+  h->timed = timed;
+  if (rc) {
+    release();
+    return rc;
+  }
+  e = bd::launch_unpack(G, r->p, nb, r->m, r->n, d_Abar, ldabar, h->stream);
+  if (e == cudaSuccess && d_Arec) e = bd::launch_unpack(S, r->p, nb, r->m, r->n, d_Arec, ldarec, h->stream);
+  release();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint unpack");
+  return BIDIAG_OK;
+}
 
 // Batched form: `count` independent reductions in one persistent launch.  Each matrix keeps its own
 // plan (tile size, tree, variant); the device programs are merged by critical-path priority and every
@@ -847,6 +975,16 @@ int bidiag_apply_q_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nc
   return apply_side(h, r, true, trans, ncols, d_C, ldc);
 }
 
+int bidiag_band_backward(bidiag_handle h, bidiag_result_t r, const double* d_abbar, int64_t ldab, double* d_Abar,
+                         int64_t ldabar, double* d_Arec, int64_t ldarec) {
+  return backward_impl<double>(h, r, d_abbar, ldab, d_Abar, ldabar, d_Arec, ldarec);
+}
+
+int bidiag_band_backward_f32(bidiag_handle h, bidiag_result_t r, const float* d_abbar, int64_t ldab, float* d_Abar,
+                             int64_t ldabar, float* d_Arec, int64_t ldarec) {
+  return backward_impl<float>(h, r, d_abbar, ldab, d_Abar, ldabar, d_Arec, ldarec);
+}
+
 int bidiag_apply_p(bidiag_handle h, bidiag_result_t r, int trans, int64_t nrows, double* d_C, int64_t ldc) {
   if (!h) return -1;
   if (!r) return fail(h, -2, "result is NULL");
@@ -1022,6 +1160,40 @@ int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int vari
     if (strip_w_used) *strip_w_used = pl.strip_w;
     if (program && cap >= *count) std::memcpy(program, pl.dev.data(), pl.dev.size() * sizeof(bd::DevTask));
     if (deps && dcap >= *ndeps) std::memcpy(deps, pl.deps.data(), pl.deps.size() * sizeof(int32_t));
+  } catch (const std::bad_alloc&) {
+    return BIDIAG_ERR_NOMEM;
+  } catch (...) {
+    return BIDIAG_ERR_UNSUPPORTED;
+  }
+  return BIDIAG_OK;
+}
+
+int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources, int strip_w,
+                         int32_t* program, int32_t* fwd, int64_t cap, int64_t* count, int32_t* deps, int64_t dcap,
+                         int64_t* ndeps, int64_t* slot_off, int64_t scap, int64_t* nslot_off, int32_t* pinfo,
+                         int64_t pcap, int64_t* npinfo) {
+  if (m < 1 || n < 1 || m < n) return -1;
+  if (nb < 1 || nb > bd::kMaxNb) return -3;
+  if (ib < 1 || nb % ib) return -4;
+  if (tree < 0 || tree > 3) return -5;
+  if (variant < 0 || variant > 1) return -6;
+  if (!count || !ndeps || !nslot_off || !npinfo) return -10;
+  int w = std::max(ib, (strip_w / ib) * ib);
+  w = std::min(w, nb);
+  try {
+    bd::Plan pl;
+    bd::build_plan(pl, m, n, nb, ib, tree, variant, resources, w);
+    bd::BwdPlan bp;
+    bd::build_backward(pl, bp);
+    *count = (int64_t)bp.dev.size();
+    *ndeps = (int64_t)bp.deps.size();
+    *nslot_off = (int64_t)bp.slot_off.size();
+    *npinfo = (int64_t)bp.pinfo.size();
+    if (program && cap >= *count) std::memcpy(program, bp.dev.data(), bp.dev.size() * sizeof(bd::DevTask));
+    if (fwd && cap >= *count) std::memcpy(fwd, bp.fwd.data(), bp.fwd.size() * sizeof(int32_t));
+    if (deps && dcap >= *ndeps) std::memcpy(deps, bp.deps.data(), bp.deps.size() * sizeof(int32_t));
+    if (slot_off && scap >= *nslot_off) std::memcpy(slot_off, bp.slot_off.data(), bp.slot_off.size() * sizeof(int64_t));
+    if (pinfo && pcap >= *npinfo) std::memcpy(pinfo, bp.pinfo.data(), bp.pinfo.size() * sizeof(int32_t));
   } catch (const std::bad_alloc&) {
     return BIDIAG_ERR_NOMEM;
   } catch (...) {

@@ -80,7 +80,8 @@ struct Layout {
   int lp, lv, lc;            // col-major panel ld; row-major V ld; row-major C / W ld
   int P, V, Cs, Ct, Rt, Tb, G, W, W2, total;
 };
-constexpr int kHeaderDoubles = 64 + 32;   // tau[<= 64], red[32]
+// tau[<= 64], red[32]; the adjoint panel also uses three more arrays of 64 doubles
+constexpr int kHeaderDoubles = 64 + 32 + 3 * 64;
 __host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
 __host__ __device__ inline Layout layout_panel(int nb, int ib, int esize) {
   Layout L{};
@@ -108,6 +109,48 @@ __host__ __device__ inline Layout layout_update(int nb, int ib, int w, int esize
   L.W = o;   o = align4(o + ib * L.lc);
   L.W2 = o;  o = align4(o + ib * L.lc);
   L.P = L.Rt = L.G = -1;
+  L.total = o;
+  return L;
+}
+
+// Adjoint sub-tasks.  Update adjoint: state and gradient rows of a column chunk (hw columns), the
+// top rows of both, one reflector block and T, and three ib x hw products.  Panel adjoint: reflector
+// tails, state and gradient of one column block (column-major, ld lp), the top triangles and S.
+struct BwdLayout {
+  int lc, lv, lp;
+  int Cs, Cg, Cts, Ctg, V, Tb, W, W2s, W2g, Ms, Mg, Rts, Rtg, Sb, total;
+};
+__host__ __device__ inline BwdLayout layout_bwd_update(int nb, int ib, int hw, int esize) {
+  BwdLayout L{};
+  L.lc = rm_ld(hw, esize);
+  L.lv = rm_ld(ib, esize);
+  L.lp = 0;
+  int o = 0;
+  L.Cs = o;  o = align4(o + nb * L.lc);
+  L.Cg = o;  o = align4(o + nb * L.lc);
+  L.Cts = o; o = align4(o + ib * L.lc);
+  L.Ctg = o; o = align4(o + ib * L.lc);
+  L.V = o;   o = align4(o + nb * L.lv);
+  L.Tb = o;  o = align4(o + ib * ib);
+  L.W = o;   o = align4(o + ib * L.lc);
+  L.W2s = o; o = align4(o + ib * L.lc);
+  L.W2g = o; o = align4(o + ib * L.lc);
+  L.Ms = L.Mg = L.Rts = L.Rtg = L.Sb = -1;
+  L.total = o;
+  return L;
+}
+__host__ __device__ inline BwdLayout layout_bwd_panel(int nb, int ib, int esize) {
+  BwdLayout L{};
+  L.lp = odd_ld(nb);
+  L.lc = L.lv = 0;
+  int o = 0;
+  L.V = o;   o = align4(o + L.lp * ib);
+  L.Ms = o;  o = align4(o + L.lp * ib);
+  L.Mg = o;  o = align4(o + L.lp * ib);
+  L.Rts = o; o = align4(o + ib * ib);
+  L.Rtg = o; o = align4(o + ib * ib);
+  L.Sb = o;  o = align4(o + ib * ib);
+  L.Cs = L.Cg = L.Cts = L.Ctg = L.Tb = L.W = L.W2s = L.W2g = -1;
   L.total = o;
   return L;
 }
@@ -630,6 +673,271 @@ __device__ void task_update(unsigned char* smb, int type, const E* X, E* Cp, E* 
   store_tile(Cs + row_lo * L.lc, L.lc, 1, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Adjoint of the reduction (reverse sweep).  Each Householder step of the forward sweep is
+// M' = H(x) M on the rows it acts on, H = I - tau v v^T, x its pivot column, H x = beta e_1.  Going
+// backwards with the gradient G' of M':  M = H M' (H is its own inverse), G = H G', and the
+// reflector's derivatives  tau_bar = -a.b,  v_bar = -tau (G' a + M b)  with a = M^T v, b = G'^T v,
+// summed over every column the reflector was applied to, then pushed through house() into the pivot
+// column.  For a compact-WY block (V, T) applied to columns C as C' = Q^T C, Q = I - V T V^T:
+//   undoing it is C = Q C' (T applied as T: W2s = T V^T C' = -Z with Z_k = tau_k v_k^T M_k),
+//   the gradient is G = Q G' (W2g = T V^T G' = Y with Y_k = tau_k v_k^T G_k),
+// where M_k / G_k are the column states around reflector k.  Writing M_k and G_k through V, Z, Y
+// gives, for the reflectors of the block,
+//   v_bar_k = -(P')_k + sum_{l <= k} v_l D_lk,   tau_bar_k = -S_kk / tau_k^2,
+//   P' = C W2g^T - G W2s^T (pre-step state and gradient),  S = -W2g W2s^T,
+//   D_lk = S_kl - S_lk (l < k),  D_kk = -S_kk,
+// all sums over columns, so every column chunk adds its P' and S to a partial slot.
+// ---------------------------------------------------------------------------------------------
+template <typename E>
+__device__ void bwd_partial(const E* Cs, const E* Cg, int lc, int vrows, int kb, int nc, const E* W2s, const E* W2g,
+                            E* P, E* S, bool accumulate) {
+  if ((kb & 3) == 0) {
+    const int nunits = vrows * (kb >> 2);
+    for (int u = threadIdx.x; u < nunits; u += kThreads) {
+      const int r = u % vrows, k0 = (u / vrows) << 2;
+      E a0 = E(0), a1 = E(0), a2 = E(0), a3 = E(0);
+      const E* cs = Cs + r * lc;
+      const E* cg = Cg + r * lc;
+      for (int c = 0; c < nc; ++c) {
+        const E x = cs[c], y = -cg[c];
+        a0 = fma(x, W2g[k0 * lc + c], fma(y, W2s[k0 * lc + c], a0));
+        a1 = fma(x, W2g[(k0 + 1) * lc + c], fma(y, W2s[(k0 + 1) * lc + c], a1));
+        a2 = fma(x, W2g[(k0 + 2) * lc + c], fma(y, W2s[(k0 + 2) * lc + c], a2));
+        a3 = fma(x, W2g[(k0 + 3) * lc + c], fma(y, W2s[(k0 + 3) * lc + c], a3));
+      }
+      E* pp = P + (size_t)r * kb + k0;
+      if (accumulate) {
+        a0 += ldg(pp); a1 += ldg(pp + 1); a2 += ldg(pp + 2); a3 += ldg(pp + 3);
+      }
+      stg(pp, a0); stg(pp + 1, a1); stg(pp + 2, a2); stg(pp + 3, a3);
+    }
+  } else {
+    for (int u = threadIdx.x; u < vrows * kb; u += kThreads) {
+      const int r = u % vrows, k = u / vrows;
+      E a = E(0);
+      for (int c = 0; c < nc; ++c) a = fma(Cs[r * lc + c], W2g[k * lc + c], fma(-Cg[r * lc + c], W2s[k * lc + c], a));
+      E* pp = P + (size_t)r * kb + k;
+      if (accumulate) a += ldg(pp);
+      stg(pp, a);
+    }
+  }
+  for (int u = threadIdx.x; u < kb * kb; u += kThreads) {
+    const int a = u / kb, k = u % kb;
+    E v = E(0);
+    for (int c = 0; c < nc; ++c) v = fma(-W2g[a * lc + c], W2s[k * lc + c], v);
+    if (accumulate) v += ldg(S + u);
+    stg(S + u, v);
+  }
+}
+
+// Adjoint of an update (UNMQR / TSMQR / TTMQR strip, or PU(b, s) with C = the panel tile): blocks
+// [blk0, blk1) are undone in decreasing order on the state (C_s, Cp_s) and the gradient (C_g, Cp_g) of
+// columns [col0, col0 + ncols), chunk by chunk, and each block's P' (vrows x ib, row-major) and S
+// (ib x ib) go to the slot: block beta at (beta - blk0) nb ib, its S after all P blocks.
+template <typename E>
+__device__ void task_bwd_update(unsigned char* smb, int type, const E* X, E* Cp_s, E* C_s, E* Cp_g, E* C_g, int tr,
+                                const E* Tg, int nb, int ib, int hw, int blk0, int blk1, int col0, int ncols, E* slot,
+                                bool simt) {
+  const BwdLayout L = layout_bwd_update(nb, ib, hw, (int)sizeof(E));
+  E* sm = reinterpret_cast<E*>(smb + kHeaderDoubles * sizeof(double));
+  E *Cs = sm + L.Cs, *Cg = sm + L.Cg, *Cts = sm + L.Cts, *Ctg = sm + L.Ctg, *V = sm + L.V, *Tb = sm + L.Tb;
+  E *W = sm + L.W, *W2s = sm + L.W2s, *W2g = sm + L.W2g;
+  const int lc = L.lc, lv = L.lv;
+  const int row_lo = (type == UNMQR) ? blk0 * ib : 0;
+  const int row_hi = (type == TTMQR) ? blk1 * ib : nb;
+  const int nbk = blk1 - blk0;
+  const size_t pstride = (size_t)nb * ib, sbase = (size_t)nbk * nb * ib;
+  for (int ch = 0; ch < ncols; ch += hw) {
+    const int nc = min(hw, ncols - ch);
+    load_tile(Cs + row_lo * lc, lc, 1, C_s, nb, tr, row_lo, col0 + ch, row_hi - row_lo, nc, M_NONE);
+    load_tile(Cg + row_lo * lc, lc, 1, C_g, nb, tr, row_lo, col0 + ch, row_hi - row_lo, nc, M_NONE);
+    for (int bb = 0; bb < nbk; ++bb) {
+      const int b = blk1 - 1 - bb;
+      const int c0 = b * ib, kb = ib;
+      int vrows;
+      E *Cbs, *Cbg, *Tops = nullptr, *Topg = nullptr;
+      if (type == UNMQR) {
+        vrows = nb - c0;
+        load_tile(V, lv, 1, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+        Cbs = Cs + c0 * lc;
+        Cbg = Cg + c0 * lc;
+      } else {
+        vrows = (type == TSMQR) ? nb : c0 + kb;
+        load_tile(V, lv, 1, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER);
+        load_tile(Cts, lc, 1, Cp_s, nb, tr, c0, col0 + ch, kb, nc, M_NONE);
+        load_tile(Ctg, lc, 1, Cp_g, nb, tr, c0, col0 + ch, kb, nc, M_NONE);
+        Tops = Cts;
+        Topg = Ctg;
+        Cbs = Cs;
+        Cbg = Cg;
+      }
+      for (int o = threadIdx.x; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
+      __syncthreads();
+      apply_rm(V, lv, vrows, kb, Tb, true, Tops, Cbs, lc, nc, W, W2s, simt);
+      apply_rm(V, lv, vrows, kb, Tb, true, Topg, Cbg, lc, nc, W, W2g, simt);
+      bwd_partial(Cbs, Cbg, lc, vrows, kb, nc, W2s, W2g, slot + (size_t)(b - blk0) * pstride,
+                  slot + sbase + (size_t)(b - blk0) * kb * kb, ch > 0);
+      if (Tops) {
+        store_tile(Cts, lc, 1, Cp_s, nb, tr, c0, col0 + ch, kb, nc, M_NONE);
+        store_tile(Ctg, lc, 1, Cp_g, nb, tr, c0, col0 + ch, kb, nc, M_NONE);
+      }
+      __syncthreads();
+    }
+    store_tile(Cs + row_lo * lc, lc, 1, C_s, nb, tr, row_lo, col0 + ch, row_hi - row_lo, nc, M_NONE);
+    store_tile(Cg + row_lo * lc, lc, 1, C_g, nb, tr, row_lo, col0 + ch, row_hi - row_lo, nc, M_NONE);
+    __syncthreads();
+  }
+}
+
+// Adjoint of PF(b): sums the block's partial slots (every update strip of the panel task, and the
+// PU(b, s) sub-tasks), forms the tails' derivative from the columns right of the block (written to
+// red, column-major, ld nb) and tau_bar, then undoes the block's reflectors one at a time on its own
+// columns, pushing (v_bar, tau_bar) through house():
+//   x = beta (e_1 - tau v), alpha = beta (1 - tau), g = -(v_bar . v_tail) / (beta tau),
+//   alpha_bar = -tau_bar / beta - g,  beta_bar = tau_bar alpha / beta^2 + g,
+//   x_bar = [alpha_bar + beta_bar alpha / beta;  -v_bar / (beta tau) - beta_bar tau v_tail].
+// The post-step state of the block is its R triangle (GE: rows c0.. of X; TS / TT: the pivot's
+// triangle) with the eliminated entries exactly zero, and so is the gradient there.
+template <typename E>
+__device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s, E* X_s, E* A_g, E* X_g, int tr,
+                               const E* Tg, int nb, int ib, int b, const E* part, const int64_t* slot_off, int u0,
+                               int nu, int pu0, E* red) {
+  const BwdLayout L = layout_bwd_panel(nb, ib, (int)sizeof(E));
+  double* tau = reinterpret_cast<double*>(smb);
+  double* rsc = tau + 64;
+  double* wsA = tau + 96;
+  double* bA = tau + 160;
+  double* tbt = tau + 224;
+  E* sm = reinterpret_cast<E*>(smb + kHeaderDoubles * sizeof(double));
+  E *V = sm + L.V, *Ms = sm + L.Ms, *Mg = sm + L.Mg, *Rts = sm + L.Rts, *Rtg = sm + L.Rtg, *Sb = sm + L.Sb;
+  const int lp = L.lp, c0 = b * ib, kb = ib, nblk = nb / ib;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool ge = kind == PM_GE, tt = kind == PM_TT;
+  const int vrows = ge ? nb - c0 : (kind == PM_TS ? nb : c0 + kb);
+  E* redb = red + (size_t)b * nb * ib;
+  if (ge) load_tile(V, 1, lp, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+  else load_tile(V, 1, lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+  for (int k = threadIdx.x; k < kb; k += kThreads) tau[k] = (double)ldg(Tg + (size_t)c0 * ib + k + k * ib);
+  // partial sums, in slot order (deterministic); Ms holds P' meanwhile
+  const size_t pblk = (size_t)b * nb * ib, sblk = (size_t)nblk * nb * ib + (size_t)b * kb * kb;
+  const int pu_first = pu0 + b * nblk - b * (b + 1) / 2;
+  for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
+    const int k = o % kb, r = o / kb;
+    double s = 0.0;
+    for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + pblk + (size_t)r * kb + k);
+    for (int sb = b + 1; sb < nblk; ++sb) s += (double)ldg(part + slot_off[pu_first + sb - b - 1] + (size_t)r * kb + k);
+    Ms[r + k * lp] = (E)s;
+  }
+  for (int o = threadIdx.x; o < kb * kb; o += kThreads) {
+    double s = 0.0;
+    for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + sblk + o);
+    for (int sb = b + 1; sb < nblk; ++sb) s += (double)ldg(part + slot_off[pu_first + sb - b - 1] + (size_t)nb * kb + o);
+    Sb[o] = (E)s;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
+    const int r = o % vrows, k = o / vrows;
+    double s = -(double)Ms[r + k * lp] - (double)V[r + k * lp] * (double)Sb[k * kb + k];
+    for (int l = 0; l < k; ++l) s += (double)V[r + l * lp] * ((double)Sb[k * kb + l] - (double)Sb[l * kb + k]);
+    stg(redb + (size_t)k * nb + r, (E)s);
+  }
+  for (int k = threadIdx.x; k < kb; k += kThreads)
+    tbt[k] = tau[k] != 0.0 ? -(double)Sb[k * kb + k] / (tau[k] * tau[k]) : 0.0;
+  __syncthreads();
+  if (ge) {
+    load_tile(Ms, 1, lp, X_s, nb, tr, c0, c0, vrows, kb, M_UPPER);
+    load_tile(Mg, 1, lp, X_g, nb, tr, c0, c0, vrows, kb, M_UPPER);
+  } else {
+    load_tile(Rts, 1, kb, A_s, nb, tr, c0, c0, kb, kb, M_UPPER);
+    load_tile(Rtg, 1, kb, A_g, nb, tr, c0, c0, kb, kb, M_UPPER);
+    for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
+      const int r = o % vrows, k = o / vrows;
+      Ms[r + k * lp] = E(0);
+      Mg[r + k * lp] = E(0);
+    }
+  }
+  __syncthreads();
+  const int lts = ge ? lp : kb;
+  for (int k = kb - 1; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    const int t0 = ge ? k + 1 : 0;
+    const int t1 = ge ? vrows : (tt ? min(vrows, c0 + k + 1) : vrows);
+    E* ts = ge ? Ms + k : Rts + k;      // top entries of column j at ts[j * lts]
+    E* tg = ge ? Mg + k : Rtg + k;
+    const double beta = (double)ts[k * lts];
+    const int r = t0 + threadIdx.x;
+    const bool row = r < t1;
+    const double vbtr = row ? (double)ldg(redb + (size_t)k * nb + r) : 0.0;
+    const double v = row ? (double)V[r + k * lp] : 0.0;
+    const double vv = block_sum(v * v, rsc);
+    for (int j = k + 1 + warp; j < kb; j += kWarps) {
+      double s1 = 0.0, s2 = 0.0;
+      for (int rr = t0 + lane; rr < t1; rr += 32) {
+        const double vr = (double)V[rr + k * lp];
+        s1 += vr * (double)Ms[rr + j * lp];
+        s2 += vr * (double)Mg[rr + j * lp];
+      }
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        wsA[j] = (double)ts[j * lts] + s1;
+        bA[j] = (double)tg[j * lts] + s2;
+      }
+    }
+    if (threadIdx.x == 0) bA[k] = (double)tg[k * lts];
+    __syncthreads();
+    const double om = 1.0 - t * (1.0 + vv);   // a_j = om (v^T M')_j, a_k = om beta (v^T v = 1 + |tail|^2)
+    double tb = tbt[k] - beta * om * bA[k];
+    for (int j = k + 1; j < kb; ++j) tb -= wsA[j] * om * bA[j];
+    double vbar = 0.0;
+    if (row) {
+      double sG = 0.0, sM = 0.0;
+      for (int j = k + 1; j < kb; ++j) {
+        const double g = (double)Mg[r + j * lp];
+        const double mpre = (double)Ms[r + j * lp] - t * v * wsA[j];
+        sG += g * wsA[j] * om;
+        sM += mpre * bA[j];
+        Ms[r + j * lp] = (E)mpre;
+        Mg[r + j * lp] = (E)(g - t * v * bA[j]);
+      }
+      const double mk = -beta * t * v;
+      sM += mk * bA[k];
+      vbar = vbtr - t * (sG + sM);
+      Ms[r + k * lp] = (E)mk;
+      Mg[r + k * lp] = (E)(-t * v * bA[k]);
+    }
+    if (threadIdx.x < kb - k) {
+      const int j = k + threadIdx.x;
+      if (j == k) {
+        ts[k * lts] = (E)(beta * (1.0 - t));
+        tg[k * lts] = (E)((double)tg[k * lts] - t * bA[k]);
+      } else {
+        ts[j * lts] = (E)((double)ts[j * lts] - t * wsA[j]);
+        tg[j * lts] = (E)((double)tg[j * lts] - t * bA[j]);
+      }
+    }
+    const double vbv = block_sum(vbar * v, rsc);
+    const double g = -vbv / (beta * t);
+    const double alpha = beta * (1.0 - t);
+    const double abar = -tb / beta - g;
+    const double bbar = tb * alpha / (beta * beta) + g;
+    if (row) Mg[r + k * lp] = (E)((double)Mg[r + k * lp] - vbar / (beta * t) - bbar * t * v);
+    if (threadIdx.x == 0) tg[k * lts] = (E)((double)tg[k * lts] + abar + bbar * alpha / beta);
+    __syncthreads();
+  }
+  if (ge) {
+    store_tile(Ms, 1, lp, X_s, nb, tr, c0, c0, vrows, kb, M_NONE);
+    store_tile(Mg, 1, lp, X_g, nb, tr, c0, c0, vrows, kb, M_NONE);
+  } else {
+    store_tile(Rts, 1, kb, A_s, nb, tr, c0, c0, kb, kb, M_UPPER);
+    store_tile(Rtg, 1, kb, A_g, nb, tr, c0, c0, kb, kb, M_UPPER);
+    store_tile(Ms, 1, lp, X_s, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+    store_tile(Mg, 1, lp, X_g, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
+  }
+}
+
 template <typename E>
 __device__ void task_copy(const E* src, E* dst, int nb, bool diag) {
   for (int o = threadIdx.x; o < nb * nb; o += kThreads) {
@@ -641,25 +949,37 @@ __device__ void task_copy(const E* src, E* dst, int nb, bool diag) {
 // Tile reference (buffer << 28 | tile index) -> address, with the matrix's offsets and tile size.
 struct MatView {
   int nb, ib, w, npanels;
-  int64_t off[3], offT, nt[3];
+  int64_t off[6], offT, nt[6];
 };
 template <typename E>
 __device__ __forceinline__ E* tile_ptr(const ExecParams& prm, const MatView& mv, int32_t ref, bool& ok) {
   if (ref < 0) { ok = false; return nullptr; }
   const int buf = (int)((uint32_t)ref >> 28);
   const int64_t idx = ref & 0x0fffffff;
-  if (buf > 2) { ok = false; return nullptr; }
-  void* base = buf == 0 ? prm.buf[0] : (buf == 1 ? prm.buf[1] : prm.buf[2]);
-  const int64_t nt = buf == 0 ? mv.nt[0] : (buf == 1 ? mv.nt[1] : mv.nt[2]);
-  const int64_t off = buf == 0 ? mv.off[0] : (buf == 1 ? mv.off[1] : mv.off[2]);
+  if (buf > 5) { ok = false; return nullptr; }
+  // selects instead of indexing, so that the small arrays stay in registers
+  void* base = nullptr;
+  int64_t nt = 0, off = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+    if (buf == i) {
+      base = prm.buf[i];
+      nt = mv.nt[i];
+      off = mv.off[i];
+    }
   if (base == nullptr || idx >= nt) { ok = false; return nullptr; }
   return static_cast<E*>(base) + off + (size_t)idx * mv.nb * mv.nb;
+}
+// The adjoint's gradient tile at the same position as a state tile (buffer 2 / 3 -> 4 / 5).
+__device__ __forceinline__ int32_t grad_ref(int32_t ref) {
+  const int buf = (int)((uint32_t)ref >> 28);
+  return (ref < 0 || buf < 2 || buf > 3) ? -1 : ref + (2 << 28);
 }
 
 // Persistent dataflow executor: CTAs take sub-tasks from a queue in topological priority order,
 // wait (bounded) until the sub-tasks they depend on are done, run them and publish completion.
 // Taking tasks in queue order makes the scheme deadlock-free whatever the number of resident CTAs.
-template <typename E>
+template <typename E, bool kBwd>
 __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm) {
   extern __shared__ __align__(16) unsigned char smb[];
   __shared__ int s_idx;
@@ -718,14 +1038,15 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       const int mat = (t.flags >> 8) & 0xffffff;
       if (mat >= prm.nmats) {
         ok = false;
-        mv = MatView{prm.nb, prm.ib, prm.w, 0, {0, 0, 0}, 0, {0, 0, 0}};
+        mv = MatView{prm.nb, prm.ib, prm.w, 0, {0, 0, 0, 0, 0, 0}, 0, {0, 0, 0, 0, 0, 0}};
       } else {
         const MatInfo mi = prm.mats[mat];
-        mv = MatView{mi.nb, mi.ib, mi.w, mi.npanels, {mi.off[0], mi.off[1], 0}, mi.offT,
-                     {mi.ntiles[0], mi.ntiles[1], 0}};
+        mv = MatView{mi.nb, mi.ib, mi.w, mi.npanels, {mi.off[0], mi.off[1], 0, 0, 0, 0}, mi.offT,
+                     {mi.ntiles[0], mi.ntiles[1], 0, 0, 0, 0}};
       }
     } else {
-      mv = MatView{prm.nb, prm.ib, prm.w, prm.npanels, {0, 0, 0}, 0, {prm.ntiles[0], prm.ntiles[1], prm.ntiles[2]}};
+      mv = MatView{prm.nb, prm.ib, prm.w, prm.npanels, {0, 0, 0, 0, 0, 0}, 0,
+                   {prm.ntiles[0], prm.ntiles[1], prm.ntiles[2], prm.ntiles[3], prm.ntiles[4], prm.ntiles[5]}};
     }
     const int nb = mv.nb, ib = mv.ib, wst = mv.w;
     const int nblk = nb / ib;
@@ -733,6 +1054,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     E* Tg = (ok && t.tslot >= 0 && t.tslot < mv.npanels)
                 ? static_cast<E*>(prm.T) + mv.offT + (size_t)t.tslot * ib * nb
                 : nullptr;
+    if constexpr (!kBwd) {
     switch (type) {
       case PF: {
         E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
@@ -771,6 +1093,74 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       default:
         ok = false;
     }
+    } else {
+    switch (type) {
+      case BPF: {
+        const BwdParams& bw = prm.bwd;
+        E* As = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
+        E* Ag = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, grad_ref(t.a), ok);
+        E* Xs = tile_ptr<E>(prm, mv, t.c, ok);
+        E* Xg = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
+        if (ok && Tg && blk < nblk && kind <= PM_TT && bw.part && bw.red) {
+          const int32_t* pi = bw.pinfo + 4 * t.tslot;
+          const int u0 = pi[0], nu = pi[1], pu0 = pi[2];
+          if (u0 < 0 || nu < 0 || u0 + nu > bw.nslots || pu0 < 0 || pu0 + nblk * (nblk - 1) / 2 > bw.nslots) {
+            ok = false;
+          } else {
+            task_bwd_panel(smb, kind, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, blk, static_cast<const E*>(bw.part),
+                           bw.slot_off, u0, nu, pu0, static_cast<E*>(bw.red) + (size_t)t.tslot * nb * nb);
+          }
+        } else {
+          ok = false;
+        }
+        break;
+      }
+      case BPU: {
+        const BwdParams& bw = prm.bwd;
+        E* As = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
+        E* Ag = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, grad_ref(t.a), ok);
+        E* Xs = tile_ptr<E>(prm, mv, t.c, ok);
+        E* Xg = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
+        const int utype = kind == PM_GE ? UNMQR : (kind == PM_TS ? TSMQR : TTMQR);
+        if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT && bw.part && t.flags >= 0 &&
+            t.flags < bw.nslots)
+          task_bwd_update(smb, utype, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, bw.hw, blk, blk + 1, strip * ib, ib,
+                          static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
+        else
+          ok = false;
+        break;
+      }
+      case BUPD: {
+        const BwdParams& bw = prm.bwd;
+        const int utype = kind == 0 ? UNMQR : (kind == 1 ? TSMQR : TTMQR);
+        E* Cps = (utype == UNMQR) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
+        E* Cpg = (utype == UNMQR) ? nullptr : tile_ptr<E>(prm, mv, grad_ref(t.a), ok);
+        E* Cs = tile_ptr<E>(prm, mv, t.c, ok);
+        E* Cg = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
+        const int col0 = strip * wst;
+        if (ok && Tg && col0 < nb && kind <= 2 && bw.part && t.flags >= 0 && t.flags < bw.nslots)
+          task_bwd_update(smb, utype, X, Cps, Cs, Cpg, Cg, tr, Tg, nb, ib, bw.hw, 0, nblk, col0, min(wst, nb - col0),
+                          static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
+        else
+          ok = false;
+        break;
+      }
+      case BCOPY: {   // gradient of the copied part of R tile c back onto pre-QR tile x
+        E* Ga = tile_ptr<E>(prm, mv, grad_ref(t.x), ok);
+        E* Gr = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
+        if (ok) {
+          const bool diag = t.flags & 1;
+          for (int o = threadIdx.x; o < nb * nb; o += kThreads) {
+            const int r = o % nb, c = o / nb;
+            if (!diag || r <= c) stg(Ga + o, ldg(Ga + o) + ldg(Gr + o));
+          }
+        }
+        break;
+      }
+      default:
+        ok = false;
+    }
+    }
     if (!ok && threadIdx.x == 0 && atomicCAS(prm.err, 0, DERR_BADTASK) == 0) {
       prm.err[1] = idx;
       prm.err[2] = -1;
@@ -789,6 +1179,31 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         rec[3] = t.op;
       }
     }
+  }
+}
+
+template <typename E>
+__global__ void r_part_kernel(const E* __restrict__ src, E* __restrict__ dst, int64_t rows_t, int64_t cols_t, int nb) {
+  const int64_t tile = blockIdx.x;
+  const int64_t a = tile % rows_t, b = tile / rows_t;
+  const E* s = src + (size_t)tile * nb * nb;
+  E* d = dst + (size_t)tile * nb * nb;
+  for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
+    const int r = o % nb, c = o / nb;
+    const bool keep = a < cols_t && (a < b || (a == b && r <= c));
+    d[o] = keep ? s[o] : E(0);
+  }
+}
+
+// Band into a zeroed tile buffer: tile (i / nb, j / nb) entry (i % nb, j % nb) = ab(nb + i - j, j).
+template <typename E>
+__global__ void scatter_band_kernel(const E* __restrict__ ab, int64_t ldab, int nb, int64_t n, E* __restrict__ tiles,
+                                    int64_t rows_t) {
+  const int64_t j = blockIdx.x;
+  for (int d = threadIdx.x; d <= nb; d += blockDim.x) {
+    const int64_t i = j + d - nb;
+    if (i < 0) continue;
+    tiles[(size_t)((j / nb) * rows_t + i / nb) * nb * nb + (i % nb) + (j % nb) * nb] = ab[d + j * ldab];
   }
 }
 
@@ -907,6 +1322,21 @@ size_t exec_smem_bytes(int nb, int ib, int w, int esize) {
   return kHeaderDoubles * sizeof(double) + (size_t)esize * (size_t)(a.total > b.total ? a.total : b.total);
 }
 
+size_t bwd_smem_bytes(int nb, int ib, int hw, int esize) {
+  const BwdLayout a = layout_bwd_update(nb, ib, hw, esize), b = layout_bwd_panel(nb, ib, esize);
+  return kHeaderDoubles * sizeof(double) + (size_t)esize * (size_t)(a.total > b.total ? a.total : b.total);
+}
+
+int choose_bwd_chunk(int nb, int ib, int w, size_t smem_limit, int esize) {
+  if (ib > 64 || nb > kThreads) return 0;
+  if (kHeaderDoubles * sizeof(double) + (size_t)esize * layout_bwd_panel(nb, ib, esize).total > smem_limit) return 0;
+  for (int hw = w; hw >= 1; hw /= 2) {
+    if (bwd_smem_bytes(nb, ib, hw, esize) <= smem_limit) return hw;
+    if (hw <= 8) break;
+  }
+  return 0;
+}
+
 int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit, int esize) {
   if (ib > 64) return 0;
   for (int want = preferred; want >= 1; want /= 2) {
@@ -918,22 +1348,34 @@ int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit, int esi
   return 0;
 }
 
-cudaError_t exec_set_smem(size_t smem, int esize) {
-  if (esize == 4) return cudaFuncSetAttribute(exec_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(exec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+namespace {
+template <typename E>
+const void* exec_fn(bool bwd) {
+  return bwd ? reinterpret_cast<const void*>(exec_kernel<E, true>) : reinterpret_cast<const void*>(exec_kernel<E, false>);
+}
+}  // namespace
+
+cudaError_t exec_set_smem(size_t smem, int esize, bool bwd) {
+  return cudaFuncSetAttribute(esize == 4 ? exec_fn<float>(bwd) : exec_fn<double>(bwd),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int exec_max_ctas_per_sm(size_t smem, int esize) {
+int exec_max_ctas_per_sm(size_t smem, int esize, bool bwd) {
   int n = 0;
-  cudaError_t e = esize == 4
-                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, exec_kernel<float>, kThreads, smem)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, exec_kernel<double>, kThreads, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &n, esize == 4 ? exec_fn<float>(bwd) : exec_fn<double>(bwd), kThreads, smem);
   return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st) {
-  if (prm.esize == 4) exec_kernel<float><<<grid, kThreads, smem, st>>>(prm);
-  else exec_kernel<double><<<grid, kThreads, smem, st>>>(prm);
+  const bool bwd = prm.bwd.part != nullptr;
+  if (prm.esize == 4) {
+    if (bwd) exec_kernel<float, true><<<grid, kThreads, smem, st>>>(prm);
+    else exec_kernel<float, false><<<grid, kThreads, smem, st>>>(prm);
+  } else {
+    if (bwd) exec_kernel<double, true><<<grid, kThreads, smem, st>>>(prm);
+    else exec_kernel<double, false><<<grid, kThreads, smem, st>>>(prm);
+  }
   return cudaGetLastError();
 }
 
@@ -970,6 +1412,32 @@ cudaError_t launch_unpack(const float* tiles, int64_t rows_t, int nb, int64_t m,
 cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
                            cudaStream_t st) {
   return extract_t(tiles, rows_t, nb, n, ab, ldab, st);
+}
+template <typename E>
+cudaError_t r_part_t(const E* src, E* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st) {
+  if (rows_t * cols_t == 0) return cudaSuccess;
+  r_part_kernel<E><<<(unsigned)(rows_t * cols_t), 256, 0, st>>>(src, dst, rows_t, cols_t, nb);
+  return cudaGetLastError();
+}
+cudaError_t launch_r_part(const double* src, double* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st) {
+  return r_part_t(src, dst, rows_t, cols_t, nb, st);
+}
+cudaError_t launch_r_part(const float* src, float* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st) {
+  return r_part_t(src, dst, rows_t, cols_t, nb, st);
+}
+template <typename E>
+cudaError_t scatter_t(const E* ab, int64_t ldab, int nb, int64_t n, E* tiles, int64_t rows_t, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  scatter_band_kernel<E><<<(unsigned)n, 256, 0, st>>>(ab, ldab, nb, n, tiles, rows_t);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter_band(const double* ab, int64_t ldab, int nb, int64_t n, double* tiles, int64_t rows_t,
+                                cudaStream_t st) {
+  return scatter_t(ab, ldab, nb, n, tiles, rows_t, st);
+}
+cudaError_t launch_scatter_band(const float* ab, int64_t ldab, int nb, int64_t n, float* tiles, int64_t rows_t,
+                                cudaStream_t st) {
+  return scatter_t(ab, ldab, nb, n, tiles, rows_t, st);
 }
 cudaError_t launch_extract(const float* tiles, int64_t rows_t, int nb, int64_t n, float* ab, int64_t ldab,
                            cudaStream_t st) {

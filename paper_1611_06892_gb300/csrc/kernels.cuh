@@ -31,6 +31,16 @@ struct PackDesc {
   int32_t nb, pad;
 };
 
+// Extra arguments of the adjoint program (reverse sweep).
+struct BwdParams {
+  void* part;               // partial slots (element type by esize)
+  const int64_t* slot_off;  // element offset of each slot
+  int32_t nslots;
+  const int32_t* pinfo;     // per panel task: first update slot, number of update slots, first PU slot, 0
+  void* red;                // per panel task nb x nb: summed derivative of its reflector tails
+  int hw;                   // column chunk of the update adjoints
+};
+
 struct ExecParams {
   const DevTask* tasks;
   const int32_t* deps;
@@ -39,8 +49,9 @@ struct ExecParams {
   int* done;
   int* head;
   int* err;
-  void* buf[3];         // tile buffers (element type by esize): A tiles, R copy (R-BiDiag), apply target
-  int64_t ntiles[3];
+  void* buf[6];         // tile buffers (element type by esize): A tiles, R copy (R-BiDiag), apply target;
+                        // the adjoint uses 2 / 3 as the state of A / R and 4 / 5 as their gradients
+  int64_t ntiles[6];
   void* T;
   int32_t npanels;
   int nb, ib, w;        // tile size, inner blocking, strip width
@@ -50,6 +61,7 @@ struct ExecParams {
   const MatInfo* mats;  // batched program: per-matrix parameters (null for one matrix)
   int nmats;
   int f32_simt;         // FP32 tiles only: 1 = updates by FP32 FFMA instead of three TF32 tensor-core products
+  BwdParams bwd;        // adjoint program only
 };
 
 // Shared memory (bytes) the executor needs for (nb, ib, w) and element size esize (8 or 4).
@@ -58,9 +70,15 @@ size_t exec_smem_bytes(int nb, int ib, int w, int esize);
 // as the shared-memory limit allows; 0 if even w = ib does not fit.
 int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit, int esize);
 
+// Shared memory of the adjoint program and the column chunk of its update sub-tasks (0 if the panel
+// adjoint does not fit).
+size_t bwd_smem_bytes(int nb, int ib, int hw, int esize);
+int choose_bwd_chunk(int nb, int ib, int w, size_t smem_limit, int esize);
+
+// Executor launch: the adjoint instantiation when prm.bwd.part is set (bwd below must match).
 cudaError_t launch_exec(const ExecParams& prm, int grid, size_t smem, cudaStream_t st);
-cudaError_t exec_set_smem(size_t smem, int esize);
-int exec_max_ctas_per_sm(size_t smem, int esize);
+cudaError_t exec_set_smem(size_t smem, int esize, bool bwd = false);
+int exec_max_ctas_per_sm(size_t smem, int esize, bool bwd = false);
 
 // Column-major (ld) matrix <-> zero-padded tile buffer (grid of rows_t x cols_t tiles of nb x nb).
 cudaError_t launch_pack(const double* A, int64_t lda, int64_t m, int64_t n, int nb, double* tiles, int64_t rows_t,
@@ -74,6 +92,15 @@ cudaError_t launch_unpack(const float* tiles, int64_t rows_t, int nb, int64_t m,
 // Batched pack / extract over `count` matrices described on the device (total = tiles / columns).
 cudaError_t launch_pack_batched(const PackDesc* d, int count, int64_t total_tiles, int esize, cudaStream_t st);
 cudaError_t launch_extract_batched(const PackDesc* d, int count, int64_t total_cols, int esize, cudaStream_t st);
+// R-BiDiag adjoint start: dst = the R factor of the pre-QR held in src (tiles (a, b) with a <= b < q:
+// upper triangle of diagonal tiles, whole tiles above), zero elsewhere; grid rows_t x cols_t.
+cudaError_t launch_r_part(const double* src, double* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st);
+cudaError_t launch_r_part(const float* src, float* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st);
+// Band ab ((nb+1) x n, ld ldab) into a zeroed tile buffer (grid rows rows_t): the inverse of extraction.
+cudaError_t launch_scatter_band(const double* ab, int64_t ldab, int nb, int64_t n, double* tiles, int64_t rows_t,
+                                cudaStream_t st);
+cudaError_t launch_scatter_band(const float* ab, int64_t ldab, int nb, int64_t n, float* tiles, int64_t rows_t,
+                                cudaStream_t st);
 // Band extraction: ab((nb+1) x n, ld ldab) from the tile buffer (grid rows rows_t).
 cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
                            cudaStream_t st);

@@ -659,6 +659,129 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Adjoint program.  The reverse sweep undoes the forward sub-tasks in an order compatible with the
+// reversed DAG: a sub-task's adjoint reads the state and gradient its forward counterpart wrote and
+// writes those its counterpart read, so every forward hazard edge, reversed, orders the adjoints.  The
+// derivatives of the reflectors of panel block b are sums over every column block the block was
+// applied to: each BUPD strip (all blocks of its panel task) and each BPU(b, s) writes its part into a
+// partial slot of its own, and BPF(b) -- which depends on all of them through the reversed edges
+// (update strip -> last sub-task of its panel; PU(b, s) -> PF(b)) -- sums the slots in a fixed order.
+// Slot layout: an update strip's slot holds, for every block beta, a nb x ib block (rows of the
+// reflector tails) then an ib x ib block per beta; a PU slot holds the two blocks of its one block.
+// ---------------------------------------------------------------------------------------------
+void build_backward(const Plan& pl, BwdPlan& bp) {
+  const int nb = pl.nb, ib = pl.ib, nblk = nb / ib;
+  const int32_t nsub = (int32_t)pl.dev.size();
+  auto state_ref = [&](int32_t ref) -> int32_t {   // forward buffer 0 / 1 -> state buffer 2 / 3
+    if (ref < 0) return -1;
+    const int buf = (int)((uint32_t)ref >> 28);
+    return tile_ref(buf + 2, ref & 0x0fffffff);
+  };
+  // slots: per panel task, its update strips first (in program order), then its PU sub-tasks
+  const int npu = nblk * (nblk - 1) / 2;
+  std::vector<int32_t> nupd(std::max(1, pl.npanels), 0);
+  for (const DevTask& f : pl.dev) {
+    const int type = f.op & 15;
+    if (type == UNMQR || type == TSMQR || type == TTMQR) {
+      if (f.tslot < 0 || f.tslot >= pl.npanels) throw std::logic_error("update without a panel");
+      ++nupd[f.tslot];
+    }
+  }
+  bp.pinfo.assign((size_t)4 * std::max(1, pl.npanels), 0);
+  bp.slot_off.clear();
+  int64_t off = 0;
+  const int64_t upd_size = (int64_t)nb * nb + (int64_t)nb * ib, pu_size = (int64_t)nb * ib + (int64_t)ib * ib;
+  for (int t = 0; t < pl.npanels; ++t) {
+    bp.pinfo[4 * t + 0] = (int32_t)bp.slot_off.size();
+    bp.pinfo[4 * t + 1] = nupd[t];
+    for (int u = 0; u < nupd[t]; ++u) {
+      bp.slot_off.push_back(off);
+      off += upd_size;
+    }
+    bp.pinfo[4 * t + 2] = (int32_t)bp.slot_off.size();
+    for (int u = 0; u < npu; ++u) {
+      bp.slot_off.push_back(off);
+      off += pu_size;
+    }
+  }
+  bp.slot_off.push_back(off);
+  if (bp.slot_off.size() >= (1u << 31)) throw std::invalid_argument("too many partial slots");
+  std::vector<int32_t> next_upd(std::max(1, pl.npanels), 0);
+  auto pu_index = [&](int b, int s) { return b * nblk - b * (b + 1) / 2 + (s - b - 1); };
+
+  std::vector<DevTask> sub(nsub);
+  std::vector<int64_t> wt(nsub, 1);
+  const int64_t ib2 = (int64_t)ib * ib, w = pl.strip_w;
+  for (int32_t y = 0; y < nsub; ++y) {
+    const DevTask& f = pl.dev[y];
+    const int type = f.op & 15, tr = (f.op >> 4) & 1, strip = (f.op >> 8) & 0xff, blk = (f.op >> 16) & 0xff;
+    const int kind = (f.op >> 24) & 3;
+    DevTask d{};
+    d.x = f.x;
+    d.tslot = f.tslot;
+    d.flags = 0;
+    if (type == PF || type == PU) {
+      d.a = state_ref(f.a);
+      d.c = state_ref(f.x);
+      const int64_t rows = kind == PK_GE ? nb - (int64_t)blk * ib : (kind == PK_TS ? nb : (int64_t)(blk + 1) * ib);
+      if (type == PF) {
+        d.op = make_op(BPF, tr, false, 0, blk, kind);
+        wt[y] = 10 * ib2 * rows;
+      } else {
+        d.op = make_op(BPU, tr, false, strip, blk, kind);
+        d.flags = bp.pinfo[4 * f.tslot + 2] + pu_index(blk, strip);
+        wt[y] = 14 * ib2 * rows;
+      }
+    } else if (type == UNMQR || type == TSMQR || type == TTMQR) {
+      d.a = state_ref(f.a);
+      d.c = state_ref(f.c);
+      const int uk = type == UNMQR ? 0 : (type == TSMQR ? 1 : 2);
+      d.op = make_op(BUPD, tr, false, strip, 0, uk);
+      d.flags = bp.pinfo[4 * f.tslot + 0] + next_upd[f.tslot]++;
+      wt[y] = 3 * (type == TSMQR ? 4 : 2) * (int64_t)nb * nb * w;
+    } else {
+      d.x = state_ref(f.x);
+      d.a = -1;
+      d.c = state_ref(f.c);
+      d.flags = f.flags & 1;
+      d.op = make_op(BCOPY, false, false, 0, 0, 0);
+      wt[y] = (int64_t)nb * nb;
+    }
+    sub[y] = d;
+  }
+  // reversed DAG: forward y depends on d  ->  adjoint d depends on adjoint y
+  std::vector<std::vector<int32_t>> rdeps(nsub);
+  for (int32_t y = 0; y < nsub; ++y)
+    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) rdeps[pl.deps[k]].push_back(y);
+  // bottom levels of the reversed DAG (its successors of y are y's forward dependencies)
+  std::vector<int64_t> bottom(nsub, 0);
+  for (int32_t y = 0; y < nsub; ++y) {
+    int64_t mx = 0;
+    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) mx = std::max(mx, bottom[pl.deps[k]]);
+    bottom[y] = wt[y] + mx;
+  }
+  std::vector<int32_t> order(nsub);
+  for (int32_t y = 0; y < nsub; ++y) order[y] = nsub - 1 - y;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return bottom[a] > bottom[b]; });
+  std::vector<int32_t> pos(nsub);
+  for (int32_t y = 0; y < nsub; ++y) pos[order[y]] = y;
+  bp.dev.resize(nsub);
+  bp.fwd = order;
+  bp.deps.clear();
+  for (int32_t z = 0; z < nsub; ++z) {
+    const int32_t y = order[z];
+    DevTask e = sub[y];
+    e.dep_begin = (int32_t)bp.deps.size();
+    for (int32_t dd : rdeps[y]) {
+      if (pos[dd] >= z) throw std::logic_error("adjoint order is not topological");
+      bp.deps.push_back(pos[dd]);
+    }
+    e.dep_end = (int32_t)bp.deps.size();
+    bp.dev[z] = e;
+  }
+}
+
 void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>* dev, std::vector<int32_t>* deps) {
   const size_t np = plans.size();
   if (np >= (1u << 23)) throw std::invalid_argument("too many matrices in a batch");

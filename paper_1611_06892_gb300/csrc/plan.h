@@ -10,6 +10,10 @@ enum TaskType : int { GEQRT = 0, UNMQR = 1, TSQRT = 2, TSMQR = 3, TTQRT = 4, TTM
 // Device-only sub-task types: factor one inner block of a panel (PF), apply it to a later column block
 // of the panel (PU).  Their op word carries the panel kind (0 GE, 1 TS, 2 TT) in bits 24-25.
 enum SubType : int { PF = 7, PU = 8 };
+// Sub-tasks of the adjoint program (reverse sweep): BPF / BPU undo PF / PU, BUPD undoes an update strip
+// (kind bits 24-25: 0 UNMQR, 1 TSMQR, 2 TTMQR), BCOPY undoes a COPY (adds the gradient of the copied
+// part of an R tile to the pre-QR tile it was copied from).
+enum BwdType : int { BPF = 9, BPU = 10, BUPD = 11, BCOPY = 12 };
 enum Phase : int { PH_QR = 0, PH_LQ = 1, PH_PQR = 2 };
 enum Tree : int { FLATTS = 0, FLATTT = 1, GREEDY = 2, AUTO = 3 };
 enum Variant : int { V_BIDIAG = 0, V_RBIDIAG = 1 };
@@ -53,6 +57,23 @@ struct Plan {
   std::vector<int32_t> deps;       // indices into dev (queue positions)
   std::vector<int64_t> prio;       // bottom level of each queued sub-task (flop-proportional weights)
 };
+
+// Adjoint program of a plan (the reverse sweep).  Sub-task y of the forward program becomes its
+// adjoint; every dependency is reversed, priorities are the bottom levels of the reversed DAG.  Tile
+// references: x = reflector tile of the forward result (buffers 0 / 1 as in the forward program),
+// a / c = working-state tiles: buffer 2 mirrors the forward's tile buffer 0 (p x q grid), buffer 3 its
+// R copy (q x q, R-BiDiag); the gradients are buffers 4 and 5 with the same indices.  BCOPY: x = the
+// pre-QR state tile, c = the R state tile, flags bit 0 = diagonal tile.  Update sub-tasks write their
+// contributions to the reflectors' derivatives into partial slots (flags = slot index); the factor
+// sub-task of a block sums them.
+struct BwdPlan {
+  std::vector<DevTask> dev;
+  std::vector<int32_t> deps;
+  std::vector<int64_t> slot_off;   // element offset of each partial slot; last entry = total elements
+  std::vector<int32_t> pinfo;      // per panel task (T slot): first update slot, number, first PU slot, 0
+  std::vector<int32_t> fwd;        // forward queue position of each adjoint sub-task
+};
+void build_backward(const Plan& pl, BwdPlan& bp);
 
 // Trees and task lists (independent of any device state).
 std::vector<Elim> make_eliminations(int p, int q, int tree, int variant, int64_t resources);

@@ -1,0 +1,162 @@
+"""Host-side checks of the adjoint program (the reverse sweep of bidiag_band_backward), no GPU.
+
+* Every forward sub-task is undone exactly once, by the adjoint sub-task of the matching kind.
+* Race and order check: every element of the working state / gradient that two adjoint sub-tasks
+  touch (one writing it) is ordered by the dependency DAG, and in the REVERSE of the forward order of
+  their counterparts; every partial slot is written by one sub-task that precedes the factor sub-task
+  reading it.  Footprints are modelled from what the CUDA sub-tasks load and store.
+* The slot table covers each panel task's update strips and panel-block updates exactly once.
+"""
+import numpy as np
+import pytest
+
+import paper_1611_06892_gb300 as G
+
+UNMQR, TSMQR, TTMQR, COPY, PF, PU = 1, 3, 5, 6, 7, 8
+BPF, BPU, BUPD, BCOPY = 9, 10, 11, 12
+GE, TS, TT = 0, 1, 2
+
+
+def fields(t):
+    op = int(t[0])
+    return dict(typ=op & 15, tr=(op >> 4) & 1, strip=(op >> 8) & 0xFF, blk=(op >> 16) & 0xFF, kind=(op >> 24) & 3,
+                x=int(t[1]), a=int(t[2]), c=int(t[3]), tslot=int(t[4]), flags=int(t[7]))
+
+
+def state_footprint(f, nb, ib, w):
+    """Elements (tile, row, col) of the working state / gradient an adjoint sub-task reads or writes."""
+    tr = f["tr"]
+    out = set()
+
+    def region(ref, r0, c0, rows, cols, upper=False, orient=True):
+        buf = ref >> 28
+        assert buf in (2, 3), "adjoint sub-tasks address the state buffers"
+        idx = ref & 0x0FFFFFFF
+        for r in range(rows):
+            for cc in range(cols):
+                R, C = r0 + r, c0 + cc
+                if upper and R > C:
+                    continue
+                out.add((buf, idx) + ((C, R) if (tr and orient) else (R, C)))
+
+    def update(utype, Cp, C, blk0, blk1, col0, ncols):
+        row_lo = blk0 * ib if utype == UNMQR else 0
+        row_hi = blk1 * ib if utype == TTMQR else nb
+        region(C, row_lo, col0, row_hi - row_lo, ncols)
+        if utype != UNMQR:
+            for b in range(blk0, blk1):
+                region(Cp, b * ib, col0, ib, ncols)
+
+    nblk = nb // ib
+    typ, blk, kind = f["typ"], f["blk"], f["kind"]
+    if typ == BPF:
+        c0 = blk * ib
+        if kind == GE:
+            region(f["c"], c0, c0, nb - c0, ib)
+        else:
+            region(f["a"], c0, c0, ib, ib, upper=True)
+            region(f["c"], 0, c0, nb if kind == TS else c0 + ib, ib, upper=(kind == TT))
+    elif typ == BPU:
+        utype = {GE: UNMQR, TS: TSMQR, TT: TTMQR}[kind]
+        update(utype, f["a"], f["c"], blk, blk + 1, f["strip"] * ib, ib)
+    elif typ == BUPD:
+        utype = (UNMQR, TSMQR, TTMQR)[kind]
+        col0 = f["strip"] * w
+        update(utype, f["a"], f["c"], 0, nblk, col0, min(w, nb - col0))
+    elif typ == BCOPY:
+        diag = f["flags"] & 1
+        region(f["x"], 0, 0, nb, nb, upper=bool(diag), orient=False)
+        region(f["c"], 0, 0, nb, nb, upper=bool(diag), orient=False)
+    return out
+
+
+def check_backward(m, n, nb, ib, tree, variant, strip_w):
+    fprog, fdeps, w = G.bidiag_plan_program(m, n, nb, ib, tree, variant, resources=2, strip_w=strip_w)
+    prog, fwd, deps, slot_off, pinfo = G.bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=2,
+                                                              strip_w=strip_w)
+    nsub = len(prog)
+    nblk = nb // ib
+    assert nsub == len(fprog) and sorted(fwd.tolist()) == list(range(nsub))
+    # kinds match the forward sub-tasks they undo
+    kind_map = {PF: BPF, PU: BPU, UNMQR: BUPD, TSMQR: BUPD, TTMQR: BUPD, COPY: BCOPY}
+    for y in range(nsub):
+        f, g = fields(prog[y]), fields(fprog[fwd[y]])
+        assert f["typ"] == kind_map[g["typ"]]
+        if f["typ"] in (BPF, BPU):
+            assert (f["blk"], f["kind"], f["tslot"], f["x"]) == (g["blk"], g["kind"], g["tslot"], g["x"])
+            assert f["c"] == g["x"] + (2 << 28) and f["a"] == (g["a"] + (2 << 28) if g["a"] >= 0 else -1)
+        if f["typ"] == BUPD:
+            assert f["kind"] == {UNMQR: 0, TSMQR: 1, TTMQR: 2}[g["typ"]] and f["strip"] == g["strip"]
+    # ancestors in the adjoint DAG
+    anc = [0] * nsub
+    for y in range(nsub):
+        acc = 0
+        for d in deps[prog[y, 5]:prog[y, 6]]:
+            d = int(d)
+            assert d < y
+            acc |= anc[d] | (1 << d)
+        anc[y] = acc
+    # state / gradient: conflicts ordered in reverse forward order
+    touch = {}
+    for y in range(nsub):
+        for e in state_footprint(fields(prog[y]), nb, ib, w):
+            touch.setdefault(e, []).append(y)
+    for e, ys in touch.items():
+        ys = sorted(ys, key=lambda y: -fwd[y])        # the order the reverse sweep must follow
+        for i in range(1, len(ys)):
+            assert (anc[ys[i]] >> ys[i - 1]) & 1, f"state element {e}: adjoint {ys[i - 1]} must precede {ys[i]}"
+    # slots: one writer each, before the factor sub-task of the block that reads it
+    writer = {}
+    for y in range(nsub):
+        f = fields(prog[y])
+        if f["typ"] in (BPU, BUPD):
+            assert f["flags"] not in writer, "a partial slot with two writers"
+            writer[f["flags"]] = y
+            t = pinfo[f["tslot"]]
+            if f["typ"] == BUPD:
+                assert t[0] <= f["flags"] < t[0] + t[1]
+            else:
+                b, s = f["blk"], f["strip"]
+                assert f["flags"] == t[2] + b * nblk - b * (b + 1) // 2 + (s - b - 1)
+    for y in range(nsub):
+        f = fields(prog[y])
+        if f["typ"] != BPF:
+            continue
+        t = pinfo[f["tslot"]]
+        b = f["blk"]
+        reads = list(range(t[0], t[0] + t[1]))
+        reads += [t[2] + b * nblk - b * (b + 1) // 2 + (s - b - 1) for s in range(b + 1, nblk)]
+        for sl in reads:
+            assert sl in writer and (anc[y] >> writer[sl]) & 1, f"slot {sl} not written before its reader {y}"
+    # slot offsets: increasing, sizes nb^2 + nb ib (update strips) and nb ib + ib^2 (panel-block updates)
+    sizes = np.diff(slot_off)
+    assert set(sizes.tolist()) <= {nb * nb + nb * ib, nb * ib + ib * ib}
+    assert len(writer) == len(slot_off) - 1
+    return nsub
+
+
+@pytest.mark.parametrize("variant", (0, 1), ids=("bidiag", "rbidiag"))
+@pytest.mark.parametrize("tree", (0, 1, 2, 3), ids=("flatts", "flattt", "greedy", "auto"))
+def test_adjoint_program_order(tree, variant):
+    # 3 x 3 ragged tiles, nb = 8, two inner blocks, strips of 4 columns
+    assert check_backward(22, 20, 8, 4, tree, variant, strip_w=4) > 0
+    # 5 x 2 tiles, inner block = tile
+    assert check_backward(20, 8, 4, 4, tree, variant, strip_w=32) > 0
+    # three inner blocks per tile, strips of two blocks
+    assert check_backward(30, 18, 6, 2, tree, variant, strip_w=4) > 0
+
+
+def test_checker_catches_a_reversed_edge(monkeypatch):
+    """Drop the dependencies of one factor adjoint: the checker must report it."""
+    real = G.bidiag_plan_backward
+
+    def broken(*args, **kw):
+        prog, fwd, deps, slot_off, pinfo = real(*args, **kw)
+        prog = prog.copy()
+        y = [i for i in range(len(prog)) if (prog[i, 0] & 15) == BPF and prog[i, 6] > prog[i, 5]][-1]
+        prog[y, 6] = prog[y, 5]
+        return prog, fwd, deps, slot_off, pinfo
+
+    monkeypatch.setattr(G, "bidiag_plan_backward", broken)
+    with pytest.raises(AssertionError):
+        check_backward(22, 20, 8, 4, 2, 0, strip_w=4)
