@@ -536,7 +536,7 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
     release();
     return cuda_fail(h, e, "adjoint set-up");
   }
-  const bool timed = h->timing != 0;
+  const bool timed = h->timing != 0 || h->tracing != 0;
   if (timed && !h->ev[0]) {
     e = cudaEventCreate(&h->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);

@@ -210,3 +210,28 @@ def test_backward_argument_errors(handle, torch_mod):
     assert lib.bidiag_band_backward(handle.h, res.r, p(W.data_ptr()), 9, p(out.data_ptr()), 39, None, 1) == -6
     assert lib.bidiag_band_backward_f32(handle.h, res.r, p(W.data_ptr()), 9, p(out.data_ptr()), 40, None, 1) == -2
     res.free()
+
+
+SPLIT_TOL = 1e-4
+
+
+@pytest.mark.parametrize("case", [(200, 136, 32, 16), (320, 96, 32, 32), (600, 400, 256, 32)],
+                         ids=lambda c: "x".join(map(str, c)))
+@pytest.mark.parametrize("variant", ("bidiag", "rbidiag"))
+def test_adjoint_split_fp32(handle, torch_mod, case, variant):
+    """FP32 storage (3xTF32 updates, FP64 reflector scalars): dL/dA against the FP64 oracle adjoint of
+    the same FP32-rounded matrix, within SPLIT_TOL of the largest entry."""
+    torch = torch_mod
+    m, n, nb, ib = case
+    A32 = inputs.gaussian(m, n, seed=m + n).astype(np.float32)
+    W32 = inputs.gaussian(nb + 1, n, seed=2 * n).astype(np.float32)
+    res_o = OB.bidiag_band(A32.astype(np.float64), nb, ib, T.GREEDY, G.VARIANTS[variant], resources=R_AUTO)
+    Ab_o, _ = AD.band_vjp(res_o, W32.astype(np.float64))
+    res_g = handle.band(dev(torch, A32), nb, ib, "greedy", variant)
+    Ab_g, Arec = res_g.backward(dev(torch, W32), reconstruct=True)
+    handle.sync()
+    err = np.abs(Ab_g.cpu().numpy().astype(np.float64) - Ab_o).max() / np.abs(Ab_o).max()
+    assert err <= SPLIT_TOL, err
+    rec = np.abs(Arec.cpu().numpy().astype(np.float64) - A32).max() / np.abs(A32).max()
+    assert rec <= 1e-5, rec
+    res_g.free()
