@@ -36,8 +36,15 @@ typedef struct bidiag_result* bidiag_result_t;
 enum { BIDIAG_FLATTS = 0, BIDIAG_FLATTT = 1, BIDIAG_GREEDY = 2, BIDIAG_AUTO = 3 };
 /* Variants: Sec. 3.4 (BiDiag) and Sec. 3.5 (R-BiDiag = QR(p,q) then BiDiag of the top square).
  * BIDIAG_AUTO_VARIANT picks the one with the shorter critical path (Sec. 4.3.3, the delta_s switch;
- * see bidiag_plan_choose_variant); the result records the variant used. */
-enum { BIDIAG_BIDIAG = 0, BIDIAG_RBIDIAG = 1, BIDIAG_AUTO_VARIANT = 2 };
+ * see bidiag_plan_choose_variant); the result records the variant used.
+ * Three-step (Sec. 4.5, partial BiDiag + pre-QR + BiDiag): BIDIAG_THREESTEP_SPLIT(s), 0 <= s < q, runs
+ * the first s BiDiag steps (QR(k), LQ(k), k < s) on A, then R-BiDiag on the trailing (p-s) x (q-s)
+ * tiles (pre-QR, copy of its R, BiDiag of that R); s = 0 is R-BiDiag (recorded as such), s = q-1 has
+ * BiDiag's critical path.  BIDIAG_THREESTEP picks the split with the shortest critical path by trying
+ * every s (the paper's brute force; see bidiag_plan_best_split).  Not available in the batched and
+ * allocation-free forms. */
+enum { BIDIAG_BIDIAG = 0, BIDIAG_RBIDIAG = 1, BIDIAG_AUTO_VARIANT = 2, BIDIAG_THREESTEP = 3 };
+#define BIDIAG_THREESTEP_SPLIT(s) (4 + (s))
 /* Status codes. */
 enum {
   BIDIAG_OK = 0,
@@ -280,6 +287,7 @@ int bidiag_destroy(bidiag_handle h);
  * Host-only planner queries (no device work; usable without a GPU).  They expose the planner's
  * elimination list, task list and task DAG so that they can be checked against the paper's critical
  * path formulas (Sec. 4) and an independent implementation.  `resources` is the Auto tree's R.
+ * `variant` is BIDIAG_BIDIAG, BIDIAG_RBIDIAG or BIDIAG_THREESTEP_SPLIT(s) with s < q.
  * --------------------------------------------------------------------------------------------- */
 
 /* Canonical elimination list: records of 5 int32 (phase, k, i, piv, kind[0 = TS, 1 = TT]).  When
@@ -300,6 +308,11 @@ int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resou
  * the pointers are not NULL.  Errors: -1 (p, q), -3 (tree), -5 (variant NULL). */
 int bidiag_plan_choose_variant(int64_t p, int64_t q, int tree, int64_t resources, int* variant,
                                int64_t* cp_bidiag, int64_t* cp_rbidiag);
+
+/* Host-only: the three-step split s with the shortest critical path for p x q tiles (Table 1 weights,
+ * unbounded resources; ties keep the smallest s) and, if cp is not NULL, that critical path.
+ * Errors: -1 sizes (need p >= q >= 1), -3 tree, -5 split NULL. */
+int bidiag_plan_best_split(int64_t p, int64_t q, int tree, int64_t resources, int* split, int64_t* cp);
 
 /* The device program the executor runs for a reduction (host-only, for validation): *count sub-tasks
  * of 8 int32 in queue order (op word: type | orientation << 4 | Q-instead-of-Q^T << 5 | strip << 8 |

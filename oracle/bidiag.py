@@ -61,7 +61,7 @@ def run_tasks(state, tasks):
             src = src[:dst.shape[0], :]    # a ragged last tile of R keeps only its n - (q-1) nb rows
             dst[...] = np.triu(src) if i == j else src
             continue
-        mat = state["R"] if (variant == T.RBIDIAG and phase != T.PQR) else state["A"]
+        mat = state["R"] if T.task_buffer(phase, k, variant) == 1 else state["A"]
         lq = phase == T.LQ
         if typ == T.GEQRT:
             X = mat.otile(lq, i, k)
@@ -104,7 +104,7 @@ def new_state(A, nb, ib, tree, variant, resources=None, gamma=2):
         raise ValueError("need 1 <= ib <= nb and nb % ib == 0")
     p, q = -(-m // nb), -(-n // nb)
     tasks = T.task_list(p, q, tree, variant, resources, gamma)
-    return {"A": Tiles(A, nb), "R": Tiles(np.zeros((n, n)), nb) if variant == T.RBIDIAG else None,
+    return {"A": Tiles(A, nb), "R": Tiles(np.zeros((n, n)), nb) if T.split_of(variant) is not None else None,
             "nb": nb, "ib": ib, "tree": tree, "variant": variant, "m": m, "n": n, "p": p, "q": q,
             "tasks": tasks, "refl": {}, "owner": {}}
 
@@ -132,10 +132,16 @@ def bidiag_band(A, nb, ib, tree, variant, resources=None, gamma=2):
     """Reduce A (m x n, m >= n) to band bidiagonal form.  Returns a result dict (see module doc)."""
     st = new_state(A, nb, ib, tree, variant, resources, gamma)
     run_tasks(st, list(enumerate(st["tasks"])))
-    final = st["R"].M if variant == T.RBIDIAG else st["A"].M
+    s = T.split_of(variant)
+    if s is None:
+        final = st["A"].M
+    else:
+        # rows of the first s tile rows come from the BiDiag steps on A, the rest from the R copy
+        final = st["R"].M.copy()
+        final[:s * nb, :] = st["A"].M[:s * nb, :]
     st["ab"] = band_of(final, nb)
     st["work"] = st["A"].M
-    st["work2"] = st["R"].M if variant == T.RBIDIAG else None
+    st["work2"] = st["R"].M if s is not None else None
     return st
 
 

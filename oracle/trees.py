@@ -51,8 +51,10 @@ import math
 # tree codes
 FLATTS, FLATTT, GREEDY, AUTO = 0, 1, 2, 3
 TREE_NAMES = {FLATTS: "flatts", FLATTT: "flattt", GREEDY: "greedy", AUTO: "auto"}
-# variant codes
+# variant codes; three-step with split s (Sec. 4.5: s BiDiag steps, then R-BiDiag on the trailing
+# (p - s) x (q - s) tiles) is THREESTEP + s
 BIDIAG, RBIDIAG = 0, 1
+THREESTEP = 4
 # phases
 QR, LQ, PQR = 0, 1, 2
 # task types
@@ -140,21 +142,44 @@ def greedy_multicolumn(p, q):
     return out
 
 
-def _steps(p, q, variant):
-    """List of (phase, k, panel_rows, ntrail) in sequence order (Sec. 3.4 / 3.5)."""
-    steps = []
+def split_of(variant):
+    """Number of BiDiag steps before the switch to R-BiDiag: 0 for R-BiDiag, s for THREESTEP + s,
+    None for BiDiag (no second phase)."""
     if variant == BIDIAG:
-        for k in range(q):
-            steps.append((QR, k, list(range(k, p)), q - k - 1))
-            if k < q - 1:
-                steps.append((LQ, k, list(range(k + 1, q)), p - k - 1))
-    elif variant == RBIDIAG:
-        for k in range(q - 1):
-            steps.append((LQ, k, list(range(k + 1, q)), q - k - 1))
-            steps.append((QR, k + 1, list(range(k + 1, q)), q - k - 2))
-    else:
-        raise ValueError(f"unknown variant {variant}")
-    return steps
+        return None
+    if variant == RBIDIAG:
+        return 0
+    if variant >= THREESTEP:
+        return variant - THREESTEP
+    raise ValueError(f"unknown variant {variant}")
+
+
+def task_buffer(phase, k, variant):
+    """Matrix a task works on: 0 = A (m x n), 1 = the R copy of the second phase.  The second phase is
+    the BiDiag of the trailing R: its LQ steps k >= s and QR steps k >= s + 1 (QR(s) is the pre-QR)."""
+    s = split_of(variant)
+    if s is None or phase == PQR:
+        return 0
+    return 1 if (phase == LQ and k >= s) or (phase == QR and k > s) else 0
+
+
+def _steps(p, q, variant):
+    """(first-phase steps, second-phase steps), each a list of (phase, k, panel_rows, ntrail) in
+    sequence order (Sec. 3.4 / 3.5; the three-step of Sec. 4.5 runs s BiDiag steps on A, the pre-QR of
+    the trailing tiles, then BiDiag on their R)."""
+    first, second = [], []
+    s = split_of(variant)
+    if s is not None and not 0 <= s < q:
+        raise ValueError("three-step split must be in [0, q)")
+    for k in range(q if s is None else s):
+        first.append((QR, k, list(range(k, p)), q - k - 1))
+        if k < q - 1:
+            first.append((LQ, k, list(range(k + 1, q)), p - k - 1))
+    if s is not None:
+        for k in range(s, q - 1):
+            second.append((LQ, k, list(range(k + 1, q)), q - k - 1))
+            second.append((QR, k + 1, list(range(k + 1, q)), q - k - 2))
+    return first, second
 
 
 def _elim_tasks(phase, k, elims, ntrail_cols, tasks, tri):
@@ -199,18 +224,26 @@ def _single_tile(phase, k, row, ntrail_cols, tasks, tri):
         tasks.append((UNMQR, phase, k, row, -1, j))
 
 
+def _preqr_eliminations(p, q, s, tree, resources, gamma):
+    """Eliminations [(k, i, piv, kind)] of the pre-QR of tiles s..p-1 x s..q-1, in program order."""
+    if tree == GREEDY:
+        return [(k + s, i + s, piv + s, TT) for (k, i, piv) in greedy_multicolumn(p - s, q - s)]
+    return [(k, i, piv, kind) for k in range(s, q)
+            for (i, piv, kind) in step_eliminations(range(k, p), q - k - 1, tree, resources, gamma)]
+
+
 def eliminations(p, q, tree, variant, resources=None, gamma=2):
     """Canonical elimination list [(phase, k, i, piv, kind)] in program order."""
     out = []
-    if variant == RBIDIAG:
-        if tree == GREEDY:
-            for (k, i, piv) in greedy_multicolumn(p, q):
-                out.append((PQR, k, i, piv, TT))
-        else:
-            for k in range(min(p, q)):
-                for (i, piv, kind) in step_eliminations(range(k, p), q - k - 1, tree, resources, gamma):
-                    out.append((PQR, k, i, piv, kind))
-    for (phase, k, rows, ntrail) in _steps(p, q, variant):
+    first, second = _steps(p, q, variant)
+    for (phase, k, rows, ntrail) in first:
+        for (i, piv, kind) in step_eliminations(rows, ntrail, tree, resources, gamma):
+            out.append((phase, k, i, piv, kind))
+    s = split_of(variant)
+    if s is not None:
+        for (k, i, piv, kind) in _preqr_eliminations(p, q, s, tree, resources, gamma):
+            out.append((PQR, k, i, piv, kind))
+    for (phase, k, rows, ntrail) in second:
         for (i, piv, kind) in step_eliminations(rows, ntrail, tree, resources, gamma):
             out.append((phase, k, i, piv, kind))
     return out
@@ -222,32 +255,39 @@ def task_list(p, q, tree, variant, resources=None, gamma=2):
         raise ValueError("need p >= q >= 1 tiles")
     tasks = []
     tri = set()
-    if variant == RBIDIAG:
+
+    def run_steps(steps):
+        for (phase, k, rows, ntrail) in steps:
+            el = step_eliminations(rows, ntrail, tree, resources, gamma)
+            if el:
+                _elim_tasks(phase, k, el, ntrail, tasks, tri)
+            else:
+                _single_tile(phase, k, rows[0], ntrail, tasks, tri)
+
+    first, second = _steps(p, q, variant)
+    run_steps(first)
+    s = split_of(variant)
+    if s is not None:
         if tree == GREEDY:
-            # time-stepped multi-column greedy: program order by (s, k)
-            by_col = {}
-            for (k, i, piv) in greedy_multicolumn(p, q):
-                _elim_tasks(PQR, k, [(i, piv, TT)], q - k - 1, tasks, tri)
-                by_col[k] = True
-            for k in range(min(p, q)):
+            # time-stepped multi-column greedy: program order by (time, column)
+            by_col = set()
+            for (k, i, piv, kind) in _preqr_eliminations(p, q, s, tree, resources, gamma):
+                _elim_tasks(PQR, k, [(i, piv, kind)], q - k - 1, tasks, tri)
+                by_col.add(k)
+            for k in range(s, q):
                 if k not in by_col:       # single-tile column (p == q, last column)
                     _single_tile(PQR, k, k, q - k - 1, tasks, tri)
         else:
-            for k in range(min(p, q)):
+            for k in range(s, q):
                 el = step_eliminations(range(k, p), q - k - 1, tree, resources, gamma)
                 if el:
                     _elim_tasks(PQR, k, el, q - k - 1, tasks, tri)
                 else:
                     _single_tile(PQR, k, k, q - k - 1, tasks, tri)
-        for a in range(q):
+        for a in range(s, q):
             for b in range(a, q):
                 tasks.append((COPY, PQR, -1, a, -1, b))
-    for (phase, k, rows, ntrail) in _steps(p, q, variant):
-        el = step_eliminations(rows, ntrail, tree, resources, gamma)
-        if el:
-            _elim_tasks(phase, k, el, ntrail, tasks, tri)
-        else:
-            _single_tile(phase, k, rows[0], ntrail, tasks, tri)
+    run_steps(second)
     return tasks
 
 
@@ -268,7 +308,7 @@ def _item(buf, a, b, part):
 def task_access(task, variant):
     """(reads, writes) item sets of a task; matrix 0 is A (m x n), matrix 1 the R copy of R-BiDiag."""
     typ, phase, k, i, piv, j = task
-    buf = 1 if (variant == RBIDIAG and phase != PQR) else 0
+    buf = task_buffer(phase, k, variant)
     lq = phase == LQ
 
     def act(a, b):
@@ -376,6 +416,17 @@ def critical_path(p, q, tree, variant, resources=None):
     """Critical path length (Table 1 units) of the task DAG, unbounded resources (Sec. 4 model)."""
     tasks = task_list(p, q, tree, variant, resources)
     return dag(tasks, variant)[2]
+
+
+def best_split(p, q, tree, resources=None):
+    """Sec. 4.5: the three-step split with the shortest critical path, found by trying every
+    s in [0, q); ties keep the smallest s.  Returns (s, critical path)."""
+    best = None
+    for s in range(q):
+        c = critical_path(p, q, tree, THREESTEP + s, resources)
+        if best is None or c < best[1]:
+            best = (s, c)
+    return best
 
 
 def weight_total(tasks):

@@ -20,8 +20,13 @@ LIB_PATH = os.path.join(_HERE, "libbidiag.so")
 
 FLATTS, FLATTT, GREEDY, AUTO = 0, 1, 2, 3
 TREES = {"flatts": FLATTS, "flattt": FLATTT, "greedy": GREEDY, "auto": AUTO}
-BIDIAG, RBIDIAG, AUTO_VARIANT = 0, 1, 2
-VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG, "auto": AUTO_VARIANT}
+BIDIAG, RBIDIAG, AUTO_VARIANT, THREESTEP = 0, 1, 2, 3
+VARIANTS = {"bidiag": BIDIAG, "rbidiag": RBIDIAG, "auto": AUTO_VARIANT, "threestep": THREESTEP}
+
+
+def threestep_split(s):
+    """Variant code of the three-step reduction with s BiDiag steps before the switch (Sec. 4.5)."""
+    return 4 + s
 OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = 0, 1, 2, 3, 4, 5
 NOALLOC_SCRATCH_BYTES = 8 << 20
 OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING, OPT_TRACE = 1, 2, 3, 4, 5, 6
@@ -85,6 +90,7 @@ def load_library(path=LIB_PATH):
         "bidiag_plan_eliminations": (cint, [i64, i64, cint, cint, i64, P(i32), i64, P(i64)]),
         "bidiag_plan_tasks": (cint, [i64, i64, cint, cint, i64, P(i32), P(i32), i64, P(i64), P(i64)]),
         "bidiag_plan_choose_variant": (cint, [i64, i64, cint, i64, P(cint), P(i64), P(i64)]),
+        "bidiag_plan_best_split": (cint, [i64, i64, cint, i64, P(cint), P(i64)]),
         "bidiag_plan_program": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), i64, P(i64), P(i32),
                                        i64, P(i64), P(i32)]),
         "bidiag_plan_backward": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), P(i32), i64, P(i64),
@@ -220,6 +226,13 @@ def bidiag_plan_choose_variant(p, q, tree, resources=1):
     _check(None, load_library().bidiag_plan_choose_variant(p, q, tree, resources, ctypes.byref(v), ctypes.byref(cb),
                                                           ctypes.byref(cr)))
     return v.value, cb.value, cr.value
+
+
+def bidiag_plan_best_split(p, q, tree, resources=1):
+    """(split, critical path) of the best three-step split for p x q tiles."""
+    sp, cp = ctypes.c_int(), ctypes.c_int64()
+    _check(None, load_library().bidiag_plan_best_split(p, q, tree, resources, ctypes.byref(sp), ctypes.byref(cp)))
+    return sp.value, cp.value
 
 
 def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):

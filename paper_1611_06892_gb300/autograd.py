@@ -31,7 +31,7 @@ def _handle(device):
 def reflector_bytes(m, n, nb, ib, variant, esize):
     """Device bytes of a result's reflector store (tiles, R copy, T factors), as the library sizes it."""
     p, q = -(-m // nb), -(-n // nb)
-    tiles = p * q + (q * q if variant == "rbidiag" else 0)
+    tiles = p * q + (0 if variant in ("bidiag", 0) else q * q)
     panels = 2 * p * q        # upper bound on the panel tasks of either variant
     return esize * (tiles * nb * nb + panels * ib * nb)
 

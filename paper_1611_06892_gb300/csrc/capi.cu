@@ -88,6 +88,7 @@ struct bidiag_ctx {
   int tracing = 0;
   int f32_simt = 0;                // FP32 storage: updates by FFMA instead of 3xTF32 tensor-core products
   int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
+  std::map<std::tuple<int, int, int, int64_t>, int> splits;   // best three-step split per (p, q, tree, R)
   int64_t trace_cap = 0, trace_len = 0;
 };
 
@@ -321,7 +322,7 @@ int apply_side(bidiag_handle h, bidiag_result_t r, bool left, int trans, int64_t
   };
   for (int32_t x : panels) {
     const bd::Task& t = pl.tasks[x];
-    const int buf = (r->variant == BIDIAG_RBIDIAG && t.phase != bd::PH_PQR) ? 1 : 0;
+    const int buf = bd::task_buffer(t.phase, t.k, r->variant);
     const int grid_rows = buf == 0 ? r->p : r->q;
     const bool lq = t.phase == bd::PH_LQ;
     const int ax = lq ? t.k : t.i, ay = lq ? t.i : t.k;     // actual tile of oriented (i, k)
@@ -384,7 +385,8 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   if (nb < 1 || nb > bd::kMaxNb) return fail(h, -6, "nb out of range");
   if (ib < 1 || ib > std::min(nb, 64) || nb % ib) return fail(h, -7, "ib out of range or does not divide nb");
   if (tree < 0 || tree > 3) return fail(h, -8, "unknown tree");
-  if (variant < 0 || variant > 2) return fail(h, -9, "unknown variant");
+  if (variant < 0 || (variant > BIDIAG_THREESTEP && variant - BIDIAG_THREESTEP_SPLIT(0) >= (n + nb - 1) / nb))
+    return fail(h, -9, "unknown variant or three-step split >= q");
   if (!out) return fail(h, -10, "out is NULL");
   *out = nullptr;
   if (m < n) return fail(h, BIDIAG_ERR_UNSUPPORTED, "m < n: reduce the transpose");
@@ -392,14 +394,24 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   int w = 0;
   int rc = choose_strip(h, nb, ib, (int)sizeof(E), &w);
   if (rc) return rc;
-  if (variant == BIDIAG_AUTO_VARIANT) {
+  if (variant == BIDIAG_AUTO_VARIANT || variant == BIDIAG_THREESTEP) {
+    const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
+    const int64_t R = resources_of(h, nb, w);
     try {
-      variant = bd::choose_variant((int)((m + nb - 1) / nb), (int)((n + nb - 1) / nb), tree, resources_of(h, nb, w),
-                                   nullptr, nullptr);
+      if (variant == BIDIAG_AUTO_VARIANT) {
+        variant = bd::choose_variant(p, q, tree, R, nullptr, nullptr);
+      } else {
+        const auto key = std::make_tuple(p, q, tree, R);
+        auto it = h->splits.find(key);
+        const int sp = it != h->splits.end() ? it->second : bd::best_split(p, q, tree, R, nullptr);
+        h->splits[key] = sp;
+        variant = BIDIAG_THREESTEP_SPLIT(sp);
+      }
     } catch (...) {
       return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while choosing the variant");
     }
   }
+  if (variant == BIDIAG_THREESTEP_SPLIT(0)) variant = BIDIAG_RBIDIAG;   // the same task list
   std::shared_ptr<PlanDev> pd;
   rc = get_plan(h, m, n, nb, ib, tree, variant, w, &pd);
   if (rc) return rc;
@@ -420,7 +432,7 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   const size_t tile_elems = (size_t)nb * nb;
   E *tiles = nullptr, *tiles2 = nullptr, *Tst = nullptr, *ab = nullptr;
   rc = dev_alloc(h, &tiles, (size_t)r->p * r->q * tile_elems);
-  if (!rc && variant == BIDIAG_RBIDIAG) rc = dev_alloc(h, &tiles2, (size_t)r->q * r->q * tile_elems);
+  if (!rc && bd::split_of(variant) >= 0) rc = dev_alloc(h, &tiles2, (size_t)r->q * r->q * tile_elems);
   if (!rc) rc = dev_alloc(h, &Tst, (size_t)std::max(1, pd->plan.npanels) * ib * nb);
   if (!rc) rc = dev_alloc(h, &ab, (size_t)(nb + 1) * n);
   r->tiles = tiles;
@@ -454,7 +466,13 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
                 timed);
   h->timed = timed;
   if (rc) return bail(rc);
-  e = bd::launch_extract(tiles2 ? tiles2 : tiles, tiles2 ? r->q : r->p, nb, n, ab, r->ldab, h->stream);
+  if (tiles2 && variant != BIDIAG_RBIDIAG) {
+    // three-step: the band's first s tile rows come from the BiDiag steps on A, the rest from the R copy
+    e = bd::launch_extract_split(tiles, r->p, tiles2, r->q, (int64_t)bd::split_of(variant) * nb, nb, n, ab, r->ldab,
+                                 h->stream);
+  } else {
+    e = bd::launch_extract(tiles2 ? tiles2 : tiles, tiles2 ? r->q : r->p, nb, n, ab, r->ldab, h->stream);
+  }
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "extract"));
   h->live.insert(r);
   *out = r;
@@ -506,6 +524,8 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
   // forward wrote (A tiles for BiDiag, the R copy for R-BiDiag); for R-BiDiag the A tiles' state is the
   // pre-QR's R factor, which the forward leaves in the upper part of its tiles.
   const bool rb = r->tiles2 != nullptr;
+  const int split = std::max(0, bd::split_of(r->variant));      // three-step: first-phase tile rows
+  const int64_t srow = (int64_t)split * nb;
   const int64_t ntiles = (int64_t)r->p * r->q, ntiles2 = rb ? (int64_t)r->q * r->q : 0;
   const size_t tile_elems = (size_t)nb * nb;
   E *S = nullptr, *G = nullptr, *S2 = nullptr, *G2 = nullptr, *part = nullptr, *red = nullptr;
@@ -523,15 +543,20 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
     release();
     return rc;
   }
+  // band rows [0, srow) belong to the A tiles (BiDiag, or the first phase of a three-step), the others
+  // to the R copy; the A tiles of a two-phase reduction also hold the pre-QR's R factor (tiles from s on)
+  const E* abE = static_cast<const E*>(r->ab);
+  const int64_t arows = rb ? srow : r->n;
   cudaError_t e = cudaMemsetAsync(G, 0, (size_t)ntiles * tile_elems * esize, h->stream);
-  if (e == cudaSuccess && !rb) e = cudaMemsetAsync(S, 0, (size_t)ntiles * tile_elems * esize, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, (size_t)ntiles * tile_elems * esize, h->stream);
   if (e == cudaSuccess && rb) e = cudaMemsetAsync(S2, 0, (size_t)ntiles2 * tile_elems * esize, h->stream);
   if (e == cudaSuccess && rb) e = cudaMemsetAsync(G2, 0, (size_t)ntiles2 * tile_elems * esize, h->stream);
-  if (e == cudaSuccess && rb) e = bd::launch_r_part(static_cast<const E*>(r->tiles), S, r->p, r->q, nb, h->stream);
-  if (e == cudaSuccess)
-    e = bd::launch_scatter_band(static_cast<const E*>(r->ab), r->ldab, nb, r->n, rb ? S2 : S, rb ? r->q : r->p,
-                                h->stream);
-  if (e == cudaSuccess) e = bd::launch_scatter_band(d_abbar, ldab, nb, r->n, rb ? G2 : G, rb ? r->q : r->p, h->stream);
+  if (e == cudaSuccess && rb)
+    e = bd::launch_r_part(static_cast<const E*>(r->tiles), S, r->p, r->q, nb, split, h->stream);
+  if (e == cudaSuccess && arows > 0) e = bd::launch_scatter_band(abE, r->ldab, nb, r->n, S, r->p, 0, arows, h->stream);
+  if (e == cudaSuccess && rb) e = bd::launch_scatter_band(abE, r->ldab, nb, r->n, S2, r->q, srow, r->n, h->stream);
+  if (e == cudaSuccess && arows > 0) e = bd::launch_scatter_band(d_abbar, ldab, nb, r->n, G, r->p, 0, arows, h->stream);
+  if (e == cudaSuccess && rb) e = bd::launch_scatter_band(d_abbar, ldab, nb, r->n, G2, r->q, srow, r->n, h->stream);
   if (e != cudaSuccess) {
     release();
     return cuda_fail(h, e, "adjoint set-up");
@@ -615,7 +640,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
             bad[(size_t)b] = -7;
             continue;
           }
-          if (o.tree < 0 || o.tree > 3 || o.variant < 0 || o.variant > 2) {
+          if (o.tree < 0 || o.tree > 3 || o.variant < 0 || o.variant > 2) {   // no three-step in batches
             bad[(size_t)b] = -9;
             continue;
           }
@@ -1083,7 +1108,7 @@ int bidiag_plan_eliminations(int64_t p, int64_t q, int tree, int variant, int64_
                              int64_t* count) {
   if (p < 1 || q < 1 || q > p) return -1;
   if (tree < 0 || tree > 3) return -3;
-  if (variant < 0 || variant > 1) return -4;
+  if (variant < 0 || variant == 2 || variant == 3 || variant - BIDIAG_THREESTEP_SPLIT(0) >= q) return -4;
   if (!count) return -8;
   try {
     auto el = bd::make_eliminations((int)p, (int)q, tree, variant, resources);
@@ -1104,7 +1129,7 @@ int bidiag_plan_tasks(int64_t p, int64_t q, int tree, int variant, int64_t resou
                       int64_t cap, int64_t* count, int64_t* cp) {
   if (p < 1 || q < 1 || q > p) return -1;
   if (tree < 0 || tree > 3) return -3;
-  if (variant < 0 || variant > 1) return -4;
+  if (variant < 0 || variant == 2 || variant == 3 || variant - BIDIAG_THREESTEP_SPLIT(0) >= q) return -4;
   if (!count) return -9;
   try {
     auto ts = bd::make_tasks((int)p, (int)q, tree, variant, resources);
@@ -1141,6 +1166,20 @@ int bidiag_plan_choose_variant(int64_t p, int64_t q, int tree, int64_t resources
   return BIDIAG_OK;
 }
 
+int bidiag_plan_best_split(int64_t p, int64_t q, int tree, int64_t resources, int* split, int64_t* cp) {
+  if (q < 1 || p < q) return -1;
+  if (tree < 0 || tree > 3) return -3;
+  if (!split) return -5;
+  try {
+    *split = bd::best_split((int)p, (int)q, tree, resources, cp);
+  } catch (const std::bad_alloc&) {
+    return BIDIAG_ERR_NOMEM;
+  } catch (...) {
+    return BIDIAG_ERR_UNSUPPORTED;
+  }
+  return BIDIAG_OK;
+}
+
 int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources, int strip_w,
                         int32_t* program, int64_t cap, int64_t* count, int32_t* deps, int64_t dcap, int64_t* ndeps,
                         int32_t* strip_w_used) {
@@ -1148,7 +1187,8 @@ int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int vari
   if (nb < 1 || nb > bd::kMaxNb) return -3;
   if (ib < 1 || nb % ib) return -4;
   if (tree < 0 || tree > 3) return -5;
-  if (variant < 0 || variant > 1) return -6;
+  if (variant < 0 || variant == 2 || variant == 3 || variant - BIDIAG_THREESTEP_SPLIT(0) >= (n + nb - 1) / nb)
+    return -6;
   if (!count || !ndeps) return -9;
   int w = std::max(ib, (strip_w / ib) * ib);
   w = std::min(w, nb);
@@ -1176,7 +1216,8 @@ int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int var
   if (nb < 1 || nb > bd::kMaxNb) return -3;
   if (ib < 1 || nb % ib) return -4;
   if (tree < 0 || tree > 3) return -5;
-  if (variant < 0 || variant > 1) return -6;
+  if (variant < 0 || variant == 2 || variant == 3 || variant - BIDIAG_THREESTEP_SPLIT(0) >= (n + nb - 1) / nb)
+    return -6;
   if (!count || !ndeps || !nslot_off || !npinfo) return -10;
   int w = std::max(ib, (strip_w / ib) * ib);
   w = std::min(w, nb);

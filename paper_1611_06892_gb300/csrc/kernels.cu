@@ -1183,11 +1183,14 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
 }
 
 template <typename E>
-__global__ void r_part_kernel(const E* __restrict__ src, E* __restrict__ dst, int64_t rows_t, int64_t cols_t, int nb) {
+__global__ void r_part_kernel(const E* __restrict__ src, E* __restrict__ dst, int64_t rows_t, int64_t cols_t, int nb,
+                              int s0) {
   const int64_t tile = blockIdx.x;
   const int64_t a = tile % rows_t, b = tile / rows_t;
   const E* s = src + (size_t)tile * nb * nb;
   E* d = dst + (size_t)tile * nb * nb;
+  // tiles outside the trailing block keep what is already in dst (the first phase's band)
+  if (a < s0) return;
   for (int o = threadIdx.x; o < nb * nb; o += blockDim.x) {
     const int r = o % nb, c = o / nb;
     const bool keep = a < cols_t && (a < b || (a == b && r <= c));
@@ -1195,15 +1198,32 @@ __global__ void r_part_kernel(const E* __restrict__ src, E* __restrict__ dst, in
   }
 }
 
-// Band into a zeroed tile buffer: tile (i / nb, j / nb) entry (i % nb, j % nb) = ab(nb + i - j, j).
+// Band rows [r0, r1) into a zeroed tile buffer: tile (i / nb, j / nb) entry (i % nb, j % nb) =
+// ab(nb + i - j, j).
 template <typename E>
 __global__ void scatter_band_kernel(const E* __restrict__ ab, int64_t ldab, int nb, int64_t n, E* __restrict__ tiles,
-                                    int64_t rows_t) {
+                                    int64_t rows_t, int64_t r0, int64_t r1) {
   const int64_t j = blockIdx.x;
   for (int d = threadIdx.x; d <= nb; d += blockDim.x) {
     const int64_t i = j + d - nb;
-    if (i < 0) continue;
+    if (i < r0 || i >= r1 || i < 0) continue;
     tiles[(size_t)((j / nb) * rows_t + i / nb) * nb * nb + (i % nb) + (j % nb) * nb] = ab[d + j * ldab];
+  }
+}
+
+template <typename E>
+__global__ void extract_split_kernel(const E* __restrict__ A, int64_t pa, const E* __restrict__ R, int64_t pr,
+                                     int64_t srow, int nb, int64_t n, E* __restrict__ ab, int64_t ldab) {
+  const int64_t j = blockIdx.x;
+  for (int d = threadIdx.x; d <= nb; d += blockDim.x) {
+    const int64_t i = j + d - nb;
+    E v = E(0);
+    if (i >= 0) {
+      const E* t = i < srow ? A : R;
+      const int64_t rows_t = i < srow ? pa : pr;
+      v = t[(size_t)((j / nb) * rows_t + i / nb) * nb * nb + (i % nb) + (j % nb) * nb];
+    }
+    ab[d + j * ldab] = v;
   }
 }
 
@@ -1414,30 +1434,47 @@ cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t 
   return extract_t(tiles, rows_t, nb, n, ab, ldab, st);
 }
 template <typename E>
-cudaError_t r_part_t(const E* src, E* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st) {
+cudaError_t r_part_t(const E* src, E* dst, int64_t rows_t, int64_t cols_t, int nb, int s, cudaStream_t st) {
   if (rows_t * cols_t == 0) return cudaSuccess;
-  r_part_kernel<E><<<(unsigned)(rows_t * cols_t), 256, 0, st>>>(src, dst, rows_t, cols_t, nb);
+  r_part_kernel<E><<<(unsigned)(rows_t * cols_t), 256, 0, st>>>(src, dst, rows_t, cols_t, nb, s);
   return cudaGetLastError();
 }
-cudaError_t launch_r_part(const double* src, double* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st) {
-  return r_part_t(src, dst, rows_t, cols_t, nb, st);
+cudaError_t launch_r_part(const double* src, double* dst, int64_t rows_t, int64_t cols_t, int nb, int s,
+                          cudaStream_t st) {
+  return r_part_t(src, dst, rows_t, cols_t, nb, s, st);
 }
-cudaError_t launch_r_part(const float* src, float* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st) {
-  return r_part_t(src, dst, rows_t, cols_t, nb, st);
+cudaError_t launch_r_part(const float* src, float* dst, int64_t rows_t, int64_t cols_t, int nb, int s, cudaStream_t st) {
+  return r_part_t(src, dst, rows_t, cols_t, nb, s, st);
 }
 template <typename E>
-cudaError_t scatter_t(const E* ab, int64_t ldab, int nb, int64_t n, E* tiles, int64_t rows_t, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  scatter_band_kernel<E><<<(unsigned)n, 256, 0, st>>>(ab, ldab, nb, n, tiles, rows_t);
+cudaError_t scatter_t(const E* ab, int64_t ldab, int nb, int64_t n, E* tiles, int64_t rows_t, int64_t r0, int64_t r1,
+                      cudaStream_t st) {
+  if (n == 0 || r1 <= r0) return cudaSuccess;
+  scatter_band_kernel<E><<<(unsigned)n, 256, 0, st>>>(ab, ldab, nb, n, tiles, rows_t, r0, r1);
   return cudaGetLastError();
 }
 cudaError_t launch_scatter_band(const double* ab, int64_t ldab, int nb, int64_t n, double* tiles, int64_t rows_t,
-                                cudaStream_t st) {
-  return scatter_t(ab, ldab, nb, n, tiles, rows_t, st);
+                                int64_t r0, int64_t r1, cudaStream_t st) {
+  return scatter_t(ab, ldab, nb, n, tiles, rows_t, r0, r1, st);
 }
 cudaError_t launch_scatter_band(const float* ab, int64_t ldab, int nb, int64_t n, float* tiles, int64_t rows_t,
-                                cudaStream_t st) {
-  return scatter_t(ab, ldab, nb, n, tiles, rows_t, st);
+                                int64_t r0, int64_t r1, cudaStream_t st) {
+  return scatter_t(ab, ldab, nb, n, tiles, rows_t, r0, r1, st);
+}
+template <typename E>
+cudaError_t extract_split_t(const E* A, int64_t pa, const E* R, int64_t pr, int64_t srow, int nb, int64_t n, E* ab,
+                            int64_t ldab, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  extract_split_kernel<E><<<(unsigned)n, 256, 0, st>>>(A, pa, R, pr, srow, nb, n, ab, ldab);
+  return cudaGetLastError();
+}
+cudaError_t launch_extract_split(const double* A, int64_t pa, const double* R, int64_t pr, int64_t srow, int nb,
+                                 int64_t n, double* ab, int64_t ldab, cudaStream_t st) {
+  return extract_split_t(A, pa, R, pr, srow, nb, n, ab, ldab, st);
+}
+cudaError_t launch_extract_split(const float* A, int64_t pa, const float* R, int64_t pr, int64_t srow, int nb,
+                                 int64_t n, float* ab, int64_t ldab, cudaStream_t st) {
+  return extract_split_t(A, pa, R, pr, srow, nb, n, ab, ldab, st);
 }
 cudaError_t launch_extract(const float* tiles, int64_t rows_t, int nb, int64_t n, float* ab, int64_t ldab,
                            cudaStream_t st) {

@@ -94,13 +94,21 @@ cudaError_t launch_pack_batched(const PackDesc* d, int count, int64_t total_tile
 cudaError_t launch_extract_batched(const PackDesc* d, int count, int64_t total_cols, int esize, cudaStream_t st);
 // R-BiDiag adjoint start: dst = the R factor of the pre-QR held in src (tiles (a, b) with a <= b < q:
 // upper triangle of diagonal tiles, whole tiles above), zero elsewhere; grid rows_t x cols_t.
-cudaError_t launch_r_part(const double* src, double* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st);
-cudaError_t launch_r_part(const float* src, float* dst, int64_t rows_t, int64_t cols_t, int nb, cudaStream_t st);
-// Band ab ((nb+1) x n, ld ldab) into a zeroed tile buffer (grid rows rows_t): the inverse of extraction.
+// Only tiles with a >= s (the trailing block of a three-step) are kept.
+cudaError_t launch_r_part(const double* src, double* dst, int64_t rows_t, int64_t cols_t, int nb, int s,
+                          cudaStream_t st);
+cudaError_t launch_r_part(const float* src, float* dst, int64_t rows_t, int64_t cols_t, int nb, int s, cudaStream_t st);
+// Band rows [r0, r1) of ab ((nb+1) x n, ld ldab) into a zeroed tile buffer (grid rows rows_t): the
+// inverse of extraction.
 cudaError_t launch_scatter_band(const double* ab, int64_t ldab, int nb, int64_t n, double* tiles, int64_t rows_t,
-                                cudaStream_t st);
+                                int64_t r0, int64_t r1, cudaStream_t st);
 cudaError_t launch_scatter_band(const float* ab, int64_t ldab, int nb, int64_t n, float* tiles, int64_t rows_t,
-                                cudaStream_t st);
+                                int64_t r0, int64_t r1, cudaStream_t st);
+// Three-step band extraction: band rows < srow from tiles A (grid rows pa), the others from tiles R.
+cudaError_t launch_extract_split(const double* A, int64_t pa, const double* R, int64_t pr, int64_t srow, int nb,
+                                 int64_t n, double* ab, int64_t ldab, cudaStream_t st);
+cudaError_t launch_extract_split(const float* A, int64_t pa, const float* R, int64_t pr, int64_t srow, int nb,
+                                 int64_t n, float* ab, int64_t ldab, cudaStream_t st);
 // Band extraction: ab((nb+1) x n, ld ldab) from the tile buffer (grid rows rows_t).
 cudaError_t launch_extract(const double* tiles, int64_t rows_t, int nb, int64_t n, double* ab, int64_t ldab,
                            cudaStream_t st);

@@ -124,25 +124,43 @@ struct Step {
   int ntrail;
 };
 
-std::vector<Step> steps_of(int p, int q, int variant) {
-  std::vector<Step> st;
+// Steps of the first phase (BiDiag on A: all of them for BiDiag, the first s for a split s) and of
+// the second (BiDiag of the trailing R after the pre-QR).
+void steps_of(int p, int q, int variant, std::vector<Step>* first, std::vector<Step>* second) {
   auto range = [](int a, int b) {
     std::vector<int> r;
     for (int x = a; x < b; ++x) r.push_back(x);
     return r;
   };
-  if (variant == V_BIDIAG) {
-    for (int k = 0; k < q; ++k) {
-      st.push_back({PH_QR, k, range(k, p), q - k - 1});
-      if (k < q - 1) st.push_back({PH_LQ, k, range(k + 1, q), p - k - 1});
-    }
-  } else {
-    for (int k = 0; k + 1 < q; ++k) {
-      st.push_back({PH_LQ, k, range(k + 1, q), q - k - 1});
-      st.push_back({PH_QR, k + 1, range(k + 1, q), q - k - 2});
+  const int s = split_of(variant);
+  if (s >= q || s < -1) throw std::invalid_argument("three-step split must be in [0, q)");
+  first->clear();
+  second->clear();
+  for (int k = 0; k < (s < 0 ? q : s); ++k) {
+    first->push_back({PH_QR, k, range(k, p), q - k - 1});
+    if (k < q - 1) first->push_back({PH_LQ, k, range(k + 1, q), p - k - 1});
+  }
+  if (s >= 0) {
+    for (int k = s; k + 1 < q; ++k) {
+      second->push_back({PH_LQ, k, range(k + 1, q), q - k - 1});
+      second->push_back({PH_QR, k + 1, range(k + 1, q), q - k - 2});
     }
   }
-  return st;
+}
+
+// Eliminations of the pre-QR of tiles s..p-1 x s..q-1 in program order.
+std::vector<Elim> preqr_eliminations(int p, int q, int s, int tree, int64_t R) {
+  std::vector<Elim> out;
+  if (tree == GREEDY) {
+    for (auto& e : greedy_columns(p - s, q - s)) out.push_back({PH_PQR, e.k + s, e.i + s, e.piv + s, K_TT});
+  } else {
+    for (int k = s; k < q; ++k) {
+      std::vector<int> rows;
+      for (int r = k; r < p; ++r) rows.push_back(r);
+      for (auto& e : one_step(rows, q - k - 1, tree, R)) out.push_back({PH_PQR, k, e.i, e.piv, e.kind});
+    }
+  }
+  return out;
 }
 
 // Expansion of eliminations into kernel tasks (Algorithms 2 and 3).
@@ -187,19 +205,15 @@ struct Expander {
 
 std::vector<Elim> make_eliminations(int p, int q, int tree, int variant, int64_t R) {
   std::vector<Elim> out;
-  if (variant == V_RBIDIAG) {
-    if (tree == GREEDY) {
-      for (auto& e : greedy_columns(p, q)) out.push_back({PH_PQR, e.k, e.i, e.piv, K_TT});
-    } else {
-      for (int k = 0; k < std::min(p, q); ++k) {
-        std::vector<int> rows;
-        for (int r = k; r < p; ++r) rows.push_back(r);
-        for (auto& e : one_step(rows, q - k - 1, tree, R)) out.push_back({PH_PQR, k, e.i, e.piv, e.kind});
-      }
-    }
-  }
-  for (auto& s : steps_of(p, q, variant))
-    for (auto& e : one_step(s.rows, s.ntrail, tree, R)) out.push_back({s.phase, s.k, e.i, e.piv, e.kind});
+  std::vector<Step> first, second;
+  steps_of(p, q, variant, &first, &second);
+  for (auto& st : first)
+    for (auto& e : one_step(st.rows, st.ntrail, tree, R)) out.push_back({st.phase, st.k, e.i, e.piv, e.kind});
+  const int s = split_of(variant);
+  if (s >= 0)
+    for (auto& e : preqr_eliminations(p, q, s, tree, R)) out.push_back(e);
+  for (auto& st : second)
+    for (auto& e : one_step(st.rows, st.ntrail, tree, R)) out.push_back({st.phase, st.k, e.i, e.piv, e.kind});
   return out;
 }
 
@@ -207,17 +221,28 @@ std::vector<Task> make_tasks(int p, int q, int tree, int variant, int64_t R) {
   if (!(p >= q && q >= 1)) throw std::invalid_argument("need p >= q >= 1");
   std::vector<Task> tasks;
   Expander ex(tasks, p);
-  if (variant == V_RBIDIAG) {
+  std::vector<Step> first, second;
+  steps_of(p, q, variant, &first, &second);
+  auto run = [&](const std::vector<Step>& steps) {
+    for (auto& st : steps) {
+      auto el = one_step(st.rows, st.ntrail, tree, R);
+      if (el.empty()) ex.single(st.phase, st.k, st.rows[0], st.ntrail);
+      for (auto& e : el) ex.elim(st.phase, st.k, e, st.ntrail);
+    }
+  };
+  run(first);
+  const int s = split_of(variant);
+  if (s >= 0) {
     if (tree == GREEDY) {
       std::vector<char> seen(q, 0);
-      for (auto& e : greedy_columns(p, q)) {
+      for (auto& e : preqr_eliminations(p, q, s, tree, R)) {
         ex.elim(PH_PQR, e.k, {e.i, e.piv, K_TT}, q - e.k - 1);
         seen[e.k] = 1;
       }
-      for (int k = 0; k < std::min(p, q); ++k)
+      for (int k = s; k < q; ++k)
         if (!seen[k]) ex.single(PH_PQR, k, k, q - k - 1);
     } else {
-      for (int k = 0; k < std::min(p, q); ++k) {
+      for (int k = s; k < q; ++k) {
         std::vector<int> rows;
         for (int r = k; r < p; ++r) rows.push_back(r);
         auto el = one_step(rows, q - k - 1, tree, R);
@@ -225,14 +250,10 @@ std::vector<Task> make_tasks(int p, int q, int tree, int variant, int64_t R) {
         for (auto& e : el) ex.elim(PH_PQR, k, e, q - k - 1);
       }
     }
-    for (int a = 0; a < q; ++a)
+    for (int a = s; a < q; ++a)
       for (int b = a; b < q; ++b) tasks.push_back({COPY, PH_PQR, -1, a, -1, b});
   }
-  for (auto& s : steps_of(p, q, variant)) {
-    auto el = one_step(s.rows, s.ntrail, tree, R);
-    if (el.empty()) ex.single(s.phase, s.k, s.rows[0], s.ntrail);
-    for (auto& e : el) ex.elim(s.phase, s.k, e, s.ntrail);
-  }
+  run(second);
   return tasks;
 }
 
@@ -257,7 +278,7 @@ struct ItemMap {
 
 Access access_of(const Task& t, int variant, const ItemMap& im) {
   Access ac;
-  const int buf = (variant == V_RBIDIAG && t.phase != PH_PQR) ? 1 : 0;
+  const int buf = task_buffer(t.phase, t.k, variant);
   const bool lq = t.phase == PH_LQ;
   auto put = [&](int* arr, int& n, int a, int b, int part) {
     const int x = lq ? b : a, y = lq ? a : b;
@@ -371,6 +392,21 @@ int choose_variant(int p, int q, int tree, int64_t R, int64_t* cp_bidiag, int64_
   if (cp_bidiag) *cp_bidiag = cb;
   if (cp_rbidiag) *cp_rbidiag = cr;
   return cr < cb ? V_RBIDIAG : V_BIDIAG;
+}
+
+int best_split(int p, int q, int tree, int64_t R, int64_t* cp) {
+  int best = 0;
+  int64_t best_cp = -1;
+  for (int s = 0; s < q; ++s) {
+    int64_t c = 0;
+    make_dag(make_tasks(p, q, tree, V_THREESTEP + s, R), p, q, V_THREESTEP + s, nullptr, nullptr, &c);
+    if (best_cp < 0 || c < best_cp) {
+      best_cp = c;
+      best = s;
+    }
+  }
+  if (cp) *cp = best_cp;
+  return best;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -529,7 +565,7 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
 
   for (size_t x = 0; x < nt; ++x) {
     const Task& t = pl.tasks[x];
-    const int buf = (variant == V_RBIDIAG && t.phase != PH_PQR) ? 1 : 0;
+    const int buf = task_buffer(t.phase, t.k, variant);
     const bool lq = t.phase == PH_LQ;
     if (t.type == GEQRT || t.type == TSQRT || t.type == TTQRT) {
       const int kind = t.type == GEQRT ? PK_GE : (t.type == TSQRT ? PK_TS : PK_TT);

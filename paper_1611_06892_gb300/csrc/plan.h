@@ -17,6 +17,18 @@ enum BwdType : int { BPF = 9, BPU = 10, BUPD = 11, BCOPY = 12 };
 enum Phase : int { PH_QR = 0, PH_LQ = 1, PH_PQR = 2 };
 enum Tree : int { FLATTS = 0, FLATTT = 1, GREEDY = 2, AUTO = 3 };
 enum Variant : int { V_BIDIAG = 0, V_RBIDIAG = 1 };
+// Three-step (Sec. 4.5) with split s: s BiDiag steps on A, then R-BiDiag on the trailing tiles.
+// Encoded as variant V_THREESTEP + s; R-BiDiag is the split s = 0.
+constexpr int V_THREESTEP = 4;
+// Number of BiDiag steps before the switch to R-BiDiag (-1 for BiDiag: no second phase).
+inline int split_of(int variant) { return variant == V_BIDIAG ? -1 : (variant == V_RBIDIAG ? 0 : variant - V_THREESTEP); }
+// Matrix a task works on: 0 = A, 1 = the R copy of the second phase (its LQ steps k >= s and QR steps
+// k >= s + 1; QR(s) belongs to the pre-QR).
+inline int task_buffer(int phase, int k, int variant) {
+  const int s = split_of(variant);
+  if (s < 0 || phase == 2) return 0;
+  return ((phase == 1 && k >= s) || (phase == 0 && k > s)) ? 1 : 0;
+}
 enum Kind : int { K_TS = 0, K_TT = 1 };
 
 struct Task {
@@ -85,6 +97,9 @@ void make_dag(const std::vector<Task>& tasks, int p, int q, int variant,
 // matrices, switching at p/q = delta_s).  The Auto tree is compared through Greedy, whose critical path
 // the paper studies (Auto's has no meaning without a resource model).  Ties keep BiDiag.
 int choose_variant(int p, int q, int tree, int64_t resources, int64_t* cp_bidiag, int64_t* cp_rbidiag);
+// Sec. 4.5: the three-step split with the shortest critical path, trying every s in [0, q) (ties keep
+// the smallest s); returns s and, if cp is not null, its critical path.
+int best_split(int p, int q, int tree, int64_t resources, int64_t* cp);
 // Full plan for a reduction: tasks, DAG, device sub-tasks ordered by critical-path priority.
 void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
                 int strip_w);

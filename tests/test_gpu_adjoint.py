@@ -235,3 +235,22 @@ def test_adjoint_split_fp32(handle, torch_mod, case, variant):
     rec = np.abs(Arec.cpu().numpy().astype(np.float64) - A32).max() / np.abs(A32).max()
     assert rec <= 1e-5, rec
     res_g.free()
+
+
+@pytest.mark.parametrize("case", [(200, 136, 32, 8, 1), (300, 90, 32, 16, 2), (600, 520, 256, 32, 1)],
+                         ids=lambda c: "x".join(map(str, c)))
+@pytest.mark.parametrize("tree", ("flatts", "greedy", "auto"))
+def test_adjoint_parity_three_step(handle, torch_mod, case, tree):
+    torch = torch_mod
+    m, n, nb, ib, s = case
+    A = inputs.gaussian(m, n, seed=m + n + s)
+    W = inputs.gaussian(nb + 1, n, seed=5 * n)
+    v = G.threestep_split(s)
+    res_o = OB.bidiag_band(A, nb, ib, TREES[tree], v, resources=R_AUTO)
+    Ab_o, _ = AD.band_vjp(res_o, W)
+    res_g = handle.band(dev(torch, A), nb, ib, tree, v)
+    Ab_g, Arec = res_g.backward(dev(torch, W), reconstruct=True)
+    handle.sync()
+    assert np.abs(Ab_g.cpu().numpy() - Ab_o).max() <= TOL * max(1.0, np.abs(Ab_o).max())
+    assert np.abs(Arec.cpu().numpy() - A).max() <= 1e-12 * max(1.0, np.linalg.norm(A))
+    res_g.free()

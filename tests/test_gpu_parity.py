@@ -170,7 +170,8 @@ def test_argument_errors(handle, torch_mod):
     assert lib.bidiag_band(handle.h, 10, 8, p, 10, 300, 2, 0, 0, ctypes.byref(r)) == -6
     assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 3, 0, 0, ctypes.byref(r)) == -7
     assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 9, 0, ctypes.byref(r)) == -8
-    assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 0, 3, ctypes.byref(r)) == -9
+    assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 0, -1, ctypes.byref(r)) == -9
+    assert lib.bidiag_band(handle.h, 10, 8, p, 10, 4, 2, 0, 6, ctypes.byref(r)) == -9    # split 2 >= q
     assert lib.bidiag_band(handle.h, 8, 10, p, 10, 4, 2, 0, 0, ctypes.byref(r)) == G.ERR_UNSUPPORTED
     # shared memory limit: nb = 256 with ib = 64 does not fit
     big = to_dev(torch_mod, inputs.gaussian(256, 256, seed=2))
@@ -206,3 +207,39 @@ def test_auto_variant(handle, torch_mod):
         assert res_g.desc.variant == expect
         res_o = OB.bidiag_band(A, 16, 4, T.GREEDY, expect)
         compare(res_g, res_o, A, 16, 4)
+
+
+THREE_STEP_CASES = [
+    # m, n, nb, ib, split
+    (200, 136, 32, 8, 1),     # ragged 7 x 5 tiles
+    (200, 136, 32, 8, 3),
+    (300, 90, 32, 16, 1),     # tall, 10 x 3
+    (96, 96, 16, 4, 2),       # square 6 x 6
+    (600, 520, 256, 32, 1),   # the bench's tile size, 3 x 3 ragged
+]
+
+
+@pytest.mark.parametrize("case", THREE_STEP_CASES, ids=lambda c: "x".join(map(str, c)))
+@pytest.mark.parametrize("tree", list(TREES), ids=list(TREES))
+def test_parity_three_step(handle, torch_mod, case, tree):
+    """Three-step (Sec. 4.5) with a fixed split: band, tiles of both buffers, T and task list."""
+    m, n, nb, ib, s = case
+    A = inputs.gaussian(m, n, seed=m * 3 + n + s)
+    v = G.threestep_split(s)
+    res_o = OB.bidiag_band(A, nb, ib, TREES[tree], v, resources=R_AUTO)
+    res_g = gpu_reduce(handle, torch_mod, A, nb, ib, tree, v)
+    compare(res_g, res_o, A, nb, ib)
+    res_g.free()
+
+
+def test_three_step_best_split(handle, torch_mod):
+    """BIDIAG_THREESTEP picks the split with the shortest critical path and records it."""
+    m, n, nb, ib = 640, 160, 32, 8       # 20 x 5 tiles
+    A = inputs.gaussian(m, n, seed=77)
+    s, _ = G.bidiag_plan_best_split(20, 5, G.GREEDY, R_AUTO)
+    res_g = gpu_reduce(handle, torch_mod, A, nb, ib, "greedy", "threestep")
+    want = G.RBIDIAG if s == 0 else G.threestep_split(s)
+    assert res_g.desc.variant == want
+    res_o = OB.bidiag_band(A, nb, ib, T.GREEDY, T.THREESTEP + s, resources=R_AUTO)
+    compare(res_g, res_o, A, nb, ib)
+    res_g.free()

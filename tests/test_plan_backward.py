@@ -160,3 +160,10 @@ def test_checker_catches_a_reversed_edge(monkeypatch):
     monkeypatch.setattr(G, "bidiag_plan_backward", broken)
     with pytest.raises(AssertionError):
         check_backward(22, 20, 8, 4, 2, 0, strip_w=4)
+
+
+@pytest.mark.parametrize("split", (1, 2))
+@pytest.mark.parametrize("tree", (0, 1, 2, 3), ids=("flatts", "flattt", "greedy", "auto"))
+def test_adjoint_program_order_three_step(tree, split):
+    assert check_backward(22, 20, 8, 4, tree, 4 + split, strip_w=4) > 0
+    assert check_backward(30, 18, 6, 2, tree, 4 + split, strip_w=4) > 0

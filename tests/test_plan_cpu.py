@@ -94,7 +94,8 @@ def test_planner_argument_errors():
     cnt = ctypes.c_int64()
     assert lib.bidiag_plan_tasks(3, 4, 0, 0, 1, None, None, 0, ctypes.byref(cnt), None) == -1   # q > p
     assert lib.bidiag_plan_tasks(4, 3, 7, 0, 1, None, None, 0, ctypes.byref(cnt), None) == -3
-    assert lib.bidiag_plan_tasks(4, 3, 0, 5, 1, None, None, 0, ctypes.byref(cnt), None) == -4
+    assert lib.bidiag_plan_tasks(4, 3, 0, 2, 1, None, None, 0, ctypes.byref(cnt), None) == -4    # auto: not a plan
+    assert lib.bidiag_plan_tasks(4, 3, 0, 7, 1, None, None, 0, ctypes.byref(cnt), None) == -4    # split 3 >= q
     assert lib.bidiag_plan_eliminations(4, 3, 0, 0, 1, None, 0, None) == -8
 
 
@@ -120,3 +121,53 @@ def test_autotune_choices():
         assert (nb, ib) in ((32, 16), (64, 32), (128, 32))
         assert tree == T.FLATTS and variant in (T.BIDIAG, T.RBIDIAG)
         assert nb < 2 * max(32, n)          # never more than one size above the matrix's width
+
+
+def test_three_step_planner_matches_oracle():
+    """Three-step with every split s (Sec. 4.5): elimination list, task list, levels and critical path
+    bit-exact against the oracle; the best split agrees."""
+    for tree in (T.FLATTS, T.FLATTT, T.GREEDY, T.AUTO):
+        for p in range(1, 9):
+            for q in range(1, p + 1):
+                for s in range(q):
+                    v = T.THREESTEP + s
+                    tasks = T.task_list(p, q, tree, v, 3)
+                    tk, lv, cp = G.bidiag_plan_tasks(p, q, tree, v, 3)
+                    assert np.array_equal(np.array(tasks, dtype=np.int32).reshape(-1, 6), tk), (tree, p, q, s)
+                    lv_o, _, cp_o = T.dag(tasks, v)
+                    assert np.array_equal(np.array(lv_o, dtype=np.int32), lv) and cp == cp_o
+                    el_o = np.array(T.eliminations(p, q, tree, v, 3), dtype=np.int32).reshape(-1, 5)
+                    assert np.array_equal(el_o, G.bidiag_plan_eliminations(p, q, tree, v, 3))
+                assert G.bidiag_plan_best_split(p, q, tree, 3) == T.best_split(p, q, tree, 3)
+
+
+def test_three_step_end_points():
+    """Split 0 is R-BiDiag (same task list); split q-1 has BiDiag's critical path; so the best split is
+    never worse than either variant (Sec. 4.5)."""
+    for tree in (T.FLATTS, T.FLATTT, T.GREEDY, T.AUTO):
+        for (p, q) in ((5, 5), (9, 4), (13, 3), (7, 1), (20, 6)):
+            assert T.task_list(p, q, tree, T.RBIDIAG, 3) == T.task_list(p, q, tree, T.THREESTEP, 3)
+            cb = G.bidiag_plan_tasks(p, q, tree, T.BIDIAG, 3)[2]
+            cr = G.bidiag_plan_tasks(p, q, tree, T.RBIDIAG, 3)[2]
+            assert G.bidiag_plan_tasks(p, q, tree, T.THREESTEP + q - 1, 3)[2] == cb
+            assert G.bidiag_plan_best_split(p, q, tree, 3)[1] <= min(cb, cr)
+
+
+def test_three_step_figure_q30():
+    """Sec. 4.5, q = 30 tile columns, Greedy: the three-step equals BiDiag for square matrices, beats
+    both BiDiag and R-BiDiag in the middle region (p = 60 .. 260) and equals R-BiDiag beyond it (the
+    planner's critical paths; the planner is checked against the oracle above)."""
+    q = 30
+
+    def cps(p):
+        cb = G.bidiag_plan_tasks(p, q, T.GREEDY, T.BIDIAG)[2]
+        cr = G.bidiag_plan_tasks(p, q, T.GREEDY, T.RBIDIAG)[2]
+        return cb, cr, G.bidiag_plan_best_split(p, q, T.GREEDY)
+
+    cb, cr, (s, c3) = cps(30)
+    assert c3 == cb < cr
+    for p in (60, 100, 150, 200, 260):
+        cb, cr, (s, c3) = cps(p)
+        assert c3 < min(cb, cr) and 0 < s < q - 1, (p, cb, cr, s, c3)
+    cb, cr, (s, c3) = cps(300)
+    assert c3 == cr < cb and s == 0

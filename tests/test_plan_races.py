@@ -152,3 +152,11 @@ def test_checker_catches_a_missing_dependency(monkeypatch):
     monkeypatch.setattr(G, "bidiag_plan_program", broken)
     with pytest.raises(AssertionError, match="unordered conflict"):
         check_program(22, 20, 8, 4, 2, 0, strip_w=4)
+
+
+@pytest.mark.parametrize("split", (1, 2))
+@pytest.mark.parametrize("tree", (0, 1, 2, 3), ids=("flatts", "flattt", "greedy", "auto"))
+def test_three_step_program_is_race_free(tree, split):
+    """Three-step (Sec. 4.5): BiDiag steps on A, pre-QR of the trailing tiles, BiDiag on their R copy."""
+    assert check_program(22, 20, 8, 4, tree, 4 + split, strip_w=4) > 0
+    assert check_program(40, 24, 8, 4, tree, 4 + split, strip_w=8) > 0
