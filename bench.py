@@ -172,6 +172,18 @@ def barrier(world):
         dist.barrier()
 
 
+def variant_code(v):
+    """bidiag | rbidiag | auto | threestep | threestep:S | an integer code -> the library's variant code."""
+    if isinstance(v, int):
+        return v
+    v = str(v)
+    if v.startswith("threestep:"):
+        return 4 + int(v.split(":", 1)[1])
+    if v.lstrip("-").isdigit():
+        return int(v)
+    return {"bidiag": 0, "rbidiag": 1, "auto": 2, "threestep": 3}[v]
+
+
 def cpu_sample(path, w, tree, seconds, max_tasks=None):
     """Times the oracle (single BLAS thread) on the first tasks of the workload's task list."""
     import numpy as np
@@ -180,8 +192,15 @@ def cpu_sample(path, w, tree, seconds, max_tasks=None):
     from oracle import trees as T
 
     A = np.load(path, mmap_mode="r")
-    variant = {"bidiag": T.BIDIAG, "rbidiag": T.RBIDIAG}[w["variant"]]
+    variant = variant_code(w["variant"])
     treec = {"flatts": T.FLATTS, "flattt": T.FLATTT, "greedy": T.GREEDY, "auto": T.AUTO}[tree]
+    p, q = -(-A.shape[0] // w["nb"]), -(-A.shape[1] // w["nb"])
+    if variant == 2:      # the shorter critical path of the two variants (Sec. 4.3.3)
+        cb = T.critical_path(p, q, treec, T.BIDIAG, w["resources"])
+        cr = T.critical_path(p, q, treec, T.RBIDIAG, w["resources"])
+        variant = T.RBIDIAG if cr < cb else T.BIDIAG
+    elif variant == 3:    # the best three-step split (Sec. 4.5)
+        variant = T.THREESTEP + T.best_split(p, q, treec, w["resources"])[0]
     st = OB.new_state(np.asarray(A), w["nb"], w["ib"], treec, variant, resources=w["resources"])
     units = 0
     done = 0
@@ -204,7 +223,8 @@ def run_cpu_sample_subprocess(A_host_np, w, tree, seconds, max_tasks=None):
         np.save(path, A_host_np)
         env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
         cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", path, "--workload", w["name"],
-               "--tree", tree, "--cpu-seconds", str(seconds), "--auto-resources", str(w["resources"])]
+               "--tree", tree, "--cpu-seconds", str(seconds), "--auto-resources", str(w["resources"]),
+               "--variant", str(w.get("variant_used", w["variant"]))]
         if max_tasks:
             cmd += ["--cpu-max-tasks", str(max_tasks)]
         out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
@@ -524,6 +544,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS))
     ap.add_argument("--tree", default="auto", choices=("flatts", "flattt", "greedy", "auto"))
+    ap.add_argument("--variant", default=None,
+                    help="bidiag | rbidiag | auto | threestep (best split) | threestep:S (default: the workload's)")
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--precision", default="f64", choices=("f64", "f32"),
                     help="f32: FP32 storage with 3xTF32 tensor-core updates and FP64 reflector norms")
@@ -538,6 +560,8 @@ def main():
                     help="R of the Auto tree (default: SMs * 32 / nb, as the library chooses)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload], name=args.workload)
+    if args.variant:
+        w["variant"] = args.variant
     if args.workload == "square512" and args.tree == "auto":
         args.tree = "flatts"
 
@@ -565,7 +589,8 @@ def main():
     flops = metric_flops(m, n)
     f32 = args.precision == "f32"
     desc = w["desc"].replace("FP64", "FP32 storage (3xTF32 updates)") if f32 else w["desc"]
-    config = {"workload": desc + f", tree={args.tree}", "m": m, "n": n, "nb": nb, "ib": ib,
+    config = {"workload": desc + f", tree={args.tree}" + (f", variant={args.variant}" if args.variant else ""),
+              "m": m, "n": n, "nb": nb, "ib": ib,
               "tree": args.tree, "variant": w["variant"], "auto_resources": w["resources"],
               "l2": f"input {m * n * 8 / 2**20:.0f} MiB > 129 MB L2 (no flush needed)" if m * n * 8 > 129e6
               else "input smaller than L2"}
@@ -629,10 +654,13 @@ def main():
     h.set_option(G.OPT_AUTO_RESOURCES, w["resources"])
     stream = h.stream
 
+    vcode = variant_code(w["variant"])
+
     def step():
-        r = h.band(A, nb, ib, args.tree, w["variant"])
+        r = h.band(A, nb, ib, args.tree, vcode)
         h.sync()
         ms = h.last_exec_ms()
+        w["variant_used"] = int(r.desc.variant)
         r.free()
         return ms
 
@@ -661,7 +689,7 @@ def main():
     for _ in range(0 if f32 else args.e2e_steps):
         barrier(world)
         t0 = time.perf_counter()
-        G.bidiag_band_host(h.h, m, n, A_host.data_ptr(), m, nb, ib, G.TREES[args.tree], G.VARIANTS[w["variant"]],
+        G.bidiag_band_host(h.h, m, n, A_host.data_ptr(), m, nb, ib, G.TREES[args.tree], vcode,
                            ab_host.data_ptr(), nb + 1)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device) if e2e_t else None
@@ -674,6 +702,7 @@ def main():
     else:
         peak, bound, unit = FP64_PEAK_GFLOPS, "alu", "GFLOP/s"
         peak_src = "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
+    config["variant_used"] = w.get("variant_used")       # the library's code (4 + s: three-step, split s)
     line = dict(base, value=value, ms_per_step=ms_per_step,
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (nb + 1) * n * 8},
