@@ -282,29 +282,37 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
     } else {
       t0 = 0; t1 = (mode == PM_TT) ? min(rows, voff + jj + 1) : rows; alpha_p = &Rt[jj + jj * lrt];
     }
+    // FP64 issues at 2 FMA / clock / SM on this part, so the scalar work of a reflector (sum of the
+    // warp partials, sqrt, divisions) is done once by thread 0 and broadcast, not by every thread.
     double part = 0.0;
     for (int r = t0 + threadIdx.x; r < t1; r += kThreads) {
       const double x = (double)P[r + jj * lp];
       part += x * x;
     }
-    const double sigma2 = block_sum(part, red);
-    const double alpha = (double)*alpha_p;
-    double beta, tau, denom;
-    if (sigma2 == 0.0) {
-      beta = alpha; tau = 0.0; denom = 1.0;
-    } else {
-      const double nrm = sqrt(alpha * alpha + sigma2);
-      beta = alpha < 0.0 ? nrm : -nrm;
-      tau = (beta - alpha) / beta;
-      denom = alpha - beta;
-    }
-    for (int r = t0 + threadIdx.x; r < t1; r += kThreads)
-      P[r + jj * lp] = (tau != 0.0) ? (E)((double)P[r + jj * lp] / denom) : E(0);
+    part = warp_sum(part);
+    if (lane == 0) red[warp] = part;
     __syncthreads();
     if (threadIdx.x == 0) {
+      double sigma2 = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) sigma2 += red[w];
+      const double alpha = (double)*alpha_p;
+      double beta = alpha, tau = 0.0, scale = 0.0;
+      if (sigma2 != 0.0) {
+        const double nrm = sqrt(alpha * alpha + sigma2);
+        beta = alpha < 0.0 ? nrm : -nrm;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
       *alpha_p = (E)beta;
       tau_s[jj] = tau;
+      red[kWarps] = tau;
+      red[kWarps + 1] = scale;
     }
+    __syncthreads();
+    const double tau = red[kWarps], scale = red[kWarps + 1];
+    for (int r = t0 + threadIdx.x; r < t1; r += kThreads) P[r + jj * lp] = (E)((double)P[r + jj * lp] * scale);
+    __syncthreads();
     if (tau != 0.0) {
       const E taue = (E)tau;
       for (int c = jj + 1 + warp; c < kb; c += kWarps) {
