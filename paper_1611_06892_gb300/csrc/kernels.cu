@@ -867,6 +867,8 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
   }
   __syncthreads();
   const int lts = ge ? lp : kb;
+  // per-reflector scalars, computed once by thread 0 (FP64 issues at 2 FMA / clock / SM) and broadcast
+  double* sc = rsc + kWarps;
   for (int k = kb - 1; k >= 0; --k) {
     const double t = tau[k];
     if (t == 0.0) continue;
@@ -879,7 +881,9 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
     const bool row = r < t1;
     const double vbtr = row ? (double)ldg(redb + (size_t)k * nb + r) : 0.0;
     const double v = row ? (double)V[r + k * lp] : 0.0;
-    const double vv = block_sum(v * v, rsc);
+    // A: |v_tail|^2 (warp partials) and, per later column j, v^T M' and v^T G'
+    const double vvp = warp_sum(v * v);
+    if (lane == 0) rsc[warp] = vvp;
     for (int j = k + 1 + warp; j < kb; j += kWarps) {
       double s1 = 0.0, s2 = 0.0;
       for (int rr = t0 + lane; rr < t1; rr += 32) {
@@ -894,25 +898,34 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
         bA[j] = (double)tg[j * lts] + s2;
       }
     }
-    if (threadIdx.x == 0) bA[k] = (double)tg[k * lts];
     __syncthreads();
-    const double om = 1.0 - t * (1.0 + vv);   // a_j = om (v^T M')_j, a_k = om beta (v^T v = 1 + |tail|^2)
-    double tb = tbt[k] - beta * om * bA[k];
-    for (int j = k + 1; j < kb; ++j) tb -= wsA[j] * om * bA[j];
+    if (threadIdx.x == 0) {
+      double vv = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) vv += rsc[w];
+      const double om = 1.0 - t * (1.0 + vv);   // a_j = om (v^T M')_j, a_k = om beta (v^T v = 1 + |tail|^2)
+      bA[k] = (double)tg[k * lts];
+      double tb = tbt[k] - beta * om * bA[k];
+      for (int j = k + 1; j < kb; ++j) tb -= wsA[j] * om * bA[j];
+      sc[0] = om;
+      sc[1] = tb;
+    }
+    __syncthreads();
+    const double om = sc[0];
     double vbar = 0.0;
     if (row) {
       double sG = 0.0, sM = 0.0;
       for (int j = k + 1; j < kb; ++j) {
         const double g = (double)Mg[r + j * lp];
         const double mpre = (double)Ms[r + j * lp] - t * v * wsA[j];
-        sG += g * wsA[j] * om;
+        sG += g * wsA[j];
         sM += mpre * bA[j];
         Ms[r + j * lp] = (E)mpre;
         Mg[r + j * lp] = (E)(g - t * v * bA[j]);
       }
       const double mk = -beta * t * v;
       sM += mk * bA[k];
-      vbar = vbtr - t * (sG + sM);
+      vbar = vbtr - t * (om * sG + sM);
       Ms[r + k * lp] = (E)mk;
       Mg[r + k * lp] = (E)(-t * v * bA[k]);
     }
@@ -920,19 +933,30 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
       const int j = k + threadIdx.x;
       if (j == k) {
         ts[k * lts] = (E)(beta * (1.0 - t));
-        tg[k * lts] = (E)((double)tg[k * lts] - t * bA[k]);
       } else {
         ts[j * lts] = (E)((double)ts[j * lts] - t * wsA[j]);
         tg[j * lts] = (E)((double)tg[j * lts] - t * bA[j]);
       }
     }
-    const double vbv = block_sum(vbar * v, rsc);
-    const double g = -vbv / (beta * t);
-    const double alpha = beta * (1.0 - t);
-    const double abar = -tb / beta - g;
-    const double bbar = tb * alpha / (beta * beta) + g;
-    if (row) Mg[r + k * lp] = (E)((double)Mg[r + k * lp] - vbar / (beta * t) - bbar * t * v);
-    if (threadIdx.x == 0) tg[k * lts] = (E)((double)tg[k * lts] + abar + bbar * alpha / beta);
+    const double vbvp = warp_sum(vbar * v);
+    __syncthreads();                    // everyone has read sc / rsc of this step
+    if (lane == 0) rsc[warp] = vbvp;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double vbv = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) vbv += rsc[w];
+      const double tb = sc[1];
+      const double g = -vbv / (beta * t);
+      const double alpha = beta * (1.0 - t);
+      const double abar = -tb / beta - g;
+      const double bbar = tb * alpha / (beta * beta) + g;
+      tg[k * lts] = (E)((double)tg[k * lts] - t * bA[k] + abar + bbar * alpha / beta);
+      sc[2] = -1.0 / (beta * t);
+      sc[3] = -bbar * t;
+    }
+    __syncthreads();
+    if (row) Mg[r + k * lp] = (E)((double)Mg[r + k * lp] + vbar * sc[2] + sc[3] * v);
     __syncthreads();
   }
   if (ge) {
