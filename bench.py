@@ -71,6 +71,18 @@ def tf32_split_peak_gflops():
     return bf16 * TF32_RATIO * 1e3 / 3.0
 
 
+TABLE1_WEIGHTS = (4, 6, 6, 12, 2, 6, 0)   # GEQRT, UNMQR, TSQRT, TSMQR, TTQRT, TTMQR, COPY in nb^3/3 flops
+
+
+def table1_flops(G, m, n, nb, tree, variant, resources):
+    """Algorithmic flops of the executed task list (Table 1 weights x nb^3 / 3), the roofline's work:
+    it counts what the kernels do (R-BiDiag and three-step do fewer flops than 4mn^2 - 4n^3/3)."""
+    import numpy as np
+    p, q = -(-m // nb), -(-n // nb)
+    tk, _, _ = G.bidiag_plan_tasks(p, q, tree, variant, resources)
+    return float(np.asarray(TABLE1_WEIGHTS)[tk[:, 0]].sum()) * nb ** 3 / 3.0
+
+
 def metric_flops(m, n):
     return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
 
@@ -412,7 +424,8 @@ def run_grad(args, w, base, config, world, rank, local, device, G, torch):
     bwd_ms = statistics.mean(x[1] for x in ms)
     # the adjoint executor's algorithmic work: every update block is undone on the state and on the
     # gradient and contributes its partial products (three times the forward's update flops)
-    bwd_flops = 3.0 * flops
+    alg = table1_flops(G, m, n, nb, G.TREES[tree], G.VARIANTS[w["variant"]], 1)
+    bwd_flops = 3.0 * alg
     achieved = bwd_flops / (bwd_ms * 1e-3) / 1e9
     if f32:
         peak, bound, src = tf32_split_peak_gflops(), "tensor", "measured bf16 x 1.1/2.25 (TF32) / 3"
@@ -423,8 +436,8 @@ def run_grad(args, w, base, config, world, rank, local, device, G, torch):
                      "h2d_bytes_per_step": m * n * A.element_size(), "d2h_bytes_per_step": m * n * A.element_size()},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                           "frac": achieved / peak, "traffic": None,
-                          "kernel": "exec_kernel adjoint instantiation (reverse sweep), 3 x (4mn^2 - 4n^3/3) flops",
-                          "peak_source": src},
+                          "kernel": "exec_kernel adjoint instantiation (reverse sweep), 3 x the forward's Table 1 flops",
+                          "algorithmic_flops": bwd_flops, "peak_source": src},
                 forward_exec_ms=fwd_ms, backward_exec_ms=bwd_ms, backward_over_forward=bwd_ms / fwd_ms,
                 gpu_launches=(7 if w["variant"] == "bidiag" else 8) * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
@@ -499,9 +512,10 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     h2d = sum(m * n for m, n in shapes) * (4 if f32 else 8)
     if not e2e_t:
         d2h = 0
-    cfgs = [G.bidiag_autotune(m, n, torch.cuda.get_device_properties(local).multi_processor_count) for m, n in shapes]
     exec_mean = statistics.mean(exec_ms)
-    achieved = flops / (exec_mean * 1e-3) / 1e9
+    cfgs = [G.bidiag_autotune(m, n, torch.cuda.get_device_properties(local).multi_processor_count) for m, n in shapes]
+    alg = sum(table1_flops(G, m, n, c[0], c[2], c[3], 1) for (m, n), c in zip(shapes, cfgs))
+    achieved = alg / (exec_mean * 1e-3) / 1e9
     if f32:
         peak, bound, src = tf32_split_peak_gflops(), "tensor", "measured bf16 x 1.1/2.25 (TF32) / 3"
     else:
@@ -511,7 +525,8 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                           "frac": achieved / peak, "traffic": None,
-                          "kernel": "exec_kernel (persistent dataflow executor, whole batch)", "peak_source": src},
+                          "kernel": "exec_kernel (persistent dataflow executor, whole batch)",
+                          "algorithmic_flops": alg, "peak_source": src},
                 exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
         with tempfile.TemporaryDirectory() as td:
@@ -695,7 +710,8 @@ def main():
     e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device) if e2e_t else None
 
     exec_mean = statistics.mean(exec_ms)
-    achieved = flops / (exec_mean * 1e-3) / 1e9
+    alg = table1_flops(G, m, n, nb, G.TREES[args.tree], w.get("variant_used", vcode), w["resources"])
+    achieved = alg / (exec_mean * 1e-3) / 1e9
     if f32:
         peak, bound, unit = tf32_split_peak_gflops(), "tensor", "GFLOP/s"
         peak_src = "measured bf16 x 1.1/2.25 (TF32) / 3 products per useful flop"
@@ -708,7 +724,8 @@ def main():
                      "h2d_bytes_per_step": m * n * 8, "d2h_bytes_per_step": (nb + 1) * n * 8},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                           "frac": achieved / peak, "traffic": EXEC_TRAFFIC_BYTES if (not f32 and w["name"] == "square8192" and args.tree == "auto") else None,
-                          "kernel": "exec_kernel (persistent dataflow executor)", "peak_source": peak_src},
+                          "kernel": "exec_kernel (persistent dataflow executor)", "algorithmic_flops": alg,
+                          "peak_source": peak_src},
                 exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
         A_np = A.cpu().numpy()

@@ -274,82 +274,166 @@ template <typename E>
 __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, int lrt, int voff, double* tau_s,
                              double* red) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int jj = 0; jj < kb; ++jj) {
-    int t0, t1;
-    E* alpha_p;
+  double* scale_s = tau_s + 96;          // 1 / (alpha - beta) of each reflector (header scratch)
+  auto tail = [&](int j, int& t0, int& t1) {
     if (mode == PM_GE) {
-      t0 = jj + 1; t1 = rows; alpha_p = &P[jj + jj * lp];
+      t0 = j + 1;
+      t1 = rows;
     } else {
-      t0 = 0; t1 = (mode == PM_TT) ? min(rows, voff + jj + 1) : rows; alpha_p = &Rt[jj + jj * lrt];
+      t0 = 0;
+      t1 = (mode == PM_TT) ? min(rows, voff + j + 1) : rows;
     }
-    // FP64 issues at 2 FMA / clock / SM on this part, so the scalar work of a reflector (sum of the
-    // warp partials, sqrt, divisions) is done once by thread 0 and broadcast, not by every thread.
+  };
+  // beta, tau and the tail scaling 1/(alpha - beta) of column j from its tail's squared norm sigma2, by
+  // one thread (FP64 issues at 2 FMA / clock / SM on this part: the scalar chain is done once, with one
+  // division: inv = 1 / (beta d), d = alpha - beta, scale = beta inv, tau = -d^2 inv = (beta - alpha)/beta).
+  auto scalars = [&](int j, double sigma2) {
+    E* alpha_p = (mode == PM_GE) ? &P[j + j * lp] : &Rt[j + j * lrt];
+    const double alpha = (double)*alpha_p;
+    double beta = alpha, tau = 0.0, scale = 0.0;
+    if (sigma2 != 0.0) {
+      const double nrm = sqrt(alpha * alpha + sigma2);
+      beta = alpha < 0.0 ? nrm : -nrm;
+      const double d = alpha - beta;
+      const double inv = 1.0 / (beta * d);
+      scale = beta * inv;
+      tau = -d * d * inv;
+    }
+    *alpha_p = (E)beta;
+    tau_s[j] = tau;
+    scale_s[j] = scale;
+  };
+  // The tails stay unscaled during the factorization (v = [1; scale x]): applying H_j to column c is
+  // w = c_top + scale (x . c_tail), c_top -= tau w, c_tail -= (tau w scale) x, and the scaling of all
+  // tails is one parallel pass at the end, off the critical chain.  Warp 0 applies H_jj to column jj + 1
+  // and forms reflector jj + 1 (its squared norm accumulated while updating), warps 1..7 update the
+  // later columns: one barrier per column.
+  if (warp == 0) {
+    int t0, t1;
+    tail(0, t0, t1);
     double part = 0.0;
-    for (int r = t0 + threadIdx.x; r < t1; r += kThreads) {
-      const double x = (double)P[r + jj * lp];
+    for (int r = t0 + lane; r < t1; r += 32) {
+      const double x = (double)P[r];
       part += x * x;
     }
     part = warp_sum(part);
-    if (lane == 0) red[warp] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sigma2 = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) sigma2 += red[w];
-      const double alpha = (double)*alpha_p;
-      double beta = alpha, tau = 0.0, scale = 0.0;
-      if (sigma2 != 0.0) {
-        const double nrm = sqrt(alpha * alpha + sigma2);
-        beta = alpha < 0.0 ? nrm : -nrm;
-        tau = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
+    if (lane == 0) scalars(0, part);
+  }
+  __syncthreads();
+  for (int jj = 0; jj < kb; ++jj) {
+    const double tau = tau_s[jj];
+    const E se = (E)scale_s[jj];
+    int t0, t1;
+    tail(jj, t0, t1);
+    if (warp == 0) {
+      if (jj + 1 < kb) {
+        const int c = jj + 1;
+        int n0, n1;                      // tail of reflector c
+        tail(c, n0, n1);
+        double part = 0.0;
+        if (tau != 0.0) {
+          E sum = E(0);
+          for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
+          sum = warp_sum(sum);
+          E* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
+          const E wv = *top + se * sum;
+          __syncwarp();
+          if (lane == 0) *top = *top - (E)tau * wv;
+          const E tw = (E)tau * wv * se;
+          for (int r = t0 + lane; r < t1; r += 32) {
+            const E x = P[r + c * lp] - P[r + jj * lp] * tw;
+            P[r + c * lp] = x;
+            if (r >= n0 && r < n1) part += (double)x * (double)x;
+          }
+        } else {
+          for (int r = t0 + lane; r < t1; r += 32) {
+            const double x = (double)P[r + c * lp];
+            if (r >= n0 && r < n1) part += x * x;
+          }
+        }
+        for (int r = max(n0, t1) + lane; r < n1; r += 32) {   // rows of tail c outside tail jj
+          const double x = (double)P[r + c * lp];
+          part += x * x;
+        }
+        part = warp_sum(part);
+        __syncwarp();
+        if (lane == 0) scalars(c, part);
       }
-      *alpha_p = (E)beta;
-      tau_s[jj] = tau;
-      red[kWarps] = tau;
-      red[kWarps + 1] = scale;
-    }
-    __syncthreads();
-    const double tau = red[kWarps], scale = red[kWarps + 1];
-    for (int r = t0 + threadIdx.x; r < t1; r += kThreads) P[r + jj * lp] = (E)((double)P[r + jj * lp] * scale);
-    __syncthreads();
-    if (tau != 0.0) {
+    } else if (tau != 0.0) {
       const E taue = (E)tau;
-      for (int c = jj + 1 + warp; c < kb; c += kWarps) {
-        E s = E(0);
-        for (int r = t0 + lane; r < t1; r += 32) s += P[r + jj * lp] * P[r + c * lp];
-        s = warp_sum(s);
+      for (int c = jj + 2 + (warp - 1); c < kb; c += kWarps - 1) {
+        E sum = E(0);
+        for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
+        sum = warp_sum(sum);
         E* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
-        const E wv = *top + s;
+        const E wv = *top + se * sum;
         __syncwarp();
         if (lane == 0) *top = *top - taue * wv;
-        const E tw = taue * wv;
+        const E tw = taue * wv * se;
         for (int r = t0 + lane; r < t1; r += 32) P[r + c * lp] -= P[r + jj * lp] * tw;
       }
     }
     __syncthreads();
   }
+  // scale the tails
+  for (int jj = warp; jj < kb; jj += kWarps) {
+    int t0, t1;
+    tail(jj, t0, t1);
+    const double sc = scale_s[jj];
+    for (int r = t0 + lane; r < t1; r += 32) P[r + jj * lp] = (E)((double)P[r + jj * lp] * sc);
+  }
+  __syncthreads();
 }
 
 // T factor (kb x kb, upper) of the kb reflectors in P: T[l,l] = tau_l,
-// T[0:l, l] = -tau_l T[0:l, 0:l] (V[:, 0:l]^T v_l).  G is kb x kb scratch.
+// T[0:l, l] = -tau_l T[0:l, 0:l] (V[:, 0:l]^T v_l).  G is kb x kb scratch.  The Gram entries V^T V are
+// computed in 2 x 2 blocks per thread (no cross-lane reductions); the recurrence uses four independent
+// partial sums per entry.
 template <typename E>
 __device__ void build_t(int mode, const E* P, int lp, int rows, int kb, int voff, const double* tau_s, E* Tb, int ldt,
                         E* G) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int pr = warp; pr < kb * kb; pr += kWarps) {
-    const int a = pr % kb, l = pr / kb;
-    if (a >= l) continue;
-    E s = E(0);
+  // reflector tail values: GE unit lower trapezoid, TS the full tail, TT the tail up to row voff + c
+  auto vval = [&](int r, int c) -> E {
+    if (mode == PM_GE) return r > c ? P[r + c * lp] : (r == c ? E(1) : E(0));
+    if (mode == PM_TT && r > voff + c) return E(0);
+    return P[r + c * lp];
+  };
+  const int nbk = (kb + 1) >> 1;
+  const int nblocks = nbk * (nbk + 1) / 2;      // 2 x 2 blocks (bi <= bj) of the upper triangle
+  for (int u = threadIdx.x; u < nblocks; u += kThreads) {
+    int bj = 0, rem = u;
+    while (rem > bj) { rem -= bj + 1; ++bj; }
+    const int bi = rem;
+    const int a0 = 2 * bi, l0 = 2 * bj;
+    const int a1 = min(a0 + 1, kb - 1), l1 = min(l0 + 1, kb - 1);
+    const int rlo = (mode == PM_GE) ? a0 : 0;
+    const int rhi = (mode == PM_TT) ? min(rows, voff + l1 + 1) : rows;
+    const int rplain = (mode == PM_GE) ? l1 + 1 : (mode == PM_TT ? min(rhi, voff + a0 + 1) : rhi);
+    E s00 = E(0), s01 = E(0), s10 = E(0), s11 = E(0);
+    int r = rlo;
     if (mode == PM_GE) {
-      for (int r = l + 1 + lane; r < rows; r += 32) s += P[r + a * lp] * P[r + l * lp];
-      s = warp_sum(s) + P[l + a * lp];
+      for (; r < min(rplain, rhi); ++r) {
+        const E va0 = vval(r, a0), va1 = vval(r, a1), vl0 = vval(r, l0), vl1 = vval(r, l1);
+        s00 += va0 * vl0; s01 += va0 * vl1; s10 += va1 * vl0; s11 += va1 * vl1;
+      }
+      for (; r < rhi; ++r) {
+        const E va0 = P[r + a0 * lp], va1 = P[r + a1 * lp], vl0 = P[r + l0 * lp], vl1 = P[r + l1 * lp];
+        s00 += va0 * vl0; s01 += va0 * vl1; s10 += va1 * vl0; s11 += va1 * vl1;
+      }
     } else {
-      const int r1 = (mode == PM_TT) ? min(rows, voff + a + 1) : rows;
-      for (int r = lane; r < r1; r += 32) s += P[r + a * lp] * P[r + l * lp];
-      s = warp_sum(s);
+      for (; r < rplain; ++r) {
+        const E va0 = P[r + a0 * lp], va1 = P[r + a1 * lp], vl0 = P[r + l0 * lp], vl1 = P[r + l1 * lp];
+        s00 += va0 * vl0; s01 += va0 * vl1; s10 += va1 * vl0; s11 += va1 * vl1;
+      }
+      for (; r < rhi; ++r) {
+        const E va0 = vval(r, a0), va1 = vval(r, a1), vl0 = vval(r, l0), vl1 = vval(r, l1);
+        s00 += va0 * vl0; s01 += va0 * vl1; s10 += va1 * vl0; s11 += va1 * vl1;
+      }
     }
-    if (lane == 0) G[a + l * kb] = s;
+    if (a0 < l0) G[a0 + l0 * kb] = s00;
+    if (a0 < l1 && l1 != l0) G[a0 + l1 * kb] = s01;
+    if (a1 < l0 && a1 != a0) G[a1 + l0 * kb] = s10;
+    if (a1 < l1 && a1 != a0 && l1 != l0) G[a1 + l1 * kb] = s11;
   }
   __syncthreads();
   for (int l = 0; l < kb; ++l) {
@@ -358,9 +442,16 @@ __device__ void build_t(int mode, const E* P, int lp, int rows, int kb, int voff
       if (a == l) {
         v = (E)tau_s[l];
       } else if (a < l) {
-        E s = E(0);
-        for (int t = a; t < l; ++t) s += Tb[a + t * ldt] * G[t + l * kb];
-        v = -(E)tau_s[l] * s;
+        E p0 = E(0), p1 = E(0), p2 = E(0), p3 = E(0);
+        int t = a;
+        for (; t + 3 < l; t += 4) {
+          p0 += Tb[a + t * ldt] * G[t + l * kb];
+          p1 += Tb[a + (t + 1) * ldt] * G[t + 1 + l * kb];
+          p2 += Tb[a + (t + 2) * ldt] * G[t + 2 + l * kb];
+          p3 += Tb[a + (t + 3) * ldt] * G[t + 3 + l * kb];
+        }
+        for (; t < l; ++t) p0 += Tb[a + t * ldt] * G[t + l * kb];
+        v = -(E)tau_s[l] * ((p0 + p1) + (p2 + p3));
       }
       Tb[a + l * ldt] = v;
     }
