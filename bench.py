@@ -163,8 +163,10 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        # NCCL between GPUs; gloo when there is no GPU (the multi-process CPU tests)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
 
 
@@ -572,7 +574,7 @@ def main():
     ap.add_argument("--cpu-sample-batch", default=None)
     ap.add_argument("--cpu-sample-grad", default=None)
     ap.add_argument("--auto-resources", type=int, default=None,
-                    help="R of the Auto tree (default: SMs * 32 / nb, as the library chooses)")
+                    help="R of the Auto tree (default: SMs * 32 / nb, twice that for FP32 storage, as the library chooses)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload], name=args.workload)
     if args.variant:
@@ -596,10 +598,15 @@ def main():
     import numpy as np
     import torch
 
-    torch.cuda.set_device(local)
-    device = f"cuda:{local}"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+        device = f"cuda:{local}"
+    else:
+        device = "cpu"          # only the reference (oracle) arm runs without a GPU
     if w["resources"] is None and w["nb"]:
-        w["resources"] = max(1, torch.cuda.get_device_properties(local).multi_processor_count * 32 // w["nb"])
+        # the library's default R of the Auto tree: SMs x strip width / nb, twice that for FP32 storage
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count if torch.cuda.is_available() else 152
+        w["resources"] = max(1, nsm * 32 * (2 if args.precision == "f32" else 1) // w["nb"])
     m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
     flops = metric_flops(m, n)
     f32 = args.precision == "f32"
@@ -639,6 +646,8 @@ def main():
         del A
         torch.cuda.empty_cache()
         per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+        if args.cpu_seconds != CPU_SAMPLE_SECONDS:
+            per_step = args.cpu_seconds
         res = [run_cpu_sample_subprocess(A_host, w, args.tree, per_step) for _ in range(args.warmup + args.steps)]
         timed = res[args.warmup:]
         val = sum(r["flops"] for r in timed) / sum(r["seconds"] for r in timed) / 1e12

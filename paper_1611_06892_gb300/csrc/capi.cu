@@ -147,10 +147,13 @@ int upload_program(bidiag_handle h, PlanDev& pd, const std::vector<bd::DevTask>&
 
 // Resources R of the Auto tree (Sec. 5 "nbcores"): the number of workers that each take one tile
 // task.  A tile update is spread over nb / w SMs (one column strip each), so the default is
-// SMs * w / nb; BIDIAG_OPT_AUTO_RESOURCES overrides it.
-int64_t resources_of(bidiag_handle h, int nb, int w) {
+// SMs * w / nb for FP64 storage.  With FP32 storage the updates are about ten times faster while the
+// panels are not, so more, smaller groups (twice the R) pay: 8192^2 takes 190 ms with 2 SMs w / nb
+// against 232 ms with SMs w / nb (FP64: 1398 vs 1386 ms, and 4096^2 prefers the smaller R).
+// BIDIAG_OPT_AUTO_RESOURCES overrides it.
+int64_t resources_of(bidiag_handle h, int nb, int w, int esize) {
   if (h->auto_res > 0) return h->auto_res;
-  return std::max<int64_t>(1, (int64_t)h->nsm * w / nb);
+  return std::max<int64_t>(1, (int64_t)h->nsm * w * (esize == 4 ? 2 : 1) / nb);
 }
 
 // Executor launch of a program held in pd with the given buffers.
@@ -215,9 +218,9 @@ int choose_strip(bidiag_handle h, int nb, int ib, int esize, int* w) {
   return fail(h, BIDIAG_ERR_UNSUPPORTED, "tile size / inner blocking need more shared memory than the device has");
 }
 
-int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int w,
+int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int w, int esize,
              std::shared_ptr<PlanDev>* out) {
-  const int64_t R = resources_of(h, nb, w);
+  const int64_t R = resources_of(h, nb, w, esize);
   const bool debug = h->debug_unset != 0;
   PlanKey key{m, n, nb, ib, tree, variant, R, w};
   if (!debug) {
@@ -396,7 +399,7 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   if (rc) return rc;
   if (variant == BIDIAG_AUTO_VARIANT || variant == BIDIAG_THREESTEP) {
     const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
-    const int64_t R = resources_of(h, nb, w);
+    const int64_t R = resources_of(h, nb, w, (int)sizeof(E));
     try {
       if (variant == BIDIAG_AUTO_VARIANT) {
         variant = bd::choose_variant(p, q, tree, R, nullptr, nullptr);
@@ -413,7 +416,7 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   }
   if (variant == BIDIAG_THREESTEP_SPLIT(0)) variant = BIDIAG_RBIDIAG;   // the same task list
   std::shared_ptr<PlanDev> pd;
-  rc = get_plan(h, m, n, nb, ib, tree, variant, w, &pd);
+  rc = get_plan(h, m, n, nb, ib, tree, variant, w, (int)sizeof(E), &pd);
   if (rc) return rc;
   bidiag_result* r = new (std::nothrow) bidiag_result();
   if (!r) return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed");
@@ -650,7 +653,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
             continue;
           }
           const int p = (int)((m[b] + o.nb - 1) / o.nb), q = (int)((n[b] + o.nb - 1) / o.nb);
-          const int64_t R = resources_of(h, o.nb, o.w);
+          const int64_t R = resources_of(h, o.nb, o.w, esize);
           if (o.variant == BIDIAG_AUTO_VARIANT) o.variant = bd::choose_variant(p, q, o.tree, R, nullptr, nullptr);
           o.pd = std::make_shared<PlanDev>();
           bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w);
