@@ -254,3 +254,22 @@ def test_adjoint_parity_three_step(handle, torch_mod, case, tree):
     assert np.abs(Ab_g.cpu().numpy() - Ab_o).max() <= TOL * max(1.0, np.abs(Ab_o).max())
     assert np.abs(Arec.cpu().numpy() - A).max() <= 1e-12 * max(1.0, np.linalg.norm(A))
     res_g.free()
+
+
+@pytest.mark.parametrize("case", [(1, 1, 4, 2), (3, 1, 8, 4), (7, 7, 8, 8), (33, 32, 32, 32), (9, 2, 4, 4),
+                                  (17, 16, 4, 1)], ids=lambda c: "x".join(map(str, c)))
+@pytest.mark.parametrize("tree", ("flatts", "greedy", "auto"))
+@pytest.mark.parametrize("variant", ("bidiag", "rbidiag"))
+def test_adjoint_edge_sizes(handle, torch_mod, case, tree, variant):
+    torch = torch_mod
+    m, n, nb, ib = case
+    A = inputs.gaussian(m, n, seed=m * 13 + n)
+    W = inputs.gaussian(nb + 1, n, seed=m + 7 * n)
+    res_o = OB.bidiag_band(A, nb, ib, TREES[tree], G.VARIANTS[variant], resources=R_AUTO)
+    Ab_o, _ = AD.band_vjp(res_o, W)
+    res_g = handle.band(dev(torch, A), nb, ib, tree, variant)
+    Ab_g, Arec = res_g.backward(dev(torch, W), reconstruct=True)
+    handle.sync()
+    assert np.abs(Ab_g.cpu().numpy() - Ab_o).max() <= TOL * max(1.0, np.abs(Ab_o).max())
+    assert np.abs(Arec.cpu().numpy() - A).max() <= 1e-12 * max(1.0, np.linalg.norm(A))
+    res_g.free()

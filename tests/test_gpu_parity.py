@@ -243,3 +243,22 @@ def test_three_step_best_split(handle, torch_mod):
     res_o = OB.bidiag_band(A, nb, ib, T.GREEDY, T.THREESTEP + s, resources=R_AUTO)
     compare(res_g, res_o, A, nb, ib)
     res_g.free()
+
+
+EDGE_CASES = [
+    # m, n, nb, ib: a 1 x 1 matrix, one row of tiles narrower than the tile, a tile larger than the
+    # matrix, one extra row past a tile boundary, two columns
+    (1, 1, 4, 2), (3, 1, 8, 4), (7, 7, 8, 8), (33, 32, 32, 32), (9, 2, 4, 4), (17, 16, 4, 1),
+]
+
+
+@pytest.mark.parametrize("case", EDGE_CASES, ids=lambda c: "x".join(map(str, c)))
+@pytest.mark.parametrize("tree", list(TREES), ids=list(TREES))
+@pytest.mark.parametrize("variant", ("bidiag", "rbidiag"))
+def test_parity_edge_sizes(handle, torch_mod, case, tree, variant):
+    m, n, nb, ib = case
+    A = inputs.gaussian(m, n, seed=m * 11 + n)
+    res_o = OB.bidiag_band(A, nb, ib, TREES[tree], G.VARIANTS[variant], resources=R_AUTO)
+    res_g = gpu_reduce(handle, torch_mod, A, nb, ib, tree, variant)
+    compare(res_g, res_o, A, nb, ib)
+    res_g.free()
