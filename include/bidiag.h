@@ -332,12 +332,15 @@ int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int vari
  * forward result, a / c = state tiles of the m x n grid, flags = partial slot), fwd[y] = the forward
  * queue position it undoes, *ndeps dependency indices, *nslot_off slot offsets (the last one is the
  * total number of elements) and *npinfo = 4 per panel task (first update slot, number of update
- * slots, first panel-update slot, 0).  Arrays are filled only when their capacity suffices.  Errors as
- * bidiag_plan_program, -10 for a NULL count pointer. */
+ * slots, first panel-update slot, 0), and *strip_w_used = the column width of its update strips (half
+ * the forward's when that is at least 16: each forward strip is undone as two sub-tasks).  Arrays are
+ * filled only when their capacity suffices.  Errors as bidiag_plan_program, -10 for a NULL count
+ * pointer. */
 int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
                          int strip_w, int32_t* program, int32_t* fwd, int64_t cap, int64_t* count,
                          int32_t* deps, int64_t dcap, int64_t* ndeps, int64_t* slot_off, int64_t scap,
-                         int64_t* nslot_off, int32_t* pinfo, int64_t pcap, int64_t* npinfo);
+                         int64_t* nslot_off, int32_t* pinfo, int64_t pcap, int64_t* npinfo,
+                         int32_t* strip_w_used);
 
 #ifdef __cplusplus
 }

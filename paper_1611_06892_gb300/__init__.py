@@ -94,7 +94,7 @@ def load_library(path=LIB_PATH):
         "bidiag_plan_program": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), i64, P(i64), P(i32),
                                        i64, P(i64), P(i32)]),
         "bidiag_plan_backward": (cint, [i64, i64, cint, cint, cint, cint, i64, cint, P(i32), P(i32), i64, P(i64),
-                                        P(i32), i64, P(i64), P(i64), i64, P(i64), P(i32), i64, P(i64)]),
+                                        P(i32), i64, P(i64), P(i64), i64, P(i64), P(i32), i64, P(i64), P(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,14 +253,15 @@ def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
 
 def bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
     """Adjoint program of a reduction: (sub-tasks (count x 8), forward position of each, dependency
-    array, slot offsets, per-panel slot table (npanels x 4))."""
+    array, slot offsets, per-panel slot table (npanels x 4), column width of its update strips)."""
     lib = load_library()
     cnt, nd, ns, npi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    wb = ctypes.c_int32()
     I32 = ctypes.POINTER(ctypes.c_int32)
     I64 = ctypes.POINTER(ctypes.c_int64)
     args = (m, n, nb, ib, tree, variant, resources, strip_w)
     _check(None, lib.bidiag_plan_backward(*args, None, None, 0, ctypes.byref(cnt), None, 0, ctypes.byref(nd), None, 0,
-                                          ctypes.byref(ns), None, 0, ctypes.byref(npi)))
+                                          ctypes.byref(ns), None, 0, ctypes.byref(npi), ctypes.byref(wb)))
     prog = np.zeros((max(cnt.value, 1), 8), dtype=np.int32)
     fwd = np.zeros(max(cnt.value, 1), dtype=np.int32)
     deps = np.zeros(max(nd.value, 1), dtype=np.int32)
@@ -269,9 +270,9 @@ def bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
     _check(None, lib.bidiag_plan_backward(*args, prog.ctypes.data_as(I32), fwd.ctypes.data_as(I32), cnt.value,
                                           ctypes.byref(cnt), deps.ctypes.data_as(I32), nd.value, ctypes.byref(nd),
                                           slot.ctypes.data_as(I64), ns.value, ctypes.byref(ns),
-                                          pinfo.ctypes.data_as(I32), npi.value, ctypes.byref(npi)))
+                                          pinfo.ctypes.data_as(I32), npi.value, ctypes.byref(npi), ctypes.byref(wb)))
     return (prog[:cnt.value], fwd[:cnt.value], deps[:nd.value], slot[:ns.value],
-            pinfo[:npi.value].reshape(-1, 4))
+            pinfo[:npi.value].reshape(-1, 4), wb.value)
 
 
 # ---- torch-facing wrappers ---------------------------------------------------------------------

@@ -26,7 +26,7 @@ struct BwdDev;
 
 struct PlanDev {
   bd::Plan plan;
-  std::shared_ptr<BwdDev> bwd;   // adjoint program of this plan, built on first use
+  std::shared_ptr<BwdDev> bwd[2];   // adjoint program of this plan (FP64, FP32 storage), built on first use
   bd::DevTask* d_tasks = nullptr;
   int32_t* d_deps = nullptr;
   int* d_done = nullptr;
@@ -501,12 +501,11 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
   CK(h, cudaSetDevice(h->device));
   const bd::Plan& pl = r->pd->plan;
   const int nb = r->nb, ib = r->ib, esize = (int)sizeof(E);
-  const int hw = bd::choose_bwd_chunk(nb, ib, pl.strip_w, h->smem_optin, esize);
-  if (!hw) return fail(h, BIDIAG_ERR_UNSUPPORTED, "the adjoint of this tile size / inner blocking needs more shared memory");
-  if (!r->pd->bwd) {
+  const int bi = esize == 8 ? 0 : 1;
+  if (!r->pd->bwd[bi]) {
     auto bw = std::make_shared<BwdDev>();
     try {
-      bd::build_backward(pl, bw->bp);
+      bd::build_backward(pl, bw->bp, esize == 8);
     } catch (const std::bad_alloc&) {
       return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning the adjoint");
     } catch (const std::exception& e) {
@@ -519,9 +518,11 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
     CK(h, cudaMemcpy(bw->d_slot_off, bw->bp.slot_off.data(), bw->bp.slot_off.size() * sizeof(int64_t),
                      cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(bw->d_pinfo, bw->bp.pinfo.data(), bw->bp.pinfo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    r->pd->bwd = bw;
+    r->pd->bwd[bi] = bw;
   }
-  const BwdDev& bw = *r->pd->bwd;
+  const BwdDev& bw = *r->pd->bwd[bi];
+  const int hw = bd::choose_bwd_chunk(nb, ib, bw.bp.strip_w, h->smem_optin, esize);
+  if (!hw) return fail(h, BIDIAG_ERR_UNSUPPORTED, "the adjoint of this tile size / inner blocking needs more shared memory");
   // Working state and gradient, tiled like the forward's buffers: S / G mirror the A tiles (p x q);
   // for R-BiDiag, S2 / G2 mirror the R copy (q x q).  Start: the band lives in the last buffer the
   // forward wrote (A tiles for BiDiag, the R copy for R-BiDiag); for R-BiDiag the A tiles' state is the
@@ -583,7 +584,7 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
   const void* bx[3] = {S2, G, G2};
   const int64_t nx[3] = {ntiles2, ntiles, ntiles2};
   rc = run_exec(h, bw.prog, (int)bw.bp.dev.size(), r->tiles, ntiles, r->tiles2, ntiles2, S, ntiles, r->T, pl.npanels,
-                nb, ib, pl.strip_w, esize, timed, nullptr, 0, 0, bx, nx, &bp);
+                nb, ib, bw.bp.strip_w, esize, timed, nullptr, 0, 0, bx, nx, &bp);
   h->timed = timed;
   if (rc) {
     release();
@@ -1214,7 +1215,7 @@ int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int vari
 int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources, int strip_w,
                          int32_t* program, int32_t* fwd, int64_t cap, int64_t* count, int32_t* deps, int64_t dcap,
                          int64_t* ndeps, int64_t* slot_off, int64_t scap, int64_t* nslot_off, int32_t* pinfo,
-                         int64_t pcap, int64_t* npinfo) {
+                         int64_t pcap, int64_t* npinfo, int32_t* strip_w_used) {
   if (m < 1 || n < 1 || m < n) return -1;
   if (nb < 1 || nb > bd::kMaxNb) return -3;
   if (ib < 1 || nb % ib) return -4;
@@ -1233,6 +1234,7 @@ int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int var
     *ndeps = (int64_t)bp.deps.size();
     *nslot_off = (int64_t)bp.slot_off.size();
     *npinfo = (int64_t)bp.pinfo.size();
+    if (strip_w_used) *strip_w_used = bp.strip_w;
     if (program && cap >= *count) std::memcpy(program, bp.dev.data(), bp.dev.size() * sizeof(bd::DevTask));
     if (fwd && cap >= *count) std::memcpy(fwd, bp.fwd.data(), bp.fwd.size() * sizeof(int32_t));
     if (deps && dcap >= *ndeps) std::memcpy(deps, bp.deps.data(), bp.deps.size() * sizeof(int32_t));

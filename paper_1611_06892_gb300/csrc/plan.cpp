@@ -706,22 +706,34 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
 // Slot layout: an update strip's slot holds, for every block beta, a nb x ib block (rows of the
 // reflector tails) then an ib x ib block per beta; a PU slot holds the two blocks of its one block.
 // ---------------------------------------------------------------------------------------------
-void build_backward(const Plan& pl, BwdPlan& bp) {
+void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
   const int nb = pl.nb, ib = pl.ib, nblk = nb / ib;
   const int32_t nsub = (int32_t)pl.dev.size();
+  // An update strip's adjoint has three times its flops; with split_strips it is undone as two column
+  // halves (each with its own partial slot) when the strip is at least 16 wide, which halves its
+  // latency on the critical path.
+  const int w = pl.strip_w, split = (split_strips && w >= 16 && w % 2 == 0) ? 2 : 1, wb = w / split;
+  bp.strip_w = wb;
   auto state_ref = [&](int32_t ref) -> int32_t {   // forward buffer 0 / 1 -> state buffer 2 / 3
     if (ref < 0) return -1;
     const int buf = (int)((uint32_t)ref >> 28);
     return tile_ref(buf + 2, ref & 0x0fffffff);
   };
-  // slots: per panel task, its update strips first (in program order), then its PU sub-tasks
+  auto is_upd = [](int type) { return type == UNMQR || type == TSMQR || type == TTMQR; };
+  auto pieces = [&](const DevTask& f) {   // adjoint strips of a forward update strip
+    const int strip = (f.op >> 8) & 0xff;
+    int n = 0;
+    for (int h = 0; h < split; ++h)
+      if ((int64_t)(strip * split + h) * wb < nb) ++n;
+    return n;
+  };
+  // slots: per panel task, its adjoint update strips first (in program order), then its PU sub-tasks
   const int npu = nblk * (nblk - 1) / 2;
   std::vector<int32_t> nupd(std::max(1, pl.npanels), 0);
   for (const DevTask& f : pl.dev) {
-    const int type = f.op & 15;
-    if (type == UNMQR || type == TSMQR || type == TTMQR) {
+    if (is_upd(f.op & 15)) {
       if (f.tslot < 0 || f.tslot >= pl.npanels) throw std::logic_error("update without a panel");
-      ++nupd[f.tslot];
+      nupd[f.tslot] += pieces(f);
     }
   }
   bp.pinfo.assign((size_t)4 * std::max(1, pl.npanels), 0);
@@ -746,10 +758,14 @@ void build_backward(const Plan& pl, BwdPlan& bp) {
   std::vector<int32_t> next_upd(std::max(1, pl.npanels), 0);
   auto pu_index = [&](int b, int s) { return b * nblk - b * (b + 1) / 2 + (s - b - 1); };
 
-  std::vector<DevTask> sub(nsub);
-  std::vector<int64_t> wt(nsub, 1);
-  const int64_t ib2 = (int64_t)ib * ib, w = pl.strip_w;
+  // adjoint nodes: one per forward sub-task, `split` per forward update strip
+  std::vector<DevTask> sub;
+  std::vector<int64_t> wt;
+  std::vector<int32_t> fwd_of;
+  std::vector<int32_t> first(nsub + 1, 0);
+  const int64_t ib2 = (int64_t)ib * ib;
   for (int32_t y = 0; y < nsub; ++y) {
+    first[y] = (int32_t)sub.size();
     const DevTask& f = pl.dev[y];
     const int type = f.op & 15, tr = (f.op >> 4) & 1, strip = (f.op >> 8) & 0xff, blk = (f.op >> 16) & 0xff;
     const int kind = (f.op >> 24) & 3;
@@ -763,49 +779,69 @@ void build_backward(const Plan& pl, BwdPlan& bp) {
       const int64_t rows = kind == PK_GE ? nb - (int64_t)blk * ib : (kind == PK_TS ? nb : (int64_t)(blk + 1) * ib);
       if (type == PF) {
         d.op = make_op(BPF, tr, false, 0, blk, kind);
-        wt[y] = 10 * ib2 * rows;
+        wt.push_back(10 * ib2 * rows);
       } else {
         d.op = make_op(BPU, tr, false, strip, blk, kind);
         d.flags = bp.pinfo[4 * f.tslot + 2] + pu_index(blk, strip);
-        wt[y] = 14 * ib2 * rows;
+        wt.push_back(14 * ib2 * rows);
       }
-    } else if (type == UNMQR || type == TSMQR || type == TTMQR) {
+      sub.push_back(d);
+      fwd_of.push_back(y);
+    } else if (is_upd(type)) {
       d.a = state_ref(f.a);
       d.c = state_ref(f.c);
       const int uk = type == UNMQR ? 0 : (type == TSMQR ? 1 : 2);
-      d.op = make_op(BUPD, tr, false, strip, 0, uk);
-      d.flags = bp.pinfo[4 * f.tslot + 0] + next_upd[f.tslot]++;
-      wt[y] = 3 * (type == TSMQR ? 4 : 2) * (int64_t)nb * nb * w;
+      for (int h = 0; h < split; ++h) {
+        const int sb = strip * split + h;
+        if ((int64_t)sb * wb >= nb) continue;
+        if (sb > 255) throw std::invalid_argument("too many adjoint strips");
+        DevTask e = d;
+        e.op = make_op(BUPD, tr, false, sb, 0, uk);
+        e.flags = bp.pinfo[4 * f.tslot + 0] + next_upd[f.tslot]++;
+        sub.push_back(e);
+        wt.push_back(3 * (type == TSMQR ? 4 : 2) * (int64_t)nb * nb * wb);
+        fwd_of.push_back(y);
+      }
     } else {
       d.x = state_ref(f.x);
       d.a = -1;
       d.c = state_ref(f.c);
       d.flags = f.flags & 1;
       d.op = make_op(BCOPY, false, false, 0, 0, 0);
-      wt[y] = (int64_t)nb * nb;
+      wt.push_back((int64_t)nb * nb);
+      sub.push_back(d);
+      fwd_of.push_back(y);
     }
-    sub[y] = d;
   }
-  // reversed DAG: forward y depends on d  ->  adjoint d depends on adjoint y
-  std::vector<std::vector<int32_t>> rdeps(nsub);
+  first[nsub] = (int32_t)sub.size();
+  const int32_t nnode = (int32_t)sub.size();
+  // reversed DAG: forward y depends on d  ->  every adjoint node of d depends on every node of y
+  std::vector<std::vector<int32_t>> rdeps(nnode);
   for (int32_t y = 0; y < nsub; ++y)
-    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) rdeps[pl.deps[k]].push_back(y);
-  // bottom levels of the reversed DAG (its successors of y are y's forward dependencies)
-  std::vector<int64_t> bottom(nsub, 0);
+    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) {
+      const int32_t d = pl.deps[k];
+      for (int32_t a = first[d]; a < first[d + 1]; ++a)
+        for (int32_t b = first[y]; b < first[y + 1]; ++b) rdeps[a].push_back(b);
+    }
+  // bottom levels of the reversed DAG (the successors of y's nodes are the nodes of y's dependencies)
+  std::vector<int64_t> bottom(nnode, 0);
   for (int32_t y = 0; y < nsub; ++y) {
     int64_t mx = 0;
-    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) mx = std::max(mx, bottom[pl.deps[k]]);
-    bottom[y] = wt[y] + mx;
+    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) {
+      const int32_t d = pl.deps[k];
+      for (int32_t a = first[d]; a < first[d + 1]; ++a) mx = std::max(mx, bottom[a]);
+    }
+    for (int32_t b = first[y]; b < first[y + 1]; ++b) bottom[b] = wt[b] + mx;
   }
-  std::vector<int32_t> order(nsub);
-  for (int32_t y = 0; y < nsub; ++y) order[y] = nsub - 1 - y;
+  std::vector<int32_t> order(nnode);
+  for (int32_t z = 0; z < nnode; ++z) order[z] = nnode - 1 - z;
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return bottom[a] > bottom[b]; });
-  std::vector<int32_t> pos(nsub);
-  for (int32_t y = 0; y < nsub; ++y) pos[order[y]] = y;
-  bp.dev.resize(nsub);
-  bp.fwd = order;
+  std::vector<int32_t> pos(nnode);
+  for (int32_t z = 0; z < nnode; ++z) pos[order[z]] = z;
+  bp.dev.resize(nnode);
+  bp.fwd.resize(nnode);
   bp.deps.clear();
-  for (int32_t z = 0; z < nsub; ++z) {
+  for (int32_t z = 0; z < nnode; ++z) {
     const int32_t y = order[z];
     DevTask e = sub[y];
     e.dep_begin = (int32_t)bp.deps.size();
@@ -815,6 +851,7 @@ void build_backward(const Plan& pl, BwdPlan& bp) {
     }
     e.dep_end = (int32_t)bp.deps.size();
     bp.dev[z] = e;
+    bp.fwd[z] = fwd_of[y];
   }
 }
 

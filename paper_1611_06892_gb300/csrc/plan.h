@@ -84,8 +84,11 @@ struct BwdPlan {
   std::vector<int64_t> slot_off;   // element offset of each partial slot; last entry = total elements
   std::vector<int32_t> pinfo;      // per panel task (T slot): first update slot, number, first PU slot, 0
   std::vector<int32_t> fwd;        // forward queue position of each adjoint sub-task
+  int strip_w = 0;                 // column width of the adjoint update strips
 };
-void build_backward(const Plan& pl, BwdPlan& bp);
+// split_strips: undo each update strip of >= 16 columns as two column halves (shorter critical path;
+// worth it when the arithmetic dominates, FP64, not with FP32 storage).
+void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips = true);
 
 // Trees and task lists (independent of any device state).
 std::vector<Elim> make_eliminations(int p, int q, int tree, int variant, int64_t resources);

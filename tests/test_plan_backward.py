@@ -72,11 +72,24 @@ def state_footprint(f, nb, ib, w):
 
 def check_backward(m, n, nb, ib, tree, variant, strip_w):
     fprog, fdeps, w = G.bidiag_plan_program(m, n, nb, ib, tree, variant, resources=2, strip_w=strip_w)
-    prog, fwd, deps, slot_off, pinfo = G.bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=2,
-                                                              strip_w=strip_w)
+    prog, fwd, deps, slot_off, pinfo, wb = G.bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=2,
+                                                                  strip_w=strip_w)
     nsub = len(prog)
     nblk = nb // ib
-    assert nsub == len(fprog) and sorted(fwd.tolist()) == list(range(nsub))
+    # every forward sub-task is undone: once, or (update strips) by column pieces of width wb that
+    # tile its columns exactly
+    assert set(fwd.tolist()) == set(range(len(fprog)))
+    split = w // wb
+    assert split in (1, 2) and wb * split == w
+    for y in range(len(fprog)):
+        ys = [z for z in range(nsub) if fwd[z] == y]
+        g = fields(fprog[y])
+        if g["typ"] in (UNMQR, TSMQR, TTMQR):
+            cols = sorted(fields(prog[z])["strip"] for z in ys)
+            want = [g["strip"] * split + hh for hh in range(split) if (g["strip"] * split + hh) * wb < nb]
+            assert cols == want
+        else:
+            assert len(ys) == 1
     # kinds match the forward sub-tasks they undo
     kind_map = {PF: BPF, PU: BPU, UNMQR: BUPD, TSMQR: BUPD, TTMQR: BUPD, COPY: BCOPY}
     for y in range(nsub):
@@ -86,7 +99,7 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
             assert (f["blk"], f["kind"], f["tslot"], f["x"]) == (g["blk"], g["kind"], g["tslot"], g["x"])
             assert f["c"] == g["x"] + (2 << 28) and f["a"] == (g["a"] + (2 << 28) if g["a"] >= 0 else -1)
         if f["typ"] == BUPD:
-            assert f["kind"] == {UNMQR: 0, TSMQR: 1, TTMQR: 2}[g["typ"]] and f["strip"] == g["strip"]
+            assert f["kind"] == {UNMQR: 0, TSMQR: 1, TTMQR: 2}[g["typ"]] and f["strip"] // split == g["strip"]
     # ancestors in the adjoint DAG
     anc = [0] * nsub
     for y in range(nsub):
@@ -99,7 +112,7 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
     # state / gradient: conflicts ordered in reverse forward order
     touch = {}
     for y in range(nsub):
-        for e in state_footprint(fields(prog[y]), nb, ib, w):
+        for e in state_footprint(fields(prog[y]), nb, ib, wb):
             touch.setdefault(e, []).append(y)
     for e, ys in touch.items():
         ys = sorted(ys, key=lambda y: -fwd[y])        # the order the reverse sweep must follow
@@ -140,6 +153,8 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
 def test_adjoint_program_order(tree, variant):
     # 3 x 3 ragged tiles, nb = 8, two inner blocks, strips of 4 columns
     assert check_backward(22, 20, 8, 4, tree, variant, strip_w=4) > 0
+    # nb = 32 with strips of 16 columns: undone as two 8-column halves each, the last tile ragged
+    assert check_backward(70, 40, 32, 8, tree, variant, strip_w=16) > 0
     # 5 x 2 tiles, inner block = tile
     assert check_backward(20, 8, 4, 4, tree, variant, strip_w=32) > 0
     # three inner blocks per tile, strips of two blocks
@@ -151,11 +166,11 @@ def test_checker_catches_a_reversed_edge(monkeypatch):
     real = G.bidiag_plan_backward
 
     def broken(*args, **kw):
-        prog, fwd, deps, slot_off, pinfo = real(*args, **kw)
+        prog, fwd, deps, slot_off, pinfo, wb = real(*args, **kw)
         prog = prog.copy()
         y = [i for i in range(len(prog)) if (prog[i, 0] & 15) == BPF and prog[i, 6] > prog[i, 5]][-1]
         prog[y, 6] = prog[y, 5]
-        return prog, fwd, deps, slot_off, pinfo
+        return prog, fwd, deps, slot_off, pinfo, wb
 
     monkeypatch.setattr(G, "bidiag_plan_backward", broken)
     with pytest.raises(AssertionError):
