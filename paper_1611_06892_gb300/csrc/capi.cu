@@ -53,16 +53,35 @@ struct BwdDev {
 
 using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int>;
 
+// Everything about a batch that depends only on its shapes and options: per-matrix configurations and
+// plans, the storage layout and the merged device program (cached on the handle, reused by later calls
+// with the same shapes).
+struct BatchPlan {
+  struct One {
+    int nb, ib, tree, variant, w;
+    std::shared_ptr<PlanDev> pd;
+  };
+  std::vector<One> mats;
+  std::vector<bd::MatInfo> info;
+  int64_t tot0 = 0, tot1 = 0, totT = 0, tiles_all = 0, cols_all = 0;
+  size_t smem = 0;
+  int ntasks = 0;
+  PlanDev prog;                 // the merged device program
+  void* d_mats = nullptr;       // info on the device
+  ~BatchPlan() {
+    if (d_mats) cudaFree(d_mats);
+  }
+};
+
 // Device storage shared by the results of one batched reduction (freed with the last of them).
 struct BatchStore {
   void* tiles = nullptr;
   void* tiles2 = nullptr;
   void* T = nullptr;
-  void* d_mats = nullptr;
   void* d_desc = nullptr;
-  PlanDev prog;          // the merged device program
+  std::shared_ptr<BatchPlan> plan;   // keeps the program alive while results exist
   ~BatchStore() {
-    for (void* p : {tiles, tiles2, T, d_mats, d_desc})
+    for (void* p : {tiles, tiles2, T, d_desc})
       if (p) cudaFree(p);
   }
 };
@@ -89,6 +108,7 @@ struct bidiag_ctx {
   int f32_simt = 0;                // FP32 storage: updates by FFMA instead of 3xTF32 tensor-core products
   int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
   std::map<std::tuple<int, int, int, int64_t>, int> splits;   // best three-step split per (p, q, tree, R)
+  std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> batches;   // batch programs by shapes / options
   int64_t trace_cap = 0, trace_len = 0;
 };
 
@@ -611,16 +631,35 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
   if (!out) return fail(h, -11, "out is NULL");
   CK(h, cudaSetDevice(h->device));
   const int esize = (int)sizeof(E);
-  struct One {
-    int nb, ib, tree, variant, w;
-    std::shared_ptr<PlanDev> pd;
-  };
-  std::vector<One> mats((size_t)count);
   for (int64_t b = 0; b < count; ++b) {
     out[b] = nullptr;
     if (m[b] < 1 || n[b] < 1 || m[b] < n[b] || lda[b] < m[b] || !d_A[b])
       return fail(h, -3, "matrix " + std::to_string(b) + ": need m >= n >= 1, lda >= m and A != NULL");
   }
+  // the batch program depends only on the shapes and options: look it up first
+  std::vector<int64_t> key;
+  key.reserve(6 * (size_t)count + 4);
+  key.push_back(esize);
+  key.push_back(h->strip_w);
+  key.push_back(h->auto_res);
+  key.push_back(count);
+  for (int64_t b = 0; b < count; ++b) {
+    key.push_back(m[b]);
+    key.push_back(n[b]);
+    key.push_back(nb_in ? nb_in[b] : -1);
+    key.push_back(ib_in ? ib_in[b] : -1);
+    key.push_back(tree_in ? tree_in[b] : -1);
+    key.push_back(var_in ? var_in[b] : -1);
+  }
+  std::shared_ptr<BatchPlan> bp;
+  {
+    auto it = h->batches.find(key);
+    if (it != h->batches.end()) bp = it->second;
+  }
+  if (!bp) {
+    bp = std::make_shared<BatchPlan>();
+    auto& mats = bp->mats;
+    mats.resize((size_t)count);
   // configuration (autotuned when nb is NULL) and plan of every matrix, in parallel on the host
   std::vector<int> bad((size_t)count, 0);   // 0 ok, else the error code of that matrix
   {
@@ -628,7 +667,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
     std::atomic<int64_t> next(0);
     auto worker = [&]() {
       for (int64_t b = next++; b < count; b = next++) {
-        One& o = mats[(size_t)b];
+        BatchPlan::One& o = mats[(size_t)b];
         try {
           if (nb_in) {
             o.nb = nb_in[b];
@@ -671,7 +710,6 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
     worker();
     for (auto& th : pool) th.join();
   }
-  size_t smem = 0;
   for (int64_t b = 0; b < count; ++b) {
     if (bad[(size_t)b]) {
       const int code = bad[(size_t)b];
@@ -679,33 +717,31 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
                        : code == BIDIAG_ERR_NOMEM ? "host allocation failed" : "unsupported configuration";
       return fail(h, code, "matrix " + std::to_string(b) + ": " + what);
     }
-    const One& o = mats[(size_t)b];
-    smem = std::max(smem, bd::exec_smem_bytes(o.nb, o.ib, o.w, esize));
+    const BatchPlan::One& o = mats[(size_t)b];
+    bp->smem = std::max(bp->smem, bd::exec_smem_bytes(o.nb, o.ib, o.w, esize));
   }
   // storage layout
-  std::vector<bd::MatInfo> info((size_t)count);
-  int64_t tot0 = 0, tot1 = 0, totT = 0, tiles_all = 0, cols_all = 0;
+  bp->info.resize((size_t)count);
   for (int64_t b = 0; b < count; ++b) {
     const bd::Plan& pl = mats[(size_t)b].pd->plan;
-    bd::MatInfo& mi = info[(size_t)b];
+    bd::MatInfo& mi = bp->info[(size_t)b];
     const int64_t t2 = (int64_t)pl.nb * pl.nb;
-    mi.off[0] = tot0;
+    mi.off[0] = bp->tot0;
     mi.ntiles[0] = (int64_t)pl.p * pl.q;
-    tot0 += mi.ntiles[0] * t2;
-    mi.off[1] = tot1;
+    bp->tot0 += mi.ntiles[0] * t2;
+    mi.off[1] = bp->tot1;
     mi.ntiles[1] = pl.variant == BIDIAG_RBIDIAG ? (int64_t)pl.q * pl.q : 0;
-    tot1 += mi.ntiles[1] * t2;
-    mi.offT = totT;
-    totT += (int64_t)std::max(1, pl.npanels) * pl.ib * pl.nb;
+    bp->tot1 += mi.ntiles[1] * t2;
+    mi.offT = bp->totT;
+    bp->totT += (int64_t)std::max(1, pl.npanels) * pl.ib * pl.nb;
     mi.nb = pl.nb;
     mi.ib = pl.ib;
     mi.w = pl.strip_w;
     mi.npanels = pl.npanels;
     mi.pad = 0;
-    tiles_all += mi.ntiles[0];
-    cols_all += n[b];
+    bp->tiles_all += mi.ntiles[0];
+    bp->cols_all += n[b];
   }
-  auto store = std::make_shared<BatchStore>();
   std::vector<const bd::Plan*> plans;
   for (auto& o : mats) plans.push_back(&o.pd->plan);
   std::vector<bd::DevTask> dev;
@@ -715,12 +751,24 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
   } catch (const std::exception& ex) {
     return fail(h, BIDIAG_ERR_UNSUPPORTED, std::string("merge: ") + ex.what());
   }
-  int rc = upload_program(h, store->prog, dev, deps, 1);
-  if (rc) return rc;
+  int rc0 = upload_program(h, bp->prog, dev, deps, 1);
+  if (rc0) return rc0;
+  bp->ntasks = (int)dev.size();
+  CK(h, cudaMalloc(&bp->d_mats, sizeof(bd::MatInfo) * (size_t)count));
+  CK(h, cudaMemcpy(bp->d_mats, bp->info.data(), sizeof(bd::MatInfo) * (size_t)count, cudaMemcpyHostToDevice));
+  if (h->batches.size() >= 8) h->batches.clear();
+  h->batches[key] = bp;
+  }
+  const auto& mats = bp->mats;
+  const auto& info = bp->info;
+  const int64_t tot0 = bp->tot0, tot1 = bp->tot1, totT = bp->totT, tiles_all = bp->tiles_all, cols_all = bp->cols_all;
+  const size_t smem = bp->smem;
+  auto store = std::make_shared<BatchStore>();
+  store->plan = bp;
+  int rc = 0;
   CK(h, cudaMalloc(&store->tiles, (size_t)std::max<int64_t>(1, tot0) * esize));
   if (tot1) CK(h, cudaMalloc(&store->tiles2, (size_t)tot1 * esize));
   CK(h, cudaMalloc(&store->T, (size_t)std::max<int64_t>(1, totT) * esize));
-  CK(h, cudaMalloc(&store->d_mats, sizeof(bd::MatInfo) * (size_t)count));
   CK(h, cudaMalloc(&store->d_desc, sizeof(bd::PackDesc) * 2 * (size_t)count));
   // results and their bands
   std::vector<bidiag_result*> res((size_t)count, nullptr);
@@ -766,10 +814,8 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
   }
   bd::PackDesc* d_pk = static_cast<bd::PackDesc*>(store->d_desc);
   bd::PackDesc* d_ex = d_pk + count;
-  cudaError_t e = cudaMemcpyAsync(store->d_mats, info.data(), sizeof(bd::MatInfo) * (size_t)count,
-                                  cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_pk, pk.data(), sizeof(bd::PackDesc) * (size_t)count, cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = cudaMemcpyAsync(d_pk, pk.data(), sizeof(bd::PackDesc) * (size_t)count, cudaMemcpyHostToDevice,
+                                  h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ex, ex.data(), sizeof(bd::PackDesc) * (size_t)count, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && tot1) e = cudaMemsetAsync(store->tiles2, 0, (size_t)tot1 * esize, h->stream);
@@ -781,9 +827,8 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev[1]);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaEventCreate"));
   }
-  rc = run_exec(h, store->prog, (int)dev.size(), store->tiles, tiles_all, store->tiles2, tot1 ? 1 : 0, nullptr, 0,
-                store->T, 0, 0, 1, 1, esize, timed, static_cast<const bd::MatInfo*>(store->d_mats), (int)count,
-                smem);
+  rc = run_exec(h, bp->prog, bp->ntasks, store->tiles, tiles_all, store->tiles2, tot1 ? 1 : 0, nullptr, 0, store->T,
+                0, 0, 1, 1, esize, timed, static_cast<const bd::MatInfo*>(bp->d_mats), (int)count, smem);
   if (rc) return bail(rc);
   h->timed = timed;
   e = bd::launch_extract_batched(d_ex, (int)count, cols_all, esize, h->stream);

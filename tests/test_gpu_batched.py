@@ -100,3 +100,27 @@ def test_batched_fp32(handle, torch_mod):
         ref = OB.bidiag_band(A64, d.nb, d.ib, d.tree, d.variant, resources=3)
         assert np.abs(r.band().cpu().numpy() - ref["ab"]).max() <= 5e-6 * np.linalg.norm(A64)
         r.free()
+
+
+def test_batched_program_cache(handle, torch_mod):
+    """A second call with the same shapes reuses the cached batch program: same bands bit for bit, and
+    the first call's results stay valid while the second call's exist (and after they are freed)."""
+    torch = torch_mod
+    shp = shapes(5, 12, 96)
+    As = [torch.from_numpy(np.asfortranarray(inputs.gaussian(m, n, seed=m + 3 * n))).cuda() for m, n in shp]
+    r1 = handle.band_batched(As)
+    handle.sync()
+    b1 = [r.band() for r in r1]
+    r2 = handle.band_batched(As)
+    handle.sync()
+    for x, r in zip(b1, r2):
+        assert torch.equal(x, r.band())
+    for r in r2:
+        r.free()
+    # other shapes in between, then the first results are still readable
+    r3 = handle.band_batched(As[:5])
+    handle.sync()
+    for x, r in zip(b1, r1):
+        assert torch.equal(x, r.band())
+    for r in r1 + r3:
+        r.free()
