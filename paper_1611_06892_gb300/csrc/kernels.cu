@@ -91,7 +91,7 @@ __host__ __device__ inline Layout layout_panel(int nb, int ib, int esize) {
   L.P = o;   o = align4(o + L.lp * ib);
   L.Rt = o;  o = align4(o + ib * ib);
   L.Tb = o;  o = align4(o + ib * ib);
-  L.G = o;   o = align4(o + ib * ib);
+  L.G = o;   o = align4(o + 2 * ib * ib);   // Gram matrix and a scratch block for T
   L.V = L.Cs = L.Ct = L.W = L.W2 = -1;
   L.total = o;
   return L;
@@ -385,10 +385,12 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
   __syncthreads();
 }
 
-// T factor (kb x kb, upper) of the kb reflectors in P: T[l,l] = tau_l,
-// T[0:l, l] = -tau_l T[0:l, 0:l] (V[:, 0:l]^T v_l).  G is kb x kb scratch.  The Gram entries V^T V are
-// computed in 2 x 2 blocks per thread (no cross-lane reductions); the recurrence uses four independent
-// partial sums per entry.
+// T factor (kb x kb, upper) of the kb reflectors in P, Q = H_0 ... H_{kb-1} = I - V T V^T.  G is
+// 2 kb x kb scratch (the Gram matrix V^T V, then a work block).  The Gram entries are computed in 2 x 2
+// blocks per thread (no cross-lane reductions).  T itself: the forward recurrence T[l,l] = tau_l,
+// T[0:l, l] = -tau_l T[0:l, 0:l] G[0:l, l] inside diagonal blocks of 8 columns (all blocks at once),
+// then blocks are merged pairwise, [T11 T12; 0 T22] with T12 = -T11 G12 T22 (the product of two compact
+// WY blocks), so the sequential depth is 8 + 2 log2(kb/8) barrier steps instead of kb.
 template <typename E>
 __device__ void build_t(int mode, const E* P, int lp, int rows, int kb, int voff, const double* tau_s, E* Tb, int ldt,
                         E* G) {
@@ -436,24 +438,47 @@ __device__ void build_t(int mode, const E* P, int lp, int rows, int kb, int voff
     if (a1 < l1 && a1 != a0 && l1 != l0) G[a1 + l1 * kb] = s11;
   }
   __syncthreads();
-  for (int l = 0; l < kb; ++l) {
-    for (int a = threadIdx.x; a < kb; a += kThreads) {
-      E v = E(0);
+  E* Y = G + kb * kb;
+  constexpr int kB0 = 8;
+  for (int o = threadIdx.x; o < kb * kb; o += kThreads) Tb[(o % kb) + (o / kb) * ldt] = E(0);
+  __syncthreads();
+  // diagonal blocks of kB0 columns: the forward recurrence, all blocks in parallel
+  const int nblk0 = (kb + kB0 - 1) / kB0;
+  for (int step = 0; step < kB0; ++step) {
+    for (int u = threadIdx.x; u < nblk0 * kB0; u += kThreads) {
+      const int d = u / kB0, a = d * kB0 + u % kB0, l = d * kB0 + step;
+      if (l >= kb || a > l) continue;
       if (a == l) {
-        v = (E)tau_s[l];
-      } else if (a < l) {
-        E p0 = E(0), p1 = E(0), p2 = E(0), p3 = E(0);
-        int t = a;
-        for (; t + 3 < l; t += 4) {
-          p0 += Tb[a + t * ldt] * G[t + l * kb];
-          p1 += Tb[a + (t + 1) * ldt] * G[t + 1 + l * kb];
-          p2 += Tb[a + (t + 2) * ldt] * G[t + 2 + l * kb];
-          p3 += Tb[a + (t + 3) * ldt] * G[t + 3 + l * kb];
-        }
-        for (; t < l; ++t) p0 += Tb[a + t * ldt] * G[t + l * kb];
-        v = -(E)tau_s[l] * ((p0 + p1) + (p2 + p3));
+        Tb[l + l * ldt] = (E)tau_s[l];
+      } else {
+        E acc = E(0);
+        for (int t = a; t < l; ++t) acc += Tb[a + t * ldt] * G[t + l * kb];
+        Tb[a + l * ldt] = -(E)tau_s[l] * acc;
       }
-      Tb[a + l * ldt] = v;
+    }
+    __syncthreads();
+  }
+  // pairwise merges: T12 = -T11 (G12 T22) for blocks [c0, c0 + h) and [c0 + h, c1)
+  for (int h = kB0; h < kb; h *= 2) {
+    const int npair = (kb + 2 * h - 1) / (2 * h);
+    for (int u = threadIdx.x; u < npair * h * h; u += kThreads) {     // Y = G12 T22
+      const int pr = u / (h * h), i = (u % (h * h)) % h, j = (u % (h * h)) / h;
+      const int c0 = pr * 2 * h, c1 = min(c0 + 2 * h, kb);
+      if (c0 + h + j >= c1) continue;
+      const int col = c0 + h + j;
+      E acc = E(0);
+      for (int t = c0 + h; t <= col; ++t) acc += G[(c0 + i) + t * kb] * Tb[t + col * ldt];
+      Y[(c0 + i) + col * kb] = acc;
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < npair * h * h; u += kThreads) {     // T12 = -T11 Y
+      const int pr = u / (h * h), i = (u % (h * h)) % h, j = (u % (h * h)) / h;
+      const int c0 = pr * 2 * h, c1 = min(c0 + 2 * h, kb);
+      if (c0 + h + j >= c1) continue;
+      const int row = c0 + i, col = c0 + h + j;
+      E acc = E(0);
+      for (int t = row; t < c0 + h; ++t) acc += Tb[row + t * ldt] * Y[t + col * kb];
+      Tb[row + col * ldt] = -acc;
     }
     __syncthreads();
   }
