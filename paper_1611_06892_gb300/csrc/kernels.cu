@@ -855,6 +855,43 @@ __device__ void bwd_partial(const E* Cs, const E* Cg, int lc, int vrows, int kb,
   }
 }
 
+// Sum of the update-strip partials of panel block b over rows [chunk R, (chunk + 1) R) of its P'
+// (R = kRedElems / ib, clipped to the block's vrows rows) and, with chunk 0, of its S block, in slot
+// order and in FP64, into the panel's reduced slot `out` (laid out as an update slot).  Each thread
+// keeps kRedPer independent sums, so that kRedPer loads per slot are in flight at once.
+constexpr int kRedPer = kRedElems / kThreads;
+template <typename E>
+__device__ void task_bwd_reduce(int nb, int ib, int b, int chunk, int vrows, const E* part, const int64_t* slot_off,
+                                int u0, int nu, E* out) {
+  const int kb = ib, nblk = nb / ib, rows = max(1, kRedElems / kb);
+  const int r0 = chunk * rows, r1 = min(vrows, r0 + rows);
+  const size_t pblk = (size_t)b * nb * ib, sblk = (size_t)nblk * nb * ib + (size_t)b * kb * kb;
+  const int o0 = r0 * kb, o1 = r1 * kb;    // element (r, k) of the block at pblk + r kb + k
+  double acc[kRedPer];
+#pragma unroll
+  for (int j = 0; j < kRedPer; ++j) acc[j] = 0.0;
+  for (int i = 0; i < nu; ++i) {
+    const E* src = part + slot_off[u0 + i] + pblk;
+#pragma unroll
+    for (int j = 0; j < kRedPer; ++j) {
+      const int o = o0 + (int)threadIdx.x + j * kThreads;
+      if (o < o1) acc[j] += (double)ldg(src + o);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kRedPer; ++j) {
+    const int o = o0 + (int)threadIdx.x + j * kThreads;
+    if (o < o1) stg(out + pblk + o, (E)acc[j]);
+  }
+  if (chunk == 0) {
+    for (int o = threadIdx.x; o < kb * kb; o += kThreads) {
+      double s = 0.0;
+      for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + sblk + o);
+      stg(out + sblk + o, (E)s);
+    }
+  }
+}
+
 // Adjoint of an update (UNMQR / TSMQR / TTMQR strip, or PU(b, s) with C = the panel tile): blocks
 // [blk0, blk1) are undone in decreasing order on the state (C_s, Cp_s) and the gradient (C_g, Cp_g) of
 // columns [col0, col0 + ncols), chunk by chunk, and each block's P' (vrows x ib, row-major) and S
@@ -1251,7 +1288,8 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         E* Xg = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
         if (ok && Tg && blk < nblk && kind <= PM_TT && bw.part && bw.red) {
           const int32_t* pi = bw.pinfo + 4 * t.tslot;
-          const int u0 = pi[0], nu = pi[1], pu0 = pi[2];
+          // the update strips' sum comes from the reduced slot when the panel has one
+          const int u0 = pi[3] >= 0 ? pi[3] : pi[0], nu = pi[3] >= 0 ? 1 : pi[1], pu0 = pi[2];
           if (u0 < 0 || nu < 0 || u0 + nu > bw.nslots || pu0 < 0 || pu0 + nblk * (nblk - 1) / 2 > bw.nslots) {
             ok = false;
           } else {
@@ -1291,6 +1329,24 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
                           static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
         else
           ok = false;
+        break;
+      }
+      case BRED: {
+        const BwdParams& bw = prm.bwd;
+        const int vrows = kind == PM_GE ? nb - blk * ib : (kind == PM_TS ? nb : (blk + 1) * ib);
+        if (ok && blk < nblk && kind <= PM_TT && bw.part && t.tslot >= 0 && t.tslot < mv.npanels &&
+            strip * max(1, kRedElems / ib) < vrows) {
+          const int32_t* pi = bw.pinfo + 4 * t.tslot;
+          const int u0 = pi[0], nu = pi[1], r = pi[3];
+          if (u0 < 0 || nu < 0 || u0 + nu > bw.nslots || r < 0 || r >= bw.nslots) {
+            ok = false;
+          } else {
+            task_bwd_reduce(nb, ib, blk, strip, vrows, static_cast<const E*>(bw.part), bw.slot_off, u0, nu,
+                            static_cast<E*>(bw.part) + bw.slot_off[r]);
+          }
+        } else {
+          ok = false;
+        }
         break;
       }
       case BCOPY: {   // gradient of the copied part of R tile c back onto pre-QR tile x

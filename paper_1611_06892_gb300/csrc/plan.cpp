@@ -752,6 +752,12 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
       bp.slot_off.push_back(off);
       off += pu_size;
     }
+    bp.pinfo[4 * t + 3] = -1;
+    if (nupd[t] >= kRedMinSlots) {   // reduced slot, laid out as an update slot
+      bp.pinfo[4 * t + 3] = (int32_t)bp.slot_off.size();
+      bp.slot_off.push_back(off);
+      off += upd_size;
+    }
   }
   bp.slot_off.push_back(off);
   if (bp.slot_off.size() >= (1u << 31)) throw std::invalid_argument("too many partial slots");
@@ -763,6 +769,7 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
   std::vector<int64_t> wt;
   std::vector<int32_t> fwd_of;
   std::vector<int32_t> first(nsub + 1, 0);
+  std::vector<std::vector<int32_t>> bupd_of(std::max(1, pl.npanels));   // adjoint update strips per panel
   const int64_t ib2 = (int64_t)ib * ib;
   for (int32_t y = 0; y < nsub; ++y) {
     first[y] = (int32_t)sub.size();
@@ -798,6 +805,7 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
         DevTask e = d;
         e.op = make_op(BUPD, tr, false, sb, 0, uk);
         e.flags = bp.pinfo[4 * f.tslot + 0] + next_upd[f.tslot]++;
+        bupd_of[f.tslot].push_back((int32_t)sub.size());
         sub.push_back(e);
         wt.push_back(3 * (type == TSMQR ? 4 : 2) * (int64_t)nb * nb * wb);
         fwd_of.push_back(y);
@@ -814,6 +822,31 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
     }
   }
   first[nsub] = (int32_t)sub.size();
+  // reduction sub-tasks: per block of a panel with a reduced slot, chunks of kRedElems / ib rows
+  std::vector<std::pair<int32_t, int32_t>> red_edge;   // (BRED node, BPF node it feeds)
+  const int red_rows = std::max(1, kRedElems / ib);
+  for (int32_t y = 0; y < nsub; ++y) {
+    const DevTask& f = pl.dev[y];
+    if ((f.op & 15) != PF || bp.pinfo[4 * f.tslot + 3] < 0) continue;
+    const int tr = (f.op >> 4) & 1, blk = (f.op >> 16) & 0xff, kind = (f.op >> 24) & 3;
+    const int64_t vrows = kind == PK_GE ? nb - (int64_t)blk * ib : (kind == PK_TS ? nb : (int64_t)(blk + 1) * ib);
+    const int nchunk = (int)((vrows + red_rows - 1) / red_rows);
+    if (nchunk > 255) throw std::invalid_argument("too many reduction chunks");
+    const int64_t nu = nupd[f.tslot];
+    for (int c = 0; c < nchunk; ++c) {
+      DevTask e{};
+      e.op = make_op(BRED, tr, false, c, blk, kind);
+      e.x = state_ref(f.x);
+      e.a = -1;
+      e.c = -1;
+      e.tslot = f.tslot;
+      e.flags = 0;
+      red_edge.push_back({(int32_t)sub.size(), first[y]});
+      sub.push_back(e);
+      wt.push_back(nu * std::min<int64_t>(red_rows, vrows - (int64_t)c * red_rows) * ib + (c == 0 ? nu * ib2 : 0));
+      fwd_of.push_back(y);
+    }
+  }
   const int32_t nnode = (int32_t)sub.size();
   // reversed DAG: forward y depends on d  ->  every adjoint node of d depends on every node of y
   std::vector<std::vector<int32_t>> rdeps(nnode);
@@ -823,15 +856,32 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
       for (int32_t a = first[d]; a < first[d + 1]; ++a)
         for (int32_t b = first[y]; b < first[y + 1]; ++b) rdeps[a].push_back(b);
     }
-  // bottom levels of the reversed DAG (the successors of y's nodes are the nodes of y's dependencies)
-  std::vector<int64_t> bottom(nnode, 0);
-  for (int32_t y = 0; y < nsub; ++y) {
-    int64_t mx = 0;
-    for (int32_t k = pl.dev[y].dep_begin; k < pl.dev[y].dep_end; ++k) {
-      const int32_t d = pl.deps[k];
-      for (int32_t a = first[d]; a < first[d + 1]; ++a) mx = std::max(mx, bottom[a]);
+  // a reduction waits for every update strip of its panel; the factor sub-task waits for its reductions
+  for (const auto& re : red_edge) {
+    rdeps[re.first] = bupd_of[sub[re.first].tslot];
+    rdeps[re.second].push_back(re.first);
+  }
+  // bottom levels of the reversed DAG, over a topological order (Kahn)
+  std::vector<std::vector<int32_t>> succ(nnode);
+  std::vector<int32_t> indeg(nnode, 0), topo;
+  topo.reserve(nnode);
+  for (int32_t a = 0; a < nnode; ++a)
+    for (int32_t b : rdeps[a]) {
+      succ[b].push_back(a);
+      ++indeg[a];
     }
-    for (int32_t b = first[y]; b < first[y + 1]; ++b) bottom[b] = wt[b] + mx;
+  for (int32_t a = nnode - 1; a >= 0; --a)
+    if (indeg[a] == 0) topo.push_back(a);
+  for (size_t h = 0; h < topo.size(); ++h)
+    for (int32_t a : succ[topo[h]])
+      if (--indeg[a] == 0) topo.push_back(a);
+  if ((int32_t)topo.size() != nnode) throw std::logic_error("adjoint DAG has a cycle");
+  std::vector<int64_t> bottom(nnode, 0);
+  for (int32_t h = nnode - 1; h >= 0; --h) {
+    const int32_t a = topo[h];
+    int64_t mx = 0;
+    for (int32_t b : succ[a]) mx = std::max(mx, bottom[b]);
+    bottom[a] = wt[a] + mx;
   }
   std::vector<int32_t> order(nnode);
   for (int32_t z = 0; z < nnode; ++z) order[z] = nnode - 1 - z;

@@ -13,7 +13,13 @@ enum SubType : int { PF = 7, PU = 8 };
 // Sub-tasks of the adjoint program (reverse sweep): BPF / BPU undo PF / PU, BUPD undoes an update strip
 // (kind bits 24-25: 0 UNMQR, 1 TSMQR, 2 TTMQR), BCOPY undoes a COPY (adds the gradient of the copied
 // part of an R tile to the pre-QR tile it was copied from).
-enum BwdType : int { BPF = 9, BPU = 10, BUPD = 11, BCOPY = 12 };
+enum BwdType : int { BPF = 9, BPU = 10, BUPD = 11, BCOPY = 12, BRED = 13 };
+// BRED: sums, in slot order, the update-strip partials of one block of a panel task over a chunk of
+// kRedElems / ib rows (strip field = chunk index, blk = block, kind = panel kind) into the panel's
+// reduced slot, so that the factor sub-task of the block reads one slot instead of all of them.
+// Panels with fewer than kRedMinSlots update strips keep the direct sum.
+constexpr int kRedElems = 2048;
+constexpr int kRedMinSlots = 8;
 enum Phase : int { PH_QR = 0, PH_LQ = 1, PH_PQR = 2 };
 enum Tree : int { FLATTS = 0, FLATTT = 1, GREEDY = 2, AUTO = 3 };
 enum Variant : int { V_BIDIAG = 0, V_RBIDIAG = 1 };
@@ -77,12 +83,14 @@ struct Plan {
 // R copy (q x q, R-BiDiag); the gradients are buffers 4 and 5 with the same indices.  BCOPY: x = the
 // pre-QR state tile, c = the R state tile, flags bit 0 = diagonal tile.  Update sub-tasks write their
 // contributions to the reflectors' derivatives into partial slots (flags = slot index); the factor
-// sub-task of a block sums them.
+// sub-task of a block sums them, or reads their sum from the panel's reduced slot (pinfo[3] >= 0),
+// written by the BRED sub-tasks of the block.
 struct BwdPlan {
   std::vector<DevTask> dev;
   std::vector<int32_t> deps;
   std::vector<int64_t> slot_off;   // element offset of each partial slot; last entry = total elements
-  std::vector<int32_t> pinfo;      // per panel task (T slot): first update slot, number, first PU slot, 0
+  std::vector<int32_t> pinfo;      // per panel task (T slot): first update slot, number, first PU slot,
+                                   // reduced slot (-1: none)
   std::vector<int32_t> fwd;        // forward queue position of each adjoint sub-task
   int strip_w = 0;                 // column width of the adjoint update strips
 };

@@ -6,6 +6,9 @@
   their counterparts; every partial slot is written by one sub-task that precedes the factor sub-task
   reading it.  Footprints are modelled from what the CUDA sub-tasks load and store.
 * The slot table covers each panel task's update strips and panel-block updates exactly once.
+* Panels with at least eight update strips get a reduced slot: reduction sub-tasks, which follow every
+  update strip of the panel, sum the strips' partials block by block over row chunks that tile the
+  block's rows, and the factor sub-task of a block follows its reductions.
 """
 import numpy as np
 import pytest
@@ -13,7 +16,8 @@ import pytest
 import paper_1611_06892_gb300 as G
 
 UNMQR, TSMQR, TTMQR, COPY, PF, PU = 1, 3, 5, 6, 7, 8
-BPF, BPU, BUPD, BCOPY = 9, 10, 11, 12
+BPF, BPU, BUPD, BCOPY, BRED = 9, 10, 11, 12, 13
+RED_ELEMS, RED_MIN = 2048, 8
 GE, TS, TT = 0, 1, 2
 
 
@@ -70,7 +74,7 @@ def state_footprint(f, nb, ib, w):
     return out
 
 
-def check_backward(m, n, nb, ib, tree, variant, strip_w):
+def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
     fprog, fdeps, w = G.bidiag_plan_program(m, n, nb, ib, tree, variant, resources=2, strip_w=strip_w)
     prog, fwd, deps, slot_off, pinfo, wb = G.bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=2,
                                                                   strip_w=strip_w)
@@ -82,7 +86,7 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
     split = w // wb
     assert split in (1, 2) and wb * split == w
     for y in range(len(fprog)):
-        ys = [z for z in range(nsub) if fwd[z] == y]
+        ys = [z for z in range(nsub) if fwd[z] == y and fields(prog[z])["typ"] != BRED]
         g = fields(fprog[y])
         if g["typ"] in (UNMQR, TSMQR, TTMQR):
             cols = sorted(fields(prog[z])["strip"] for z in ys)
@@ -94,6 +98,9 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
     kind_map = {PF: BPF, PU: BPU, UNMQR: BUPD, TSMQR: BUPD, TTMQR: BUPD, COPY: BCOPY}
     for y in range(nsub):
         f, g = fields(prog[y]), fields(fprog[fwd[y]])
+        if f["typ"] == BRED:        # serves the factor sub-task of the same block
+            assert g["typ"] == PF and (f["blk"], f["kind"], f["tslot"]) == (g["blk"], g["kind"], g["tslot"])
+            continue
         assert f["typ"] == kind_map[g["typ"]]
         if f["typ"] in (BPF, BPU):
             assert (f["blk"], f["kind"], f["tslot"], f["x"]) == (g["blk"], g["kind"], g["tslot"], g["x"])
@@ -111,7 +118,7 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
         anc[y] = acc
     # state / gradient: conflicts ordered in reverse forward order
     touch = {}
-    for y in range(nsub):
+    for y in range(nsub if state else 0):
         for e in state_footprint(fields(prog[y]), nb, ib, wb):
             touch.setdefault(e, []).append(y)
     for e, ys in touch.items():
@@ -131,20 +138,47 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w):
             else:
                 b, s = f["blk"], f["strip"]
                 assert f["flags"] == t[2] + b * nblk - b * (b + 1) // 2 + (s - b - 1)
+    # reductions: (panel, block) -> chunk -> sub-task; each follows every update strip of its panel
+    red = {}
+    for y in range(nsub):
+        f = fields(prog[y])
+        if f["typ"] != BRED:
+            continue
+        t = pinfo[f["tslot"]]
+        assert t[3] >= 0 and t[1] >= RED_MIN
+        chunks = red.setdefault((f["tslot"], f["blk"]), {})
+        assert f["strip"] not in chunks
+        chunks[f["strip"]] = y
+        for sl in range(t[0], t[0] + t[1]):
+            assert (anc[y] >> writer[sl]) & 1, f"reduction {y} before update slot {sl}"
+    nred = 0
     for y in range(nsub):
         f = fields(prog[y])
         if f["typ"] != BPF:
             continue
         t = pinfo[f["tslot"]]
         b = f["blk"]
-        reads = list(range(t[0], t[0] + t[1]))
+        assert (t[3] >= 0) == (t[1] >= RED_MIN)
+        if t[3] >= 0:
+            vrows = nb - b * ib if f["kind"] == GE else (nb if f["kind"] == TS else (b + 1) * ib)
+            rows = max(1, RED_ELEMS // ib)
+            chunks = red.pop((f["tslot"], b))
+            assert sorted(chunks) == list(range(-(-vrows // rows)))
+            for z in chunks.values():
+                assert (anc[y] >> z) & 1, f"factor sub-task {y} before its reduction {z}"
+            reads = []
+            nred += b == 0
+        else:
+            reads = list(range(t[0], t[0] + t[1]))
         reads += [t[2] + b * nblk - b * (b + 1) // 2 + (s - b - 1) for s in range(b + 1, nblk)]
         for sl in reads:
             assert sl in writer and (anc[y] >> writer[sl]) & 1, f"slot {sl} not written before its reader {y}"
-    # slot offsets: increasing, sizes nb^2 + nb ib (update strips) and nb ib + ib^2 (panel-block updates)
+    assert not red, "a reduction without its factor sub-task"
+    # slot offsets: increasing, sizes nb^2 + nb ib (update strips, reduced slots) and nb ib + ib^2
+    # (panel-block updates)
     sizes = np.diff(slot_off)
     assert set(sizes.tolist()) <= {nb * nb + nb * ib, nb * ib + ib * ib}
-    assert len(writer) == len(slot_off) - 1
+    assert len(writer) + nred == len(slot_off) - 1
     return nsub
 
 
@@ -182,3 +216,17 @@ def test_checker_catches_a_reversed_edge(monkeypatch):
 def test_adjoint_program_order_three_step(tree, split):
     assert check_backward(22, 20, 8, 4, tree, 4 + split, strip_w=4) > 0
     assert check_backward(30, 18, 6, 2, tree, 4 + split, strip_w=4) > 0
+
+
+@pytest.mark.parametrize("variant", (0, 1), ids=("bidiag", "rbidiag"))
+@pytest.mark.parametrize("tree", (0, 2), ids=("flatts", "greedy"))
+def test_adjoint_program_reductions(tree, variant):
+    """Tall enough that panels have many update strips: reductions appear and are ordered."""
+    prog = G.bidiag_plan_backward(100, 40, 8, 4, tree, variant, resources=2, strip_w=4)[0]
+    assert any((int(op) & 15) == BRED for op in prog[:, 0])
+    assert check_backward(100, 40, 8, 4, tree, variant, strip_w=4) > 0
+    # ib = 2: 1024-row chunks cover a block in one chunk; ib = 8 with nb = 32: 256-row chunks
+    assert check_backward(130, 24, 6, 2, tree, variant, strip_w=2) > 0
+    assert check_backward(300, 64, 32, 8, tree, variant, strip_w=16) > 0
+    # nb = 256, ib = 32: 64-row chunks, four per block (slot and order checks only)
+    assert check_backward(1600, 512, 256, 32, tree, variant, strip_w=32, state=False) > 0
