@@ -601,6 +601,7 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
   bp.pinfo = bw.d_pinfo;
   bp.red = red;
   bp.hw = hw;
+  bp.pu_split = bw.bp.pu_split;
   const void* bx[3] = {S2, G, G2};
   const int64_t nx[3] = {ntiles2, ntiles, ntiles2};
   rc = run_exec(h, bw.prog, (int)bw.bp.dev.size(), r->tiles, ntiles, r->tiles2, ntiles2, S, ntiles, r->T, pl.npanels,

@@ -963,7 +963,7 @@ __device__ void task_bwd_update(unsigned char* smb, int type, const E* X, E* Cp_
 template <typename E>
 __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s, E* X_s, E* A_g, E* X_g, int tr,
                                const E* Tg, int nb, int ib, int b, const E* part, const int64_t* slot_off, int u0,
-                               int nu, int pu0, E* red) {
+                               int nu, int pu0, int pus, E* red) {
   const BwdLayout L = layout_bwd_panel(nb, ib, (int)sizeof(E));
   double* tau = reinterpret_cast<double*>(smb);
   double* rsc = tau + 64;
@@ -982,18 +982,19 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
   for (int k = threadIdx.x; k < kb; k += kThreads) tau[k] = (double)ldg(Tg + (size_t)c0 * ib + k + k * ib);
   // partial sums, in slot order (deterministic); Ms holds P' meanwhile
   const size_t pblk = (size_t)b * nb * ib, sblk = (size_t)nblk * nb * ib + (size_t)b * kb * kb;
-  const int pu_first = pu0 + b * nblk - b * (b + 1) / 2;
+  // panel-block update slots of this block: (s - b - 1) pus + h for the later blocks s, pieces h
+  const int pu_first = pu0 + (b * nblk - b * (b + 1) / 2) * pus, npu_b = (nblk - 1 - b) * pus;
   for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
     const int k = o % kb, r = o / kb;
     double s = 0.0;
     for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + pblk + (size_t)r * kb + k);
-    for (int sb = b + 1; sb < nblk; ++sb) s += (double)ldg(part + slot_off[pu_first + sb - b - 1] + (size_t)r * kb + k);
+    for (int i = 0; i < npu_b; ++i) s += (double)ldg(part + slot_off[pu_first + i] + (size_t)r * kb + k);
     Ms[r + k * lp] = (E)s;
   }
   for (int o = threadIdx.x; o < kb * kb; o += kThreads) {
     double s = 0.0;
     for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + sblk + o);
-    for (int sb = b + 1; sb < nblk; ++sb) s += (double)ldg(part + slot_off[pu_first + sb - b - 1] + (size_t)nb * kb + o);
+    for (int i = 0; i < npu_b; ++i) s += (double)ldg(part + slot_off[pu_first + i] + (size_t)nb * kb + o);
     Sb[o] = (E)s;
   }
   __syncthreads();
@@ -1290,11 +1291,13 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
           const int32_t* pi = bw.pinfo + 4 * t.tslot;
           // the update strips' sum comes from the reduced slot when the panel has one
           const int u0 = pi[3] >= 0 ? pi[3] : pi[0], nu = pi[3] >= 0 ? 1 : pi[1], pu0 = pi[2];
-          if (u0 < 0 || nu < 0 || u0 + nu > bw.nslots || pu0 < 0 || pu0 + nblk * (nblk - 1) / 2 > bw.nslots) {
+          const int pus = bw.pu_split;
+          if (u0 < 0 || nu < 0 || u0 + nu > bw.nslots || pu0 < 0 || (pus != 1 && pus != 2) ||
+              pu0 + nblk * (nblk - 1) / 2 * pus > bw.nslots) {
             ok = false;
           } else {
             task_bwd_panel(smb, kind, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, blk, static_cast<const E*>(bw.part),
-                           bw.slot_off, u0, nu, pu0, static_cast<E*>(bw.red) + (size_t)t.tslot * nb * nb);
+                           bw.slot_off, u0, nu, pu0, pus, static_cast<E*>(bw.red) + (size_t)t.tslot * nb * nb);
           }
         } else {
           ok = false;
@@ -1308,10 +1311,11 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         E* Xs = tile_ptr<E>(prm, mv, t.c, ok);
         E* Xg = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
         const int utype = kind == PM_GE ? UNMQR : (kind == PM_TS ? TSMQR : TTMQR);
+        const int pus = bw.pu_split, half = notrans ? 1 : 0, pw = ib / max(1, pus);
         if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT && bw.part && t.flags >= 0 &&
-            t.flags < bw.nslots)
-          task_bwd_update(smb, utype, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, bw.hw, blk, blk + 1, strip * ib, ib,
-                          static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
+            t.flags < bw.nslots && (pus == 1 || pus == 2) && half < pus && pw * pus == ib)
+          task_bwd_update(smb, utype, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, bw.hw, blk, blk + 1, strip * ib + half * pw,
+                          pw, static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
         else
           ok = false;
         break;

@@ -36,9 +36,11 @@ struct BwdParams {
   void* part;               // partial slots (element type by esize)
   const int64_t* slot_off;  // element offset of each slot
   int32_t nslots;
-  const int32_t* pinfo;     // per panel task: first update slot, number of update slots, first PU slot, 0
+  const int32_t* pinfo;     // per panel task: first update slot, number of update slots, first PU slot,
+                            // reduced slot (-1: none)
   void* red;                // per panel task nb x nb: summed derivative of its reflector tails
   int hw;                   // column chunk of the update adjoints
+  int pu_split;             // column pieces of a panel-block update adjoint (1 or 2)
 };
 
 struct ExecParams {

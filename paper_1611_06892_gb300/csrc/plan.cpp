@@ -714,6 +714,8 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
   // latency on the critical path.
   const int w = pl.strip_w, split = (split_strips && w >= 16 && w % 2 == 0) ? 2 : 1, wb = w / split;
   bp.strip_w = wb;
+  const int pus = (split_strips && ib >= 16 && ib % 2 == 0) ? 2 : 1;   // BPU column pieces
+  bp.pu_split = pus;
   auto state_ref = [&](int32_t ref) -> int32_t {   // forward buffer 0 / 1 -> state buffer 2 / 3
     if (ref < 0) return -1;
     const int buf = (int)((uint32_t)ref >> 28);
@@ -728,7 +730,7 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
     return n;
   };
   // slots: per panel task, its adjoint update strips first (in program order), then its PU sub-tasks
-  const int npu = nblk * (nblk - 1) / 2;
+  const int npu = nblk * (nblk - 1) / 2 * pus;
   std::vector<int32_t> nupd(std::max(1, pl.npanels), 0);
   for (const DevTask& f : pl.dev) {
     if (is_upd(f.op & 15)) {
@@ -762,7 +764,7 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
   bp.slot_off.push_back(off);
   if (bp.slot_off.size() >= (1u << 31)) throw std::invalid_argument("too many partial slots");
   std::vector<int32_t> next_upd(std::max(1, pl.npanels), 0);
-  auto pu_index = [&](int b, int s) { return b * nblk - b * (b + 1) / 2 + (s - b - 1); };
+  auto pu_index = [&](int b, int s, int h) { return (b * nblk - b * (b + 1) / 2 + (s - b - 1)) * pus + h; };
 
   // adjoint nodes: one per forward sub-task, `split` per forward update strip
   std::vector<DevTask> sub;
@@ -787,13 +789,18 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
       if (type == PF) {
         d.op = make_op(BPF, tr, false, 0, blk, kind);
         wt.push_back(10 * ib2 * rows);
+        sub.push_back(d);
+        fwd_of.push_back(y);
       } else {
-        d.op = make_op(BPU, tr, false, strip, blk, kind);
-        d.flags = bp.pinfo[4 * f.tslot + 2] + pu_index(blk, strip);
-        wt.push_back(14 * ib2 * rows);
+        for (int h = 0; h < pus; ++h) {
+          DevTask e = d;
+          e.op = make_op(BPU, tr, h == 1, strip, blk, kind);
+          e.flags = bp.pinfo[4 * f.tslot + 2] + pu_index(blk, strip, h);
+          wt.push_back(14 * ib2 * rows / pus);
+          sub.push_back(e);
+          fwd_of.push_back(y);
+        }
       }
-      sub.push_back(d);
-      fwd_of.push_back(y);
     } else if (is_upd(type)) {
       d.a = state_ref(f.a);
       d.c = state_ref(f.c);

@@ -23,11 +23,11 @@ GE, TS, TT = 0, 1, 2
 
 def fields(t):
     op = int(t[0])
-    return dict(typ=op & 15, tr=(op >> 4) & 1, strip=(op >> 8) & 0xFF, blk=(op >> 16) & 0xFF, kind=(op >> 24) & 3,
+    return dict(typ=op & 15, tr=(op >> 4) & 1, half=(op >> 5) & 1, strip=(op >> 8) & 0xFF, blk=(op >> 16) & 0xFF, kind=(op >> 24) & 3,
                 x=int(t[1]), a=int(t[2]), c=int(t[3]), tslot=int(t[4]), flags=int(t[7]))
 
 
-def state_footprint(f, nb, ib, w):
+def state_footprint(f, nb, ib, w, pus=1):
     """Elements (tile, row, col) of the working state / gradient an adjoint sub-task reads or writes."""
     tr = f["tr"]
     out = set()
@@ -62,7 +62,8 @@ def state_footprint(f, nb, ib, w):
             region(f["c"], 0, c0, nb if kind == TS else c0 + ib, ib, upper=(kind == TT))
     elif typ == BPU:
         utype = {GE: UNMQR, TS: TSMQR, TT: TTMQR}[kind]
-        update(utype, f["a"], f["c"], blk, blk + 1, f["strip"] * ib, ib)
+        pw = ib // pus
+        update(utype, f["a"], f["c"], blk, blk + 1, f["strip"] * ib + f["half"] * pw, pw)
     elif typ == BUPD:
         utype = (UNMQR, TSMQR, TTMQR)[kind]
         col0 = f["strip"] * w
@@ -85,6 +86,10 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
     assert set(fwd.tolist()) == set(range(len(fprog)))
     split = w // wb
     assert split in (1, 2) and wb * split == w
+    # panel-block updates are undone as two column halves (op bit 5 = half) with the update strips
+    pus = 2 if any(fields(t)["typ"] == BPU and fields(t)["half"] for t in prog) else 1
+    if nb > ib:
+        assert pus == (2 if split == 2 and ib >= 16 and ib % 2 == 0 else 1)
     for y in range(len(fprog)):
         ys = [z for z in range(nsub) if fwd[z] == y and fields(prog[z])["typ"] != BRED]
         g = fields(fprog[y])
@@ -92,6 +97,8 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
             cols = sorted(fields(prog[z])["strip"] for z in ys)
             want = [g["strip"] * split + hh for hh in range(split) if (g["strip"] * split + hh) * wb < nb]
             assert cols == want
+        elif g["typ"] == PU:
+            assert sorted(fields(prog[z])["half"] for z in ys) == list(range(pus))
         else:
             assert len(ys) == 1
     # kinds match the forward sub-tasks they undo
@@ -119,7 +126,7 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
     # state / gradient: conflicts ordered in reverse forward order
     touch = {}
     for y in range(nsub if state else 0):
-        for e in state_footprint(fields(prog[y]), nb, ib, wb):
+        for e in state_footprint(fields(prog[y]), nb, ib, wb, pus):
             touch.setdefault(e, []).append(y)
     for e, ys in touch.items():
         ys = sorted(ys, key=lambda y: -fwd[y])        # the order the reverse sweep must follow
@@ -137,7 +144,7 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
                 assert t[0] <= f["flags"] < t[0] + t[1]
             else:
                 b, s = f["blk"], f["strip"]
-                assert f["flags"] == t[2] + b * nblk - b * (b + 1) // 2 + (s - b - 1)
+                assert f["flags"] == t[2] + (b * nblk - b * (b + 1) // 2 + (s - b - 1)) * pus + f["half"]
     # reductions: (panel, block) -> chunk -> sub-task; each follows every update strip of its panel
     red = {}
     for y in range(nsub):
@@ -170,7 +177,8 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
             nred += b == 0
         else:
             reads = list(range(t[0], t[0] + t[1]))
-        reads += [t[2] + b * nblk - b * (b + 1) // 2 + (s - b - 1) for s in range(b + 1, nblk)]
+        reads += [t[2] + (b * nblk - b * (b + 1) // 2 + (s - b - 1)) * pus + hh for s in range(b + 1, nblk)
+                  for hh in range(pus)]
         for sl in reads:
             assert sl in writer and (anc[y] >> writer[sl]) & 1, f"slot {sl} not written before its reader {y}"
     assert not red, "a reduction without its factor sub-task"
@@ -189,6 +197,8 @@ def test_adjoint_program_order(tree, variant):
     assert check_backward(22, 20, 8, 4, tree, variant, strip_w=4) > 0
     # nb = 32 with strips of 16 columns: undone as two 8-column halves each, the last tile ragged
     assert check_backward(70, 40, 32, 8, tree, variant, strip_w=16) > 0
+    # ib = 16: the panel-block update adjoints are split into two 8-column halves too
+    assert check_backward(70, 40, 32, 16, tree, variant, strip_w=16) > 0
     # 5 x 2 tiles, inner block = tile
     assert check_backward(20, 8, 4, 4, tree, variant, strip_w=32) > 0
     # three inner blocks per tile, strips of two blocks
