@@ -118,7 +118,7 @@ __host__ __device__ inline Layout layout_update(int nb, int ib, int w, int esize
 // tails, state and gradient of one column block (column-major, ld lp), the top triangles and S.
 struct BwdLayout {
   int lc, lv, lp;
-  int Cs, Cg, Cts, Ctg, V, Tb, W, W2s, W2g, Ms, Mg, Rts, Rtg, Sb, total;
+  int Cs, Cg, Cts, Ctg, V, Tb, W, W2s, W2g, Ms, Mg, Rts, Rtg, Sb, Sc, total;
 };
 __host__ __device__ inline BwdLayout layout_bwd_update(int nb, int ib, int hw, int esize) {
   BwdLayout L{};
@@ -135,7 +135,7 @@ __host__ __device__ inline BwdLayout layout_bwd_update(int nb, int ib, int hw, i
   L.W = o;   o = align4(o + ib * L.lc);
   L.W2s = o; o = align4(o + ib * L.lc);
   L.W2g = o; o = align4(o + ib * L.lc);
-  L.Ms = L.Mg = L.Rts = L.Rtg = L.Sb = -1;
+  L.Ms = L.Mg = L.Rts = L.Rtg = L.Sb = L.Sc = -1;
   L.total = o;
   return L;
 }
@@ -150,6 +150,7 @@ __host__ __device__ inline BwdLayout layout_bwd_panel(int nb, int ib, int esize)
   L.Rts = o; o = align4(o + ib * ib);
   L.Rtg = o; o = align4(o + ib * ib);
   L.Sb = o;  o = align4(o + ib * ib);
+  L.Sc = o;  o = align4(o + (2 * ib + kThreads) * (8 / esize));   // doubles: reciprocals, row-sum partials
   L.Cs = L.Cg = L.Cts = L.Ctg = L.Tb = L.W = L.W2s = L.W2g = -1;
   L.total = o;
   return L;
@@ -1021,8 +1022,27 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
   }
   __syncthreads();
   const int lts = ge ? lp : kb;
-  // per-reflector scalars, computed once by thread 0 (FP64 issues at 2 FMA / clock / SM) and broadcast
-  double* sc = rsc + kWarps;
+  // Per-reflector scalars are formed by warp 0 (FP64 issues at 2 FMA / clock / SM, so a serial chain
+  // of FP64 operations on one thread is slow): the eight warp partials are combined by a 3-level
+  // shuffle, and the divisions by beta_k and beta_k tau_k are replaced by reciprocals formed up front
+  // for all k in parallel (beta_k, the top entry of column k, is not changed before step k).
+  static_assert(kWarps == 8, "warp-partial reductions assume 8 warps");
+  double* sc = rsc + kWarps;       // sc[0..3]: om, tau_bar, -1 / (beta tau), -beta_bar tau
+  double* wbp = rsc + 16;          // per warp: sum_j wsA_j bA_j over its columns
+  double* vbp = rsc + 24;          // per warp: v_bar . v
+  double* rinv = reinterpret_cast<double*>(sm + L.Sc);   // [k]: 1 / beta_k, [kb + k]: 1 / (beta_k tau_k)
+  double* pbuf = rinv + 2 * kb;    // row-sum partials of the column groups 1..G-1
+  // Row update layout: G groups of RP threads, group g takes the later columns j = k + 1 + g (mod G),
+  // so that short blocks keep all warps busy; group 0 owns the row (its v_bar and column k).
+  const int RP = vrows <= 32 ? 32 : (vrows <= 64 ? 64 : (vrows <= 128 ? 128 : kThreads));
+  const int G = kThreads / RP, gq = threadIdx.x / RP, ri = threadIdx.x % RP;
+  for (int k = threadIdx.x; k < kb; k += kThreads) {
+    const double beta = ge ? (double)Ms[k + k * lp] : (double)Rts[k + k * kb];
+    const bool ok = tau[k] != 0.0 && beta != 0.0;
+    rinv[k] = ok ? 1.0 / beta : 0.0;
+    rinv[kb + k] = ok ? 1.0 / (beta * tau[k]) : 0.0;
+  }
+  __syncthreads();
   for (int k = kb - 1; k >= 0; --k) {
     const double t = tau[k];
     if (t == 0.0) continue;
@@ -1031,13 +1051,14 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
     E* ts = ge ? Ms + k : Rts + k;      // top entries of column j at ts[j * lts]
     E* tg = ge ? Mg + k : Rtg + k;
     const double beta = (double)ts[k * lts];
-    const int r = t0 + threadIdx.x;
-    const bool row = r < t1;
-    const double vbtr = row ? (double)ldg(redb + (size_t)k * nb + r) : 0.0;
+    const int r = t0 + ri;
+    const bool row = r < t1, own = row && gq == 0;
+    const double vbtr = own ? (double)ldg(redb + (size_t)k * nb + r) : 0.0;
     const double v = row ? (double)V[r + k * lp] : 0.0;
     // A: |v_tail|^2 (warp partials) and, per later column j, v^T M' and v^T G'
-    const double vvp = warp_sum(v * v);
+    const double vvp = warp_sum(own ? v * v : 0.0);
     if (lane == 0) rsc[warp] = vvp;
+    double wb = 0.0;
     for (int j = k + 1 + warp; j < kb; j += kWarps) {
       double s1 = 0.0, s2 = 0.0;
       for (int rr = t0 + lane; rr < t1; rr += 32) {
@@ -1047,29 +1068,36 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
       }
       s1 = warp_sum(s1);
       s2 = warp_sum(s2);
+      const double wa = (double)ts[j * lts] + s1, ba = (double)tg[j * lts] + s2;
+      wb += wa * ba;
       if (lane == 0) {
-        wsA[j] = (double)ts[j * lts] + s1;
-        bA[j] = (double)tg[j * lts] + s2;
+        wsA[j] = wa;
+        bA[j] = ba;
       }
     }
+    if (lane == 0) wbp[warp] = wb;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double vv = 0.0;
+    if (warp == 0) {
+      double vv = lane < kWarps ? rsc[lane] : 0.0, sw = lane < kWarps ? wbp[lane] : 0.0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) vv += rsc[w];
-      const double om = 1.0 - t * (1.0 + vv);   // a_j = om (v^T M')_j, a_k = om beta (v^T v = 1 + |tail|^2)
-      bA[k] = (double)tg[k * lts];
-      double tb = tbt[k] - beta * om * bA[k];
-      for (int j = k + 1; j < kb; ++j) tb -= wsA[j] * om * bA[j];
-      sc[0] = om;
-      sc[1] = tb;
+      for (int o = kWarps / 2; o > 0; o >>= 1) {
+        vv += __shfl_xor_sync(kFull, vv, o);
+        sw += __shfl_xor_sync(kFull, sw, o);
+      }
+      if (lane == 0) {
+        const double om = 1.0 - t * (1.0 + vv);   // a_j = om (v^T M')_j, a_k = om beta (v^T v = 1 + |tail|^2)
+        const double bk = (double)tg[k * lts];
+        bA[k] = bk;
+        sc[0] = om;
+        sc[1] = tbt[k] - om * (beta * bk + sw);
+      }
     }
     __syncthreads();
     const double om = sc[0];
     double vbar = 0.0;
     if (row) {
       double sG = 0.0, sM = 0.0;
-      for (int j = k + 1; j < kb; ++j) {
+      for (int j = k + 1 + gq; j < kb; j += G) {
         const double g = (double)Mg[r + j * lp];
         const double mpre = (double)Ms[r + j * lp] - t * v * wsA[j];
         sG += g * wsA[j];
@@ -1077,11 +1105,21 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
         Ms[r + j * lp] = (E)mpre;
         Mg[r + j * lp] = (E)(g - t * v * bA[j]);
       }
-      const double mk = -beta * t * v;
-      sM += mk * bA[k];
-      vbar = vbtr - t * (om * sG + sM);
-      Ms[r + k * lp] = (E)mk;
-      Mg[r + k * lp] = (E)(-t * v * bA[k]);
+      if (gq == 0) {
+        const double mk = -beta * t * v;
+        sM += mk * bA[k];
+        Ms[r + k * lp] = (E)mk;
+        Mg[r + k * lp] = (E)(-t * v * bA[k]);
+      }
+      vbar = om * sG + sM;
+      if (gq > 0) pbuf[(gq - 1) * RP + ri] = vbar;
+    }
+    if (G > 1) __syncthreads();
+    if (own) {
+      for (int g = 1; g < G; ++g) vbar += pbuf[(g - 1) * RP + ri];
+      vbar = vbtr - t * vbar;
+    } else {
+      vbar = 0.0;
     }
     if (threadIdx.x < kb - k) {
       const int j = k + threadIdx.x;
@@ -1093,24 +1131,25 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
       }
     }
     const double vbvp = warp_sum(vbar * v);
-    __syncthreads();                    // everyone has read sc / rsc of this step
-    if (lane == 0) rsc[warp] = vbvp;
+    if (lane == 0) vbp[warp] = vbvp;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double vbv = 0.0;
+    if (warp == 0) {
+      double vbv = lane < kWarps ? vbp[lane] : 0.0;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) vbv += rsc[w];
-      const double tb = sc[1];
-      const double g = -vbv / (beta * t);
-      const double alpha = beta * (1.0 - t);
-      const double abar = -tb / beta - g;
-      const double bbar = tb * alpha / (beta * beta) + g;
-      tg[k * lts] = (E)((double)tg[k * lts] - t * bA[k] + abar + bbar * alpha / beta);
-      sc[2] = -1.0 / (beta * t);
-      sc[3] = -bbar * t;
+      for (int o = kWarps / 2; o > 0; o >>= 1) vbv += __shfl_xor_sync(kFull, vbv, o);
+      if (lane == 0) {
+        // alpha = beta (1 - tau): alpha / beta^2 = (1 - tau) / beta, alpha / beta = 1 - tau
+        const double tb = sc[1];
+        const double g = -vbv * rinv[kb + k];
+        const double abar = -tb * rinv[k] - g;
+        const double bbar = tb * (1.0 - t) * rinv[k] + g;
+        tg[k * lts] = (E)((double)tg[k * lts] - t * bA[k] + abar + bbar * (1.0 - t));
+        sc[2] = -rinv[kb + k];
+        sc[3] = -bbar * t;
+      }
     }
     __syncthreads();
-    if (row) Mg[r + k * lp] = (E)((double)Mg[r + k * lp] + vbar * sc[2] + sc[3] * v);
+    if (own) Mg[r + k * lp] = (E)((double)Mg[r + k * lp] + vbar * sc[2] + sc[3] * v);
     __syncthreads();
   }
   if (ge) {
