@@ -999,14 +999,23 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
     Sb[o] = (E)s;
   }
   __syncthreads();
-  for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
-    const int r = o % vrows, k = o / vrows;
-    double s = -(double)Ms[r + k * lp] - (double)V[r + k * lp] * (double)Sb[k * kb + k];
-    for (int l = 0; l < k; ++l) s += (double)V[r + l * lp] * ((double)Sb[k * kb + l] - (double)Sb[l * kb + k]);
-    stg(redb + (size_t)k * nb + r, (E)s);
-  }
+  // tau_bar needs S_kk; then S becomes D in place: D_lk = S_kl - S_lk at [k kb + l] (l < k), D_kk = -S_kk
+  // (a pass writes only entries with k >= l and reads the ones with l < k, so the pass is race-free)
   for (int k = threadIdx.x; k < kb; k += kThreads)
     tbt[k] = tau[k] != 0.0 ? -(double)Sb[k * kb + k] / (tau[k] * tau[k]) : 0.0;
+  __syncthreads();
+  for (int o = threadIdx.x; o < kb * kb; o += kThreads) {
+    const int k = o / kb, l = o % kb;
+    if (l < k) Sb[o] = (E)((double)Sb[o] - (double)Sb[l * kb + k]);
+    else if (l == k) Sb[o] = -Sb[o];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
+    const int r = o % vrows, k = o / vrows;
+    double s = -(double)Ms[r + k * lp];
+    for (int l = 0; l <= k; ++l) s += (double)V[r + l * lp] * (double)Sb[k * kb + l];
+    stg(redb + (size_t)k * nb + r, (E)s);
+  }
   __syncthreads();
   if (ge) {
     load_tile(Ms, 1, lp, X_s, nb, tr, c0, c0, vrows, kb, M_UPPER);
