@@ -985,18 +985,44 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
   const size_t pblk = (size_t)b * nb * ib, sblk = (size_t)nblk * nb * ib + (size_t)b * kb * kb;
   // panel-block update slots of this block: (s - b - 1) pus + h for the later blocks s, pieces h
   const int pu_first = pu0 + (b * nblk - b * (b + 1) / 2) * pus, npu_b = (nblk - 1 - b) * pus;
-  for (int o = threadIdx.x; o < vrows * kb; o += kThreads) {
-    const int k = o % kb, r = o / kb;
-    double s = 0.0;
-    for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + pblk + (size_t)r * kb + k);
-    for (int i = 0; i < npu_b; ++i) s += (double)ldg(part + slot_off[pu_first + i] + (size_t)r * kb + k);
-    Ms[r + k * lp] = (E)s;
+  // (kRedPer independent sums per thread, so that as many loads per slot are in flight; element
+  // (r, k) of P' at r kb + k in every slot)
+  const int nsrc = nu + npu_b, np = vrows * kb;
+  for (int o0 = 0; o0 < np; o0 += kRedPer * kThreads) {
+    double acc[kRedPer];
+#pragma unroll
+    for (int j = 0; j < kRedPer; ++j) acc[j] = 0.0;
+    for (int i = 0; i < nsrc; ++i) {
+      const E* src = part + (i < nu ? slot_off[u0 + i] + pblk : slot_off[pu_first + i - nu]);
+#pragma unroll
+      for (int j = 0; j < kRedPer; ++j) {
+        const int o = o0 + (int)threadIdx.x + j * kThreads;
+        if (o < np) acc[j] += (double)ldg(src + o);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kRedPer; ++j) {
+      const int o = o0 + (int)threadIdx.x + j * kThreads;
+      if (o < np) Ms[o / kb + (o % kb) * lp] = (E)acc[j];
+    }
   }
-  for (int o = threadIdx.x; o < kb * kb; o += kThreads) {
-    double s = 0.0;
-    for (int i = 0; i < nu; ++i) s += (double)ldg(part + slot_off[u0 + i] + sblk + o);
-    for (int i = 0; i < npu_b; ++i) s += (double)ldg(part + slot_off[pu_first + i] + (size_t)nb * kb + o);
-    Sb[o] = (E)s;
+  for (int o0 = 0; o0 < kb * kb; o0 += kRedPer * kThreads) {
+    double acc[kRedPer];
+#pragma unroll
+    for (int j = 0; j < kRedPer; ++j) acc[j] = 0.0;
+    for (int i = 0; i < nsrc; ++i) {
+      const E* src = part + (i < nu ? slot_off[u0 + i] + sblk : slot_off[pu_first + i - nu] + (size_t)nb * kb);
+#pragma unroll
+      for (int j = 0; j < kRedPer; ++j) {
+        const int o = o0 + (int)threadIdx.x + j * kThreads;
+        if (o < kb * kb) acc[j] += (double)ldg(src + o);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kRedPer; ++j) {
+      const int o = o0 + (int)threadIdx.x + j * kThreads;
+      if (o < kb * kb) Sb[o] = (E)acc[j];
+    }
   }
   __syncthreads();
   // tau_bar needs S_kk; then S becomes D in place: D_lk = S_kl - S_lk at [k kb + l] (l < k), D_kk = -S_kk
