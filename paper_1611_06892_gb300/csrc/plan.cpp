@@ -714,7 +714,7 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
   // latency on the critical path.
   const int w = pl.strip_w, split = (split_strips && w >= 16 && w % 2 == 0) ? 2 : 1, wb = w / split;
   bp.strip_w = wb;
-  const int pus = (split_strips && ib >= 16 && ib % 2 == 0) ? 2 : 1;   // BPU column pieces
+  const int pus = (ib >= 16 && ib % 2 == 0) ? 2 : 1;   // BPU column pieces (both storage precisions)
   bp.pu_split = pus;
   auto state_ref = [&](int32_t ref) -> int32_t {   // forward buffer 0 / 1 -> state buffer 2 / 3
     if (ref < 0) return -1;
@@ -788,7 +788,9 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
       const int64_t rows = kind == PK_GE ? nb - (int64_t)blk * ib : (kind == PK_TS ? nb : (int64_t)(blk + 1) * ib);
       if (type == PF) {
         d.op = make_op(BPF, tr, false, 0, blk, kind);
-        wt.push_back(10 * ib2 * rows);
+        // 10 ib^2 rows flops, weighted x2: its per-reflector chain runs at about half the rate of the
+        // block sub-tasks (measured per-sub-task times on a GB300)
+        wt.push_back(20 * ib2 * rows);
         sub.push_back(d);
         fwd_of.push_back(y);
       } else {

@@ -95,9 +95,9 @@ struct BwdPlan {
   int strip_w = 0;                 // column width of the adjoint update strips
   int pu_split = 1;                // BPU sub-tasks per panel-block update (column pieces of ib / pu_split)
 };
-// split_strips: undo each update strip of >= 16 columns, and each panel-block update with ib >= 16,
-// as two column halves with a partial slot each (shorter critical path; worth it when the arithmetic
-// dominates, FP64, not with FP32 storage).  A BPU half has bit 5 of op (notrans) = its half index.
+// split_strips: undo each update strip of >= 16 columns as two column halves with a partial slot each
+// (shorter critical path; worth it when the arithmetic dominates, FP64, not with FP32 storage).  Panel-
+// block updates with ib >= 16 are always undone as two halves (bit 5 of op, notrans, = the half).
 void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips = true);
 
 // Trees and task lists (independent of any device state).

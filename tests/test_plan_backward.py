@@ -86,10 +86,10 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
     assert set(fwd.tolist()) == set(range(len(fprog)))
     split = w // wb
     assert split in (1, 2) and wb * split == w
-    # panel-block updates are undone as two column halves (op bit 5 = half) with the update strips
+    # panel-block updates with ib >= 16 are undone as two column halves (op bit 5 = half)
     pus = 2 if any(fields(t)["typ"] == BPU and fields(t)["half"] for t in prog) else 1
     if nb > ib:
-        assert pus == (2 if split == 2 and ib >= 16 and ib % 2 == 0 else 1)
+        assert pus == (2 if ib >= 16 and ib % 2 == 0 else 1)
     for y in range(len(fprog)):
         ys = [z for z in range(nsub) if fwd[z] == y and fields(prog[z])["typ"] != BRED]
         g = fields(fprog[y])
