@@ -332,31 +332,73 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
         int n0, n1;                      // tail of reflector c
         tail(c, n0, n1);
         double part = 0.0;
-        if (tau != 0.0) {
-          E sum = E(0);
-          for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
-          sum = warp_sum(sum);
-          E* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
-          const E wv = *top + se * sum;
-          __syncwarp();
-          if (lane == 0) *top = *top - (E)tau * wv;
-          const E tw = (E)tau * wv * se;
-          for (int r = t0 + lane; r < t1; r += 32) {
-            const E x = P[r + c * lp] - P[r + jj * lp] * tw;
-            P[r + c * lp] = x;
-            if (r >= n0 && r < n1) part += (double)x * (double)x;
+        if constexpr (sizeof(E) == 4) {
+          // FP32 storage: the squared norm is summed as an unevaluated pair of floats (exact products
+          // by FMA, error-free two-sums: the Sum2 / Dot2 scheme of Ogita, Rump and Oishi, "Accurate
+          // sum and dot product", SIAM J. Sci. Comput. 26, 2005), about 2^-48 relative for these
+          // lengths, and turned into FP64 once per column: the FP64 pipe (2 FMA / clock / SM) would
+          // otherwise take a conversion and an FMA per element on the chain every column waits for.
+          float sh = 0.0f, sl = 0.0f;
+          auto add_sq = [&](float x) {
+            const float p = __fmul_rn(x, x), e = fmaf(x, x, -p);   // __fmul_rn: never contracted into an FMA
+            const float s2 = sh + p, bb = s2 - sh;
+            sl += ((sh - (s2 - bb)) + (p - bb)) + e;
+            sh = s2;
+          };
+          if (tau != 0.0) {
+            float sum = 0.0f;
+            for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
+            sum = warp_sum(sum);
+            float* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
+            const float wv = *top + (float)se * sum;
+            __syncwarp();
+            if (lane == 0) *top = *top - (float)tau * wv;
+            const float tw = (float)tau * wv * (float)se;
+            for (int r = t0 + lane; r < t1; r += 32) {
+              const float x = P[r + c * lp] - P[r + jj * lp] * tw;
+              P[r + c * lp] = x;
+              if (r >= n0 && r < n1) add_sq(x);
+            }
+          } else {
+            for (int r = t0 + lane; r < t1; r += 32)
+              if (r >= n0 && r < n1) add_sq(P[r + c * lp]);
           }
+          for (int r = max(n0, t1) + lane; r < n1; r += 32) add_sq(P[r + c * lp]);   // rows of tail c outside tail jj
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(kFull, sh, o), ol = __shfl_xor_sync(kFull, sl, o);
+            const float s2 = sh + oh, bb = s2 - sh;
+            sl = sl + ol + ((sh - (s2 - bb)) + (oh - bb));
+            sh = s2;
+          }
+          part = (double)sh + (double)sl;
         } else {
-          for (int r = t0 + lane; r < t1; r += 32) {
-            const double x = (double)P[r + c * lp];
-            if (r >= n0 && r < n1) part += x * x;
+          if (tau != 0.0) {
+            E sum = E(0);
+            for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
+            sum = warp_sum(sum);
+            E* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
+            const E wv = *top + se * sum;
+            __syncwarp();
+            if (lane == 0) *top = *top - (E)tau * wv;
+            const E tw = (E)tau * wv * se;
+            for (int r = t0 + lane; r < t1; r += 32) {
+              const E x = P[r + c * lp] - P[r + jj * lp] * tw;
+              P[r + c * lp] = x;
+              if (r >= n0 && r < n1) part += (double)x * (double)x;
+            }
+          } else {
+            for (int r = t0 + lane; r < t1; r += 32) {
+              const double x = (double)P[r + c * lp];
+              if (r >= n0 && r < n1) part += x * x;
+            }
           }
+          for (int r = max(n0, t1) + lane; r < n1; r += 32) {   // rows of tail c outside tail jj
+            const double x = (double)P[r + c * lp];
+            part += x * x;
+          }
+          part = warp_sum(part);
         }
-        for (int r = max(n0, t1) + lane; r < n1; r += 32) {   // rows of tail c outside tail jj
-          const double x = (double)P[r + c * lp];
-          part += x * x;
-        }
-        part = warp_sum(part);
         __syncwarp();
         if (lane == 0) scalars(c, part);
       }
