@@ -246,8 +246,8 @@ int bidiag_apply_p_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nr
  * reverse mode, with a reflector of tau = 0 (a zero column, where the Householder map switches branch)
  * held constant.  The result must come from this handle and is not modified; FP64 results only
  * (FP32 ones: bidiag_band_backward_f32).  Device memory: two copies of the tiled matrix plus partial
- * sums (about nb^2 + nb ib elements per update strip of the reduction), allocated and freed on the
- * handle's stream.  Errors: -2 result, -3 d_abbar NULL, -4 ldab, -5 d_Abar NULL, -6 ldabar, -8 ldarec,
+ * sums (about nb^2 + nb ib elements per update strip of the reduction: 3.5 GB for 4096 x 1024 with
+ * nb = 256), allocated and freed on the handle's stream.  Bitwise deterministic (no atomics).  Errors: -2 result, -3 d_abbar NULL, -4 ldab, -5 d_Abar NULL, -6 ldabar, -8 ldarec,
  * BIDIAG_ERR_UNSUPPORTED when nb / ib need more shared memory than a block has (nb = 256 needs
  * ib <= 32), BIDIAG_ERR_NOMEM, BIDIAG_ERR_CUDA.  Stream-ordered: call bidiag_sync before reading.
  */
@@ -325,17 +325,20 @@ int bidiag_plan_program(int64_t m, int64_t n, int nb, int ib, int tree, int vari
                         int strip_w, int32_t* program, int64_t cap, int64_t* count, int32_t* deps,
                         int64_t dcap, int64_t* ndeps, int32_t* strip_w_used);
 
-/* Host-only query of the adjoint program bidiag_band_backward runs for these arguments (same rules as
- * bidiag_plan_program; strip_w is rounded to a multiple of ib): *count sub-tasks of 8 int32 in queue
+/* Host-only query of the FP64 adjoint program bidiag_band_backward runs for these arguments (same rules
+ * as bidiag_plan_program; strip_w is rounded to a multiple of ib): *count sub-tasks of 8 int32 in queue
  * order (op, x, a, c, tslot, dep_begin, dep_end, flags; op type 9 = undo a panel block, 10 = undo a
- * panel-block update, 11 = undo an update strip, 12 = no-op for a COPY; x = reflector tile of the
- * forward result, a / c = state tiles of the m x n grid, flags = partial slot), fwd[y] = the forward
- * queue position it undoes, *ndeps dependency indices, *nslot_off slot offsets (the last one is the
- * total number of elements) and *npinfo = 4 per panel task (first update slot, number of update
- * slots, first panel-update slot, 0), and *strip_w_used = the column width of its update strips (half
- * the forward's when that is at least 16: each forward strip is undone as two sub-tasks).  Arrays are
- * filled only when their capacity suffices.  Errors as bidiag_plan_program, -10 for a NULL count
- * pointer. */
+ * panel-block update (with ib >= 16 as two column halves, op bit 5 = the half), 11 = undo an update
+ * strip, 12 = gradient of a COPY, 13 = sum the update-strip partials of one panel block over a chunk of
+ * 2048 / ib rows (op bits 8-15 = chunk) into the panel's reduced slot; x = reflector tile of the forward
+ * result, a / c = state tiles of the m x n grid, flags = partial slot), fwd[y] = the forward queue
+ * position it undoes (a type-13 sub-task: the panel block it serves), *ndeps dependency indices,
+ * *nslot_off slot offsets (the last one is the total number of elements) and *npinfo = 4 per panel
+ * task (first update slot, number of update slots, first panel-update slot, reduced slot or -1; panels
+ * with at least 8 update strips have one), and *strip_w_used = the column width of its update strips
+ * (half the forward's when that is at least 16: each forward strip is undone as two sub-tasks).
+ * Arrays are filled only when their capacity suffices.  Errors as bidiag_plan_program, -10 for a NULL
+ * count pointer. */
 int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
                          int strip_w, int32_t* program, int32_t* fwd, int64_t cap, int64_t* count,
                          int32_t* deps, int64_t dcap, int64_t* ndeps, int64_t* slot_off, int64_t scap,

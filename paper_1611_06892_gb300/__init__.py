@@ -252,8 +252,9 @@ def bidiag_plan_program(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
 
 
 def bidiag_plan_backward(m, n, nb, ib, tree, variant, resources=1, strip_w=32):
-    """Adjoint program of a reduction: (sub-tasks (count x 8), forward position of each, dependency
-    array, slot offsets, per-panel slot table (npanels x 4), column width of its update strips)."""
+    """Adjoint program of an FP64 reduction: (sub-tasks (count x 8), forward position of each, dependency
+    array, slot offsets, per-panel slot table (npanels x 4: first update slot, number of update slots,
+    first panel-update slot, reduced slot or -1), column width of its update strips)."""
     lib = load_library()
     cnt, nd, ns, npi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     wb = ctypes.c_int32()
