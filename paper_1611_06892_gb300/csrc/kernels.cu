@@ -663,7 +663,8 @@ __device__ void apply_phase1_tc(const float* V, int lv, int vrows, int kb, const
       acc[2] = Ct[(m0 + g + 8) * lc + n0 + 2 * t];
       acc[3] = Ct[(m0 + g + 8) * lc + n0 + 2 * t + 1];
     }
-    for (int k0 = 0; k0 < vrows; k0 += 8) {
+#pragma unroll 4
+    for (int k0 = 0; k0 < vrows; k0 += 8) {   // the three-product chains of 4 k-steps overlap
       float a[4], b[2];
       a[0] = V[(k0 + t) * lv + m0 + g];
       a[1] = V[(k0 + t) * lv + m0 + g + 8];
@@ -690,6 +691,7 @@ __device__ void apply_phase3_tc(const float* V, int lv, int vrows, int kb, float
     float* c0p = C + (m0 + g) * lc + n0 + 2 * t;
     float* c1p = C + (m0 + g + 8) * lc + n0 + 2 * t;
     float acc[4] = {c0p[0], c0p[1], c1p[0], c1p[1]};
+#pragma unroll 4
     for (int k0 = 0; k0 < kb; k0 += 8) {
       float a[4], b[2];
       a[0] = -V[(m0 + g) * lv + k0 + t];
