@@ -51,7 +51,7 @@ struct BwdDev {
   }
 };
 
-using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int>;
+using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int, int>;   // ..., strip width, esize
 
 // Everything about a batch that depends only on its shapes and options: per-matrix configurations and
 // plans, the storage layout and the merged device program (cached on the handle, reused by later calls
@@ -242,7 +242,7 @@ int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, in
              std::shared_ptr<PlanDev>* out) {
   const int64_t R = resources_of(h, nb, w, esize);
   const bool debug = h->debug_unset != 0;
-  PlanKey key{m, n, nb, ib, tree, variant, R, w};
+  PlanKey key{m, n, nb, ib, tree, variant, R, w, esize};
   if (!debug) {
     auto it = h->cache.find(key);
     if (it != h->cache.end()) {
@@ -252,7 +252,7 @@ int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, in
   }
   auto pd = std::make_shared<PlanDev>();
   try {
-    bd::build_plan(pd->plan, m, n, nb, ib, tree, variant, R, w);
+    bd::build_plan(pd->plan, m, n, nb, ib, tree, variant, R, w, esize);
   } catch (const std::bad_alloc&) {
     return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning");
   } catch (const std::exception& e) {
@@ -697,7 +697,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
           const int64_t R = resources_of(h, o.nb, o.w, esize);
           if (o.variant == BIDIAG_AUTO_VARIANT) o.variant = bd::choose_variant(p, q, o.tree, R, nullptr, nullptr);
           o.pd = std::make_shared<PlanDev>();
-          bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w);
+          bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w, esize);
           dump_tasks(o.pd->plan.tasks, o.pd->dump);
         } catch (const std::bad_alloc&) {
           bad[(size_t)b] = BIDIAG_ERR_NOMEM;

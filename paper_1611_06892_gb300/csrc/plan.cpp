@@ -505,7 +505,8 @@ inline int32_t make_op(int type, bool tr, bool notrans, int strip, int blk, int 
 
 }  // namespace
 
-void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t R, int strip_w) {
+void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t R, int strip_w,
+                int esize) {
   pl.m = m;
   pl.n = n;
   pl.nb = nb;
@@ -596,7 +597,10 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
         wr.push_back(it.t(slot, b));
         const int64_t rows = kind == PK_GE ? nb - (int64_t)b * ib : (kind == PK_TS ? nb : (int64_t)(b + 1) * ib);
         d.op = make_op(PF, lq, false, 0, b, kind);
-        last = g.add(d, 3 * ib2 * rows * 4, rd, wr, -1);
+        // priority weights: Table 1 flops, scaled by the measured time per flop of each sub-task kind
+        // relative to the update strips (per-sub-task traces at 8192^2 on a GB300: with FP32 storage
+        // the panel chain is relatively twice as slow; panel-block updates 1.5x in both precisions)
+        last = g.add(d, (esize == 4 ? 2 : 1) * 12 * ib2 * rows, rd, wr, -1);
         // PU(b, s)
         for (int s = b + 1; s < nblk; ++s) {
           rd.clear();
@@ -617,7 +621,7 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
           }
           rd.push_back(it.t(slot, b));
           d.op = make_op(PU, lq, false, s, b, kind);
-          last = g.add(d, 4 * ib2 * rows, rd, wr, -1);
+          last = g.add(d, 6 * ib2 * rows, rd, wr, -1);
         }
       }
       panel_last[x] = last;
