@@ -56,7 +56,7 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 TF32_RATIO = 1.1 / 2.25
 # DRAM bytes (read + write) of one executor launch on the 8192^2 workload, from the ncu capture
 # summarised under profiles/ (to be reset to None whenever the kernel changes).
-EXEC_TRAFFIC_BYTES = 11574839552 + 11569368832
+EXEC_TRAFFIC_BYTES = 11551265280 + 11528699648
 CPU_SAMPLE_SECONDS = 12.0
 
 
