@@ -49,26 +49,102 @@ WORKLOADS = {
                                "+ adjoint (dL/dA from a N(0,1) band gradient W, L = <W, B>)"),
 }
 # FP64 peak of the GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA/clock/SM (4 flops) x
-# 2070 MHz = 1258.6 GFLOP/s (a DFMA loop measured 1.20 TFLOP/s, cuBLAS DGEMM 1.10, FP64 MMA 1.05).
-FP64_PEAK_GFLOPS = 152 * 4 * 2.070
-# Split-FP32 form: the updates are three TF32 tensor-core products per useful product.  TF32 dense peak
-# = measured bf16 peak x nominal TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s); one useful flop costs three.
-TF32_RATIO = 1.1 / 2.25
-# DRAM bytes (read + write) of one executor launch on the 8192^2 workload, from the ncu capture
-# summarised under profiles/ (to be reset to None whenever the kernel changes).
-EXEC_TRAFFIC_BYTES = 11551265280 + 11528699648
+# 2070 MHz = 1258.6 GFLOP/s.  Reported beside the measured peaks; the roofline divides by the measured
+# DFMA-loop rate (bidiag_measure_fp64_peaks), the FP64 unit the reduction's contractions run on.
+FP64_DERIVED_GFLOPS = 152 * 4 * 2.070
+# DRAM bytes (read + write) of one executor launch on the 8192^2 Auto workload, from the ncu capture
+# summarised under profiles/ (None until the current kernel has been captured).
+EXEC_TRAFFIC_BYTES = None
 CPU_SAMPLE_SECONDS = 12.0
 
 
-def tf32_split_peak_gflops():
-    """TF32 tensor peak (measured bf16 burst x 1.1/2.25) over the three products per useful flop."""
-    bf16 = 1926.3
+def measure_peaks(G, torch, local, f32):
+    """Measured denominators, taken on this GPU before the timed region: the FP64 DFMA and FP64 MMA
+    loops of the library's probe, cuBLAS DGEMM (torch.matmul, FP64, 4096^3) and, for the split-precision
+    form, cuBLAS TF32 (torch.matmul, FP32 with TF32 allowed, 8192^3); best of several runs each."""
+    out = {}
+    fma, mma = G.bidiag_measure_fp64_peaks(local, None)
+    out["fp64_dfma_loop_gflops"] = fma
+    out["fp64_mma_loop_gflops"] = mma
+    out["fp64_derived_gflops"] = FP64_DERIVED_GFLOPS
+
+    def best_rate(dtype, nsz, reps):
+        a = torch.randn(nsz, nsz, dtype=dtype, device=f"cuda:{local}")
+        b = torch.randn(nsz, nsz, dtype=dtype, device=f"cuda:{local}")
+        best = 0.0
+        for r in range(reps + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                best = max(best, 2.0 * nsz ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        del a, b
+        return best
+
+    out["fp64_dgemm_gflops"] = best_rate(torch.float64, 4096, 3)
+    if f32:
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        try:
+            out["tf32_gemm_gflops"] = best_rate(torch.float32, 8192, 10)
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
+def roofline_peak(peaks, f32):
+    """(peak GFLOP/s, bound, source) of the reduction's executor: FP64 storage against the measured
+    DFMA loop; FP32 storage against the measured TF32 GEMM rate over the three TF32 products that
+    make one useful product."""
+    if f32:
+        return (peaks["tf32_gemm_gflops"] / 3.0, "tensor",
+                "measured: cuBLAS TF32 GEMM 8192^3 (torch.matmul) / 3 products per useful flop")
+    return (peaks["fp64_dfma_loop_gflops"], "alu",
+            "measured: FP64 DFMA loop (bidiag_measure_fp64_peaks), all SMs")
+
+
+def cpu_info():
+    """Host threads the oracle may use (this process's CPU affinity) and the CPU model name."""
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            bf16 = json.load(fh).get("bf16_tflops", bf16)
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
         pass
-    return bf16 * TF32_RATIO * 1e3 / 3.0
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"threads": threads, "model": model or platform.processor() or platform.machine()}
+
+
+def cpu_env(threads):
+    """Environment of an oracle subprocess: its BLAS may use `threads` threads."""
+    t = str(threads)
+    return dict(os.environ, OPENBLAS_NUM_THREADS=t, OMP_NUM_THREADS=t, MKL_NUM_THREADS=t)
+
+
+def cpu_baseline_entry(value, info, r, sample):
+    """cpu_baseline object: BLAS threads allowed, the CPU time / wall time the oracle actually used,
+    the CPU model and the sample it ran on."""
+    eff = r.get("cpu_seconds", 0.0) / r["seconds"] if r.get("seconds") else None
+    return {"value": value, "unit": "TFLOP/s", "cores": info["threads"],
+            "cores_effective": round(eff, 2) if eff is not None else None, "cpu_model": info["model"],
+            "kind": "oracle", "sample": sample}
 
 
 TABLE1_WEIGHTS = (4, 6, 6, 12, 2, 6, 0)   # GEQRT, UNMQR, TSQRT, TSMQR, TTQRT, TTMQR, COPY in nb^3/3 flops
@@ -199,7 +275,7 @@ def variant_code(v):
 
 
 def cpu_sample(path, w, tree, seconds, max_tasks=None):
-    """Times the oracle (single BLAS thread) on the first tasks of the workload's task list."""
+    """Times the oracle on the first tasks of the workload's task list (wall and process CPU time)."""
     import numpy as np
 
     from oracle import bidiag as OB
@@ -218,37 +294,37 @@ def cpu_sample(path, w, tree, seconds, max_tasks=None):
     st = OB.new_state(np.asarray(A), w["nb"], w["ib"], treec, variant, resources=w["resources"])
     units = 0
     done = 0
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for idx, t in enumerate(st["tasks"]):
         OB.run_tasks(st, [(idx, t)])
         units += T.WEIGHT[t[0]]
         done += 1
         if time.perf_counter() - t0 > seconds or (max_tasks and done >= max_tasks):
             break
-    el = time.perf_counter() - t0
+    el, cpu = time.perf_counter() - t0, time.process_time() - c0
     flops = units * w["nb"] ** 3 / 3.0
-    return {"tasks": done, "total_tasks": len(st["tasks"]), "flops": flops, "seconds": el}
+    return {"tasks": done, "total_tasks": len(st["tasks"]), "flops": flops, "seconds": el, "cpu_seconds": cpu}
 
 
-def run_cpu_sample_subprocess(A_host_np, w, tree, seconds, max_tasks=None):
+def run_cpu_sample_subprocess(A_host_np, w, tree, seconds, max_tasks=None, threads=None):
     import numpy as np
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "A.npy")
         np.save(path, A_host_np)
-        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        env = cpu_env(threads or cpu_info()["threads"])
         cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", path, "--workload", w["name"],
                "--tree", tree, "--cpu-seconds", str(seconds), "--auto-resources", str(w["resources"]),
                "--variant", str(w.get("variant_used", w["variant"]))]
         if max_tasks:
             cmd += ["--cpu-max-tasks", str(max_tasks)]
-        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=1800)
         if out.returncode != 0:
             raise RuntimeError(out.stderr[-2000:])
         return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def cpu_sample_batch(path, seconds):
-    """Times the oracle (single BLAS thread) on the first matrices of the batch with their tuned configs."""
+    """Times the oracle on the first matrices of the batch with their tuned configs."""
     import numpy as np
 
     from oracle import bidiag as OB
@@ -256,7 +332,7 @@ def cpu_sample_batch(path, seconds):
     data = np.load(path)
     flops = 0.0
     done = 0
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     k = 0
     while f"A{k}" in data.files:
         A = data[f"A{k}"]
@@ -267,12 +343,13 @@ def cpu_sample_batch(path, seconds):
         k += 1
         if time.perf_counter() - t0 > seconds:
             break
-    return {"tasks": done, "total_tasks": 512, "flops": flops, "seconds": time.perf_counter() - t0}
+    return {"tasks": done, "total_tasks": 512, "flops": flops, "seconds": time.perf_counter() - t0,
+            "cpu_seconds": time.process_time() - c0}
 
 
 def reference_batched(args, w, base):
     """The oracle on the batch: each step reduces the next matrices of the batch (nb = 128, ib = 32,
-    FlatTS, the variant with the shorter critical path) for a bounded time, single BLAS thread."""
+    FlatTS, the variant with the shorter critical path) for a bounded time, BLAS on the host's cores."""
     import numpy as np
 
     from oracle import trees as OT
@@ -280,6 +357,7 @@ def reference_batched(args, w, base):
 
     shapes = batch_shapes(w["seeds"][0])
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    info = cpu_info()
     res = []
     k = 0
     with tempfile.TemporaryDirectory() as td:
@@ -294,22 +372,21 @@ def reference_batched(args, w, base):
                 sample[f"A{j}"] = inputs.gaussian(m, n, seed=w["seeds"][0] + k + j)
                 sample[f"cfg{j}"] = np.array([128, 32, OT.FLATTS, v])
             np.savez(path, **sample)
-            env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
             out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-batch", path,
-                                  "--cpu-seconds", str(per_step)], env=env, capture_output=True, text=True,
-                                 timeout=600, check=True)
+                                  "--cpu-seconds", str(per_step)], env=cpu_env(info["threads"]),
+                                 capture_output=True, text=True, timeout=600, check=True)
             r = json.loads(out.stdout.strip().splitlines()[-1])
             k += r["tasks"]
             res.append(r)
     timed = res[args.warmup:]
     val = sum(r["flops"] for r in timed) / sum(r["seconds"] for r in timed) / 1e12
     sample = (f"{sum(r['tasks'] for r in timed)} of the 512 matrices over {len(timed)} steps "
-              f"(~{per_step:.0f} s each), nb 128, FlatTS, single BLAS thread")
+              f"(~{per_step:.0f} s each), nb 128, FlatTS")
+    tot = {"seconds": sum(r["seconds"] for r in timed), "cpu_seconds": sum(r["cpu_seconds"] for r in timed)}
     line = dict(base, impl="reference", value=val, ms_per_step=1e3 * statistics.mean(r["seconds"] for r in timed),
-                cpu_baseline={"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+                cpu_baseline=cpu_baseline_entry(val, info, tot, sample),
                 e2e={"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 gpu_launches=0)
-    line["config"] = dict(line["config"], workload=w["desc"] + ", FP64")
     print(json.dumps(line), flush=True)
     return 0
 
@@ -325,7 +402,7 @@ def cpu_sample_grad(path, seconds):
     data = np.load(path)
     A, W = data["A"], data["W"]
     nb, ib = (int(x) for x in data["cfg"])
-    done, t0 = 0, time.perf_counter()
+    done, t0, c0 = 0, time.perf_counter(), time.process_time()
     while True:
         res = OB.bidiag_band(A, nb, ib, OT.GREEDY, OT.BIDIAG)
         OA.band_vjp(res, W)
@@ -333,12 +410,13 @@ def cpu_sample_grad(path, seconds):
         if time.perf_counter() - t0 > seconds:
             break
     m, n = A.shape
-    return {"tasks": done, "flops": done * metric_flops(m, n), "seconds": time.perf_counter() - t0, "m": m, "n": n}
+    return {"tasks": done, "flops": done * metric_flops(m, n), "seconds": time.perf_counter() - t0,
+            "cpu_seconds": time.process_time() - c0, "m": m, "n": n}
 
 
 def grad_cpu_leg(w, seconds):
     """Bounded oracle sample for the differentiation workload: the leading 1024 x 256 block with
-    nb = 64 (the same 4:1 shape and 16 x 4 tile grid), forward + adjoint, single BLAS thread."""
+    nb = 64 (the same 4:1 shape and 16 x 4 tile grid), forward + adjoint, BLAS on the host's cores."""
     import numpy as np
 
     from paper_1611_06892_gb300 import inputs
@@ -348,12 +426,12 @@ def grad_cpu_leg(w, seconds):
     with tempfile.TemporaryDirectory() as td:
         path = os.path.join(td, "grad.npz")
         np.savez(path, A=A, W=W, cfg=np.array([nb, ib]))
-        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
         out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-grad", path, "--cpu-seconds",
-                              str(seconds)], env=env, capture_output=True, text=True, timeout=900, check=True)
+                              str(seconds)], env=cpu_env(cpu_info()["threads"]), capture_output=True, text=True,
+                             timeout=900, check=True)
     r = json.loads(out.stdout.strip().splitlines()[-1])
     r["sample"] = (f"{r['tasks']} forward + adjoint passes of the oracle on the leading {m} x {n} block "
-                   f"(nb {nb}, ib {ib}, Greedy; {r['seconds']:.1f} s), single BLAS thread")
+                   f"(nb {nb}, ib {ib}, Greedy; {r['seconds']:.1f} s)")
     return r
 
 
@@ -369,13 +447,10 @@ def run_grad(args, w, base, config, world, rank, local, device, G, torch):
     gen = torch.Generator(device=device)
     gen.manual_seed(w["seeds"][1] + 1000 * rank)
     W = torch.randn((n, nb + 1), dtype=dt, device=device, generator=gen).t()
-    tree = "greedy" if args.tree == "auto" else args.tree
-    config = dict(config, workload=w["desc"].replace("FP64", "FP32 storage (3xTF32 updates)") if f32 else w["desc"],
-                  tree=tree, l2=f"input {m * n * A.element_size() / 2**20:.0f} MiB (the adjoint's working "
-                  "set, 3 copies of A plus partial sums, exceeds the 129 MB L2; no flush)")
-    config.pop("auto_resources", None)
+    tree = config["tree"]
     h = G.Handle(device=local)
     h.set_option(G.OPT_TIMING, 1)
+    peaks = measure_peaks(G, torch, local, f32)
 
     def step():
         r = h.band(A, nb, ib, tree, w["variant"])
@@ -429,23 +504,19 @@ def run_grad(args, w, base, config, world, rank, local, device, G, torch):
     alg = table1_flops(G, m, n, nb, G.TREES[tree], G.VARIANTS[w["variant"]], 1)
     bwd_flops = 3.0 * alg
     achieved = bwd_flops / (bwd_ms * 1e-3) / 1e9
-    if f32:
-        peak, bound, src = tf32_split_peak_gflops(), "tensor", "measured bf16 x 1.1/2.25 (TF32) / 3"
-    else:
-        peak, bound, src = FP64_PEAK_GFLOPS, "alu", "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
+    peak, bound, src = roofline_peak(peaks, f32)
     line = dict(base, config=config, dtype="f32" if f32 else "f64", value=value, ms_per_step=ms_per_step,
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": m * n * A.element_size(), "d2h_bytes_per_step": m * n * A.element_size()},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                           "frac": achieved / peak, "traffic": None,
                           "kernel": "exec_kernel adjoint instantiation (reverse sweep), 3 x the forward's Table 1 flops",
-                          "algorithmic_flops": bwd_flops, "peak_source": src},
+                          "algorithmic_flops": bwd_flops, "peak_source": src, "peaks_measured": peaks},
                 forward_exec_ms=fwd_ms, backward_exec_ms=bwd_ms, backward_over_forward=bwd_ms / fwd_ms,
                 gpu_launches=(7 if w["variant"] == "bidiag" else 8) * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
         r = grad_cpu_leg(w, CPU_SAMPLE_SECONDS)
-        line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
-                                "kind": "oracle", "sample": r["sample"]}
+        line["cpu_baseline"] = cpu_baseline_entry(r["flops"] / r["seconds"] / 1e12, cpu_info(), r, r["sample"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
@@ -463,13 +534,9 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     gen.manual_seed(w["seeds"][0] + 1000 * rank)
     As = [torch.randn(n, m, dtype=dt, device=device, generator=gen).t() for m, n in shapes]
     flops = sum(metric_flops(m, n) for m, n in shapes)
-    config = dict(config, workload=w["desc"] + (", FP32 storage (3xTF32 updates)" if f32 else ", FP64"),
-                  count=len(shapes), m="U[64,1024]", n="U[32,m]", nb="autotuned", ib="autotuned",
-                  tree="autotuned (FlatTS)", variant="critical path",
-                  l2="inputs 1.1 GB total > 129 MB L2 (no flush needed)")
-    config.pop("auto_resources", None)
     h = G.Handle(device=local)
     h.set_option(G.OPT_TIMING, 1)
+    peaks = measure_peaks(G, torch, local, f32)
 
     def step():
         res = h.band_batched(As)
@@ -518,17 +585,14 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     cfgs = [G.bidiag_autotune(m, n, torch.cuda.get_device_properties(local).multi_processor_count) for m, n in shapes]
     alg = sum(table1_flops(G, m, n, c[0], c[2], c[3], 1) for (m, n), c in zip(shapes, cfgs))
     achieved = alg / (exec_mean * 1e-3) / 1e9
-    if f32:
-        peak, bound, src = tf32_split_peak_gflops(), "tensor", "measured bf16 x 1.1/2.25 (TF32) / 3"
-    else:
-        peak, bound, src = FP64_PEAK_GFLOPS, "alu", "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
+    peak, bound, src = roofline_peak(peaks, f32)
     line = dict(base, config=config, dtype="f32" if f32 else "f64", value=value, ms_per_step=ms_per_step,
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                           "frac": achieved / peak, "traffic": None,
                           "kernel": "exec_kernel (persistent dataflow executor, whole batch)",
-                          "algorithmic_flops": alg, "peak_source": src},
+                          "algorithmic_flops": alg, "peak_source": src, "peaks_measured": peaks},
                 exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
         with tempfile.TemporaryDirectory() as td:
@@ -538,20 +602,39 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
                 sample[f"A{k}"] = As[k].double().cpu().numpy()
                 sample[f"cfg{k}"] = np.array(cfgs[k])
             np.savez(path, **sample)
-            env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+            info = cpu_info()
             out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-batch", path,
-                                  "--cpu-seconds", str(CPU_SAMPLE_SECONDS)], env=env, capture_output=True, text=True,
-                                 timeout=600)
+                                  "--cpu-seconds", str(CPU_SAMPLE_SECONDS)], env=cpu_env(info["threads"]),
+                                 capture_output=True, text=True, timeout=600)
             if out.returncode == 0:
                 r = json.loads(out.stdout.strip().splitlines()[-1])
-                line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
-                                        "kind": "oracle",
-                                        "sample": f"first {r['tasks']} of 512 matrices with their tuned "
-                                                  f"configurations ({r['seconds']:.1f} s), single BLAS thread"}
+                line["cpu_baseline"] = cpu_baseline_entry(
+                    r["flops"] / r["seconds"] / 1e12, info, r,
+                    f"first {r['tasks']} of 512 matrices with their tuned configurations ({r['seconds']:.1f} s)")
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()
     return 0
+
+
+def workload_config(args, w, config):
+    """The `config` object of both arms (ours and the reference) for the batched and the
+    differentiation workloads; the single-matrix workloads keep the generic one."""
+    f32 = args.precision == "f32"
+    if w["kind"] == "grad":
+        m, n = w["m"], w["n"]
+        config = dict(config, workload=w["desc"].replace("FP64", "FP32 storage (3xTF32 updates)") if f32 else w["desc"],
+                      tree="greedy" if args.tree == "auto" else args.tree,
+                      l2=f"input {m * n * (4 if f32 else 8) / 2**20:.0f} MiB (the adjoint's working set, 3 copies "
+                         "of A plus partial sums, exceeds the 129 MB L2; no flush)")
+        config.pop("auto_resources", None)
+    elif w["kind"] == "batch":
+        config = dict(config, workload=w["desc"] + (", FP32 storage (3xTF32 updates)" if f32 else ", FP64"),
+                      count=512, m="U[64,1024]", n="U[32,m]", nb="autotuned", ib="autotuned",
+                      tree="autotuned", variant="critical path",
+                      l2="inputs 1.1 GB total > 129 MB L2 (no flush needed)")
+        config.pop("auto_resources", None)
+    return config
 
 
 def main():
@@ -616,6 +699,7 @@ def main():
               "tree": args.tree, "variant": w["variant"], "auto_resources": w["resources"],
               "l2": f"input {m * n * 8 / 2**20:.0f} MiB > 129 MB L2 (no flush needed)" if m * n * 8 > 129e6
               else "input smaller than L2"}
+    config = workload_config(args, w, config)
     base = {"metric": "GE2BND TFLOP/s (4mn^2 - 4n^3/3 flops)", "unit": "TFLOP/s", "higher_is_better": True,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if f32 else "f64", "data": "synthetic", "config": config}
@@ -630,9 +714,9 @@ def main():
         per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
         res = [grad_cpu_leg(w, per_step) for _ in range(args.warmup + args.steps)][args.warmup:]
         val = sum(r["flops"] for r in res) / sum(r["seconds"] for r in res) / 1e12
+        tot = {"seconds": sum(r["seconds"] for r in res), "cpu_seconds": sum(r["cpu_seconds"] for r in res)}
         line = dict(base, impl="reference", value=val, ms_per_step=1e3 * statistics.mean(r["seconds"] for r in res),
-                    cpu_baseline={"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                                  "sample": res[0]["sample"]},
+                    cpu_baseline=cpu_baseline_entry(val, cpu_info(), tot, res[0]["sample"]),
                     e2e={"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                     gpu_launches=0)
         print(json.dumps(line), flush=True)
@@ -648,13 +732,18 @@ def main():
         per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
         if args.cpu_seconds != CPU_SAMPLE_SECONDS:
             per_step = args.cpu_seconds
-        res = [run_cpu_sample_subprocess(A_host, w, args.tree, per_step) for _ in range(args.warmup + args.steps)]
+        info = cpu_info()
+        full = w["name"] == "square512"      # the oracle's size: every step is the whole reduction
+        res = [run_cpu_sample_subprocess(A_host, w, args.tree, 1e9 if full else per_step, threads=info["threads"])
+               for _ in range(args.warmup + args.steps)]
         timed = res[args.warmup:]
         val = sum(r["flops"] for r in timed) / sum(r["seconds"] for r in timed) / 1e12
-        sample = (f"first {timed[0]['tasks']} of {timed[0]['total_tasks']} tasks of the task list "
-                  f"(~{per_step:.0f} s each step), single BLAS thread")
+        sample = (f"the whole task list ({timed[0]['total_tasks']} tasks) each step" if full else
+                  f"first {timed[0]['tasks']} of {timed[0]['total_tasks']} tasks of the task list "
+                  f"(~{per_step:.0f} s each step)")
+        tot = {"seconds": sum(r["seconds"] for r in timed), "cpu_seconds": sum(r["cpu_seconds"] for r in timed)}
         line = dict(base, impl="reference", value=val, ms_per_step=1e3 * statistics.mean(r["seconds"] for r in timed),
-                    cpu_baseline={"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+                    cpu_baseline=cpu_baseline_entry(val, info, tot, sample),
                     e2e={"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                     gpu_launches=0)
         print(json.dumps(line), flush=True)
@@ -677,6 +766,7 @@ def main():
     h.set_option(G.OPT_TIMING, 1)
     h.set_option(G.OPT_AUTO_RESOURCES, w["resources"])
     stream = h.stream
+    peaks = measure_peaks(G, torch, local, f32)
 
     vcode = variant_code(w["variant"])
 
@@ -731,29 +821,31 @@ def main():
     exec_mean = statistics.mean(exec_ms)
     alg = table1_flops(G, m, n, nb, G.TREES[args.tree], w.get("variant_used", vcode), w["resources"])
     achieved = alg / (exec_mean * 1e-3) / 1e9
-    if f32:
-        peak, bound, unit = tf32_split_peak_gflops(), "tensor", "GFLOP/s"
-        peak_src = "measured bf16 x 1.1/2.25 (TF32) / 3 products per useful flop"
-    else:
-        peak, bound, unit = FP64_PEAK_GFLOPS, "alu", "GFLOP/s"
-        peak_src = "derived: 152 SMs x 4 FP64 flops/clk x 2070 MHz"
-    config["variant_used"] = w.get("variant_used")       # the library's code (4 + s: three-step, split s)
+    peak, bound, peak_src = roofline_peak(peaks, f32)
+    unit = "GFLOP/s"
     line = dict(base, value=value, ms_per_step=ms_per_step,
+                variant_used=w.get("variant_used"),       # the library's code (4 + s: three-step, split s)
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": m * n * A.element_size(),
                      "d2h_bytes_per_step": (nb + 1) * n * A.element_size()},
                 roofline={"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                           "frac": achieved / peak, "traffic": EXEC_TRAFFIC_BYTES if (not f32 and w["name"] == "square8192" and args.tree == "auto") else None,
                           "kernel": "exec_kernel (persistent dataflow executor)", "algorithmic_flops": alg,
-                          "peak_source": peak_src},
+                          "peak_source": peak_src, "peaks_measured": peaks},
                 exec_ms=exec_ms, gpu_launches=3 * args.steps, clocks=clocks)
     if world == 1 and rank == 0 and not args.no_cpu and not f32:
         A_np = A.cpu().numpy()
-        r = run_cpu_sample_subprocess(A_np, w, args.tree, CPU_SAMPLE_SECONDS)
-        line["cpu_baseline"] = {"value": r["flops"] / r["seconds"] / 1e12, "unit": "TFLOP/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"first {r['tasks']} of {r['total_tasks']} tasks of the same task list "
-                                          f"({r['seconds']:.1f} s), single BLAS thread"}
+        info = cpu_info()
+        full = w["name"] == "square512"      # the oracle's size: timed on the whole reduction
+        r = run_cpu_sample_subprocess(A_np, w, args.tree, 1e9 if full else CPU_SAMPLE_SECONDS, threads=info["threads"])
+        sample = (f"the whole reduction ({r['total_tasks']} tasks, {r['seconds']:.1f} s)" if full else
+                  f"first {r['tasks']} of {r['total_tasks']} tasks of the same task list ({r['seconds']:.1f} s)")
+        line["cpu_baseline"] = cpu_baseline_entry(r["flops"] / r["seconds"] / 1e12, info, r, sample)
+        if full:
+            r1 = run_cpu_sample_subprocess(A_np, w, args.tree, 1e9, threads=1)
+            line["cpu_baseline_one_thread"] = cpu_baseline_entry(
+                r1["flops"] / r1["seconds"] / 1e12, dict(info, threads=1), r1,
+                f"the whole reduction, one BLAS thread ({r1['seconds']:.1f} s)")
     if rank == 0:
         print(json.dumps(line), flush=True)
     h.close()

@@ -187,8 +187,10 @@ int bidiag_band_host(bidiag_handle h, int64_t m, int64_t n, const double* h_A, i
  * is enqueued (a 512 x 512 BiDiag with nb = 64 needs about 3.3 MiB).  No cudaMalloc, cudaFree or
  * allocating library routine is called; the task program is planned in host memory.
  *
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and keeps
- * it; make that first call before any stream capture on the device.  All calls share the one array
+ * The first call in each CUDA context (normally once per device, in its primary context) looks up
+ * the array's device address (cudaGetSymbolAddress) and keeps it for that context; a context made
+ * after cudaDeviceReset, or another context the caller makes current, gets a lookup of its own.  Make
+ * that first call before any stream capture on the device.  All calls share the one array
  * and each call leaves its contents behind, so calls whose work overlaps on the GPU (other threads or
  * other streams at the same time) race and corrupt each other's results: serialise them.  The call
  * enqueues the work, waits for the stream and returns the device-side status (BIDIAG_OK,
@@ -344,6 +346,15 @@ int bidiag_plan_backward(int64_t m, int64_t n, int nb, int ib, int tree, int var
                          int32_t* deps, int64_t dcap, int64_t* ndeps, int64_t* slot_off, int64_t scap,
                          int64_t* nslot_off, int32_t* pinfo, int64_t pcap, int64_t* npinfo,
                          int32_t* strip_w_used);
+
+/* Measurement support (the paper has no counterpart; no reduction uses it): the FP64 throughput of
+ * the GPU `device`, the denominators of the FP64 reduction's roofline.  *gflops_fma receives the rate of
+ * a loop of independent DFMA chains (the unit the reduction's contractions run on), *gflops_mma that of
+ * a loop of mma.sync m8n8k4 f64 (the ISA's FP64 tensor-core path), both best of five launches of a few
+ * tens of milliseconds on cuda_stream (NULL = legacy default stream), in GFLOP/s.  Allocates and frees a
+ * small device buffer; makes `device` current.  Errors: -1 device, -3 / -4 NULL outputs,
+ * BIDIAG_ERR_NOMEM, BIDIAG_ERR_CUDA. */
+int bidiag_measure_fp64_peaks(int device, void* cuda_stream, double* gflops_fma, double* gflops_mma);
 
 #ifdef __cplusplus
 }

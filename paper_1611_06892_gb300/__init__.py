@@ -84,6 +84,7 @@ def load_library(path=LIB_PATH):
         "bidiag_sync": (cint, [vp]),
         "bidiag_last_exec_ms": (cint, [vp, P(ctypes.c_float)]),
         "bidiag_trace": (cint, [vp, P(i64), i64, P(i64)]),
+        "bidiag_measure_fp64_peaks": (cint, [cint, vp, P(ctypes.c_double), P(ctypes.c_double)]),
         "bidiag_last_error": (ctypes.c_char_p, [vp]),
         "bidiag_result_free": (cint, [vp]),
         "bidiag_destroy": (cint, [vp]),
@@ -150,6 +151,15 @@ def bidiag_band_host(h, m, n, h_A, lda, nb, ib, tree, variant, h_ab, ldab, keep=
 def bidiag_band_noalloc(m, n, d_A, lda, nb, ib, tree, variant, d_ab, ldab, stream=None):
     """Reduction that allocates no device memory (fixed static scratch); returns the status code."""
     return load_library().bidiag_band_noalloc(m, n, d_A, lda, nb, ib, tree, variant, d_ab, ldab, stream)
+
+
+def bidiag_measure_fp64_peaks(device=0, stream=None):
+    """Measured FP64 rates of the GPU (GFLOP/s): (DFMA loop, mma.sync m8n8k4 f64 loop)."""
+    fma, mma = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().bidiag_measure_fp64_peaks(device, stream, ctypes.byref(fma), ctypes.byref(mma))
+    if rc != OK:
+        raise BidiagError(rc, "bidiag_measure_fp64_peaks failed")
+    return fma.value, mma.value
 
 
 def bidiag_sync(h):

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libbidiag.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "kernels.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "peak.cu"]
 
 
 def _nvcc():

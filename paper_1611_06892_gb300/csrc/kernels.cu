@@ -252,18 +252,6 @@ __device__ __forceinline__ E warp_sum(E v) {
   return v;
 }
 
-// Sum over the CTA, the same value (same order) in every thread.
-__device__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) s += red[w];
-  return s;
-}
-
 enum PanelMode : int { PM_GE = 0, PM_TS = 1, PM_TT = 2 };
 
 // Unblocked factorization of kb panel columns held in P (ld lp).
@@ -1302,7 +1290,12 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       int bad = 0;
       for (int d = t.dep_begin + lane; d < t.dep_end; d += 32) {
         const int dep = prm.deps[d];
-        if (dep < 0 || dep >= prm.nflags) { bad = 2; break; }
+        if (dep < 0 || dep >= prm.nflags) {
+          // record it now, so that lanes spinning on other dependencies see the error word and stop
+          if (atomicCAS(prm.err, 0, DERR_BADTASK) == 0) { prm.err[1] = idx; prm.err[2] = -1; }
+          bad = 2;
+          break;
+        }
         const uint64_t t0 = gtime();
         while (ld_acquire(prm.done + dep) == 0) {
           if (ld_relaxed(prm.err) != 0) { bad = 3; break; }
@@ -1320,7 +1313,6 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       }
       bad = __reduce_max_sync(kFull, bad);
       if (lane == 0 && bad) {
-        if (bad == 2 && atomicCAS(prm.err, 0, DERR_BADTASK) == 0) { prm.err[1] = idx; prm.err[2] = -1; }
         s_abort = 1;
       }
     }

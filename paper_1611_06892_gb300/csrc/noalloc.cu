@@ -4,14 +4,19 @@
 // A, the R copy of R-BiDiag, the T factors, the executor's task program, its completion flags and its
 // control words) is carved out of one fixed array in device global memory, g_scratch, declared below
 // with a static size.  Every GPU that loads the library holds this array until the process exits.
-// Host code cannot use the name g_scratch as a device address, so the first call on each device looks
-// up the array's device address with cudaGetSymbolAddress (with that device current) and keeps it.
+// Host code cannot use the name g_scratch as a device address: the first call in each CUDA context
+// (normally one per device: the device's primary context) looks up the array's device address with
+// cudaGetSymbolAddress, with that device current, and keeps it for that context.  The address is
+// keyed by the context's unique ID, so a context created after cudaDeviceReset, or a non-primary
+// context made current by the caller, gets its own lookup instead of a stale address.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/bidiag.h"
@@ -25,18 +30,55 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices] = {};
+// (context ID, device address of g_scratch in that context), one entry per context seen
+std::vector<std::pair<unsigned long long, unsigned char*>> g_addr;
 
-// Device address of g_scratch on the current device `dev`, looked up once per device.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique ID of the calling thread's current context (the runtime makes the device's primary context
+// current when there is none).  False if the driver does not offer the query.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  CUcontext ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_scratch in the current context (device `dev` current), looked up once per
+// context.  Before the runtime has initialised the device there may be no current context: the
+// lookup itself initialises it, and the address is then keyed by the context it was found in.
 cudaError_t scratch_address(int dev, unsigned char** out) {
+  (void)dev;
+  unsigned long long id = 0;
+  bool keyed = current_context_id(&id);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<unsigned char*>(p);
+  if (keyed) {
+    for (const auto& kv : g_addr)
+      if (kv.first == id) {
+        *out = kv.second;
+        return cudaSuccess;
+      }
   }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return e;
+  if (!keyed) keyed = current_context_id(&id);
+  if (keyed) g_addr.emplace_back(id, static_cast<unsigned char*>(p));
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 

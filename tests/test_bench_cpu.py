@@ -1,5 +1,6 @@
 """The benchmark's JSON line on the CPU: the reference arm (the oracle on host cores) at N = 1 carries
-every key of the contract, with its own metric and unit and no host-device traffic."""
+every key of the contract, with its own metric and unit and no host-device traffic; its CPU baseline
+states the host threads it was given, the CPU time it actually used and the CPU model."""
 import json
 import os
 import subprocess
@@ -26,6 +27,9 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["unit"] == d["unit"]
     assert isinstance(cb["sample"], str) and cb["sample"]
+    assert cb["cores"] == len(os.sched_getaffinity(0))
+    assert cb["cores_effective"] > 0 and isinstance(cb["cpu_model"], str) and cb["cpu_model"]
+    assert "whole task list" in cb["sample"]       # the 512 x 512 reduction is timed in full
     e = d["e2e"]
     assert e["unit"] == d["unit"] and e["value"] == d["value"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

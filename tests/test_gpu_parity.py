@@ -124,6 +124,21 @@ def test_parity_nb256_ragged(handle, torch_mod, tree):
         compare(res_g, res_o, A, 256, 32)
 
 
+@pytest.mark.parametrize("m,n,variant", ((1536, 1536, "bidiag"), (1792, 1280, "rbidiag")))
+def test_parity_nb256_auto_groups(handle, torch_mod, m, n, variant):
+    """nb = 256, ib = 32 on 6 x 6 (BiDiag) and 7 x 5 (R-BiDiag) tiles with R = 3, where Auto's first
+    steps have 1 < a < u: FlatTS groups joined by a Greedy TT tree (Sec. 5), compared element-wise at
+    the bench's tile size."""
+    p, q = -(-m // 256), -(-n // 256)
+    a0 = T.auto_group_size(p, q - 1, R_AUTO)
+    assert 1 < a0 < p          # the first QR step mixes TS groups and TT joins
+    A = inputs.gaussian(m, n, seed=m + n)
+    res_o = OB.bidiag_band(A, 256, 32, T.AUTO, G.VARIANTS[variant], resources=R_AUTO)
+    res_g = gpu_reduce(handle, torch_mod, A, 256, 32, "auto", variant)
+    compare(res_g, res_o, A, 256, 32)
+    res_g.free()
+
+
 @pytest.mark.parametrize("variant", ("bidiag", "rbidiag"))
 def test_apply_q_p(handle, torch_mod, variant):
     A = inputs.gaussian(150, 100, seed=23)

@@ -236,3 +236,126 @@ def test_flop_count_leading_order():
         m, n = p * nb, q * nb
         ratio = units / 3.0 / (4 * n * n * (m - n / 3))
         assert abs(ratio - 1) < 3.0 / p
+
+
+# ----------------------------------------------------------------------------------------------
+# The Auto tree's composition (Sec. 5): the panel tiles of a step are cut into consecutive groups of a
+# tiles; each group is reduced by a FlatTS tree into its top tile (TS kernels), and the group heads
+# are then joined by a Greedy tree of TT kernels.  The expected elimination lists below are worked out
+# by hand from that description (not by running the oracle), as (row, pivot, kind) in program order.
+# ----------------------------------------------------------------------------------------------
+TS_, TT_ = T.TS, T.TT
+_oracle_step = T.step_eliminations      # the mutants below delegate the non-Auto trees to it
+
+AUTO_PINS = [
+    # (panel rows, trailing tiles v, resources R, group size a, expected eliminations)
+    # R small: ceil(u/a) v >= 2R already holds for a = u, so one FlatTS group (pure FlatTS, all TS).
+    (list(range(0, 5)), 3, 1, 5, [(1, 0, TS_), (2, 0, TS_), (3, 0, TS_), (4, 0, TS_)]),
+    (list(range(2, 7)), 3, 1, 5, [(3, 2, TS_), (4, 2, TS_), (5, 2, TS_), (6, 2, TS_)]),
+    # R large: no a qualifies, so a = 1 and every row is a head: pure Greedy (halving), all TT.
+    # 7 heads: round 1 eliminates rows 4, 5, 6 into 1, 2, 3; round 2 rows 2, 3 into 0, 1; round 3 row 1.
+    (list(range(0, 7)), 2, 100, 1,
+     [(4, 1, TT_), (5, 2, TT_), (6, 3, TT_), (2, 0, TT_), (3, 1, TT_), (1, 0, TT_)]),
+    # Mixed: u = 7, v = 4, R = 6.  a = 7..4 give ceil(7/a) 4 = 4 or 8 < 12; a = 3 gives 3 x 4 = 12.
+    # Groups {0,1,2}, {3,4,5}, {6}: FlatTS 1->0, 2->0, 4->3, 5->3; heads 0, 3, 6 by Greedy: 6->3, 3->0.
+    (list(range(0, 7)), 4, 6, 3,
+     [(1, 0, TS_), (2, 0, TS_), (4, 3, TS_), (5, 3, TS_), (6, 3, TT_), (3, 0, TT_)]),
+    # The same shape at step k = 2 (rows 2..8): every index moves with the panel.
+    (list(range(2, 9)), 4, 6, 3,
+     [(3, 2, TS_), (4, 2, TS_), (6, 5, TS_), (7, 5, TS_), (8, 5, TT_), (5, 2, TT_)]),
+    # u = 10, v = 3, R = 5: a = 3 is the largest with ceil(10/a) 3 >= 10 (a = 4 gives 9).
+    # Groups {0,1,2}, {3,4,5}, {6,7,8}, {9}; heads 0, 3, 6, 9: Greedy 6->0, 9->3, then 3->0.
+    (list(range(0, 10)), 3, 5, 3,
+     [(1, 0, TS_), (2, 0, TS_), (4, 3, TS_), (5, 3, TS_), (7, 6, TS_), (8, 6, TS_),
+      (6, 0, TT_), (9, 3, TT_), (3, 0, TT_)]),
+]
+
+
+def _auto_pin_failures(step):
+    """Names of the Auto pins that `step` (a step_eliminations-like function) violates."""
+    bad = []
+    for rows, v, R, a, expect in AUTO_PINS:
+        if T.auto_group_size(len(rows), v, R) != a:
+            bad.append(f"group size {rows[0]}..{rows[-1]} v={v} R={R}")
+        if list(step(rows, v, T.AUTO, R)) != expect:
+            bad.append(f"eliminations {rows[0]}..{rows[-1]} v={v} R={R}")
+    return bad
+
+
+def test_auto_composition_hand_worked():
+    """Sec. 5: FlatTS groups of a consecutive tiles (TS, pivot = top tile of the group), heads joined
+    by Greedy with TT; a = u is FlatTS, a = 1 is Greedy."""
+    assert _auto_pin_failures(T.step_eliminations) == []
+
+
+def test_auto_limits_equal_flat_and_greedy_trees():
+    """With a = u Auto is exactly FlatTS, with a = 1 exactly Greedy, on every panel size."""
+    for u in range(1, 20):
+        rows = list(range(3, 3 + u))
+        assert T.step_eliminations(rows, 2, T.AUTO, 1) == T.step_eliminations(rows, 2, T.FLATTS)
+        assert T.step_eliminations(rows, 2, T.AUTO, 10 ** 6) == T.step_eliminations(rows, 2, T.GREEDY)
+
+
+def test_auto_task_list_first_step():
+    """Task-list form of the mixed case: p = 7, q = 5 BiDiag with R = 6 has u = 7, v = 4 in QR(0), so
+    only the group heads 0, 3, 6 are factored by GEQRT; rows 1, 2, 4, 5 are eliminated by TSQRT into
+    their group's top tile; 6 -> 3 and 3 -> 0 are TTQRT, in that order."""
+    tasks = [t for t in T.task_list(7, 5, T.AUTO, T.BIDIAG, resources=6) if t[1] == T.QR and t[2] == 0]
+    assert sorted(t[3] for t in tasks if t[0] == T.GEQRT) == [0, 3, 6]
+    assert [(t[3], t[4]) for t in tasks if t[0] == T.TSQRT] == [(1, 0), (2, 0), (4, 3), (5, 3)]
+    assert [(t[3], t[4]) for t in tasks if t[0] == T.TTQRT] == [(6, 3), (3, 0)]
+
+
+def _mutant_heads_ts(rows, v, tree, R=None, gamma=2):
+    out = _oracle_step(rows, v, tree, R, gamma)
+    if tree != T.AUTO:
+        return out
+    a = T.auto_group_size(len(rows), v, R, gamma)
+    heads = set(rows[::a])
+    return [(i, piv, T.TS if i in heads else kind) for (i, piv, kind) in out]
+
+
+def _mutant_strided_groups(rows, v, tree, R=None, gamma=2):
+    if tree != T.AUTO:
+        return _oracle_step(rows, v, tree, R, gamma)
+    rows = list(rows)
+    a = T.auto_group_size(len(rows), v, R, gamma)
+    ng = -(-len(rows) // a)
+    groups = [rows[s::ng] for s in range(ng)]
+    el = [(r, g[0], T.TS) for g in groups for r in g[1:]]
+    el += [(i, piv, T.TT) for rnd in T.greedy_rounds([g[0] for g in groups]) for (i, piv) in rnd]
+    return el
+
+
+def _mutant_bottom_pivot(rows, v, tree, R=None, gamma=2):
+    if tree != T.AUTO:
+        return _oracle_step(rows, v, tree, R, gamma)
+    rows = list(rows)
+    a = T.auto_group_size(len(rows), v, R, gamma)
+    groups = [rows[s:s + a] for s in range(0, len(rows), a)]
+    el = [(r, g[-1], T.TS) for g in groups for r in g[:-1]]
+    el += [(i, piv, T.TT) for rnd in T.greedy_rounds(sorted(g[-1] for g in groups)) for (i, piv) in rnd]
+    return el
+
+
+def _mutant_heads_flat(rows, v, tree, R=None, gamma=2):
+    if tree != T.AUTO:
+        return _oracle_step(rows, v, tree, R, gamma)
+    rows = list(rows)
+    a = T.auto_group_size(len(rows), v, R, gamma)
+    groups = [rows[s:s + a] for s in range(0, len(rows), a)]
+    el = [(r, g[0], T.TS) for g in groups for r in g[1:]]
+    el += [(g[0], groups[0][0], T.TT) for g in groups[1:]]
+    return el
+
+
+@pytest.mark.parametrize("mutant", [_mutant_heads_ts, _mutant_strided_groups, _mutant_bottom_pivot,
+                                    _mutant_heads_flat], ids=lambda f: f.__name__[8:])
+def test_auto_pins_catch_planted_mistakes(mutant, monkeypatch):
+    """Each plausible misreading of Sec. 5 (heads joined with TS kernels, strided instead of
+    consecutive groups, the pivot at the bottom of a group, heads joined by a flat instead of a Greedy
+    tree) fails the hand-worked lists and the task-list form."""
+    assert _auto_pin_failures(mutant)
+    monkeypatch.setattr(T, "step_eliminations", mutant)
+    with pytest.raises(AssertionError):
+        test_auto_task_list_first_step()

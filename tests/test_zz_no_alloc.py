@@ -2,10 +2,11 @@
 
 bidiag_band_noalloc serves callers that may not allocate device memory (an application whose GPU
 memory is wholly owned by another allocator, or a service that forbids device allocation after
-start-up): its scratch is a fixed 8 MiB array that the library declares statically.  Two calls in a
-row, with different shapes, variants and trees, must each give the band of the regular entry point
-within the parity tolerance (1e-12 * ||A||_F), so that nothing the first call leaves in the shared
-array leaks into the second; a problem larger than the array must be refused before any work.
+start-up): its scratch is a fixed 8 MiB array that the library declares statically.  Three calls in a
+row, with different shapes, variants and trees (the last one smaller than the one before it), must
+each give the band of the regular entry point within the parity tolerance (1e-12 * ||A||_F), so that
+nothing an earlier call leaves in the shared array leaks into a later one; a problem larger than the
+array must be refused before any work.
 
 This file is collected last on purpose (its name sorts after the other test files).
 """
@@ -46,6 +47,9 @@ def test_noalloc_matches_regular_entry_point_twice():
     cases = [
         (300, 200, 32, 8, "greedy", "rbidiag", 7),    # ragged 10 x 7 tiles, R-BiDiag
         (512, 512, 64, 16, "auto", "bidiag", 8),      # the small square workload's shape
+        # smaller again after the larger call: its tiles, R copy, T factors and flags are a prefix of
+        # what the 512 x 512 call left behind, so stale contents would show here
+        (256, 160, 32, 8, "flatts", "rbidiag", 9),
     ]
     try:
         for (m, n, nb, ib, tree, variant, seed) in cases:
