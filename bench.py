@@ -44,6 +44,9 @@ WORKLOADS = {
                             "autotuned nb / ib / tree / variant per matrix"),
     "tall65536x2048": dict(m=65536, n=2048, nb=256, ib=32, variant="rbidiag", kind="gauss", seeds=(5,),
                            desc="tall-skinny FP64 65536x2048 N(0,1), nb=256 ib=32, R-BiDiag"),
+    "grad8192": dict(m=8192, n=8192, nb=256, ib=32, variant="bidiag", kind="grad", seeds=(12, 13), tree="auto",
+                     desc="differentiation FP64 8192x8192 N(0,1), nb=256 ib=32, BiDiag: forward reduction + adjoint "
+                          "(dL/dA from a N(0,1) band gradient W, L = <W, B>)"),
     "grad4096x1024": dict(m=4096, n=1024, nb=256, ib=32, variant="bidiag", kind="grad", seeds=(7, 8),
                           desc="differentiation FP64 4096x1024 N(0,1), nb=256 ib=32, BiDiag: forward reduction "
                                "+ adjoint (dL/dA from a N(0,1) band gradient W, L = <W, B>)"),
@@ -157,6 +160,97 @@ def table1_flops(G, m, n, nb, tree, variant, resources):
     p, q = -(-m // nb), -(-n // nb)
     tk, _, _ = G.bidiag_plan_tasks(p, q, tree, variant, resources)
     return float(np.asarray(TABLE1_WEIGHTS)[tk[:, 0]].sum()) * nb ** 3 / 3.0
+
+
+SUBTASK_NAMES = {1: "UNMQR strip", 3: "TSMQR strip", 5: "TTMQR strip", 6: "COPY", 7: "PF", 8: "PU",
+                 9: "adjoint PF", 10: "adjoint PU", 11: "adjoint strip", 12: "adjoint COPY", 13: "adjoint reduce"}
+PANEL_KINDS = {0: "GE", 1: "TS", 2: "TT"}
+UPDATE_UNITS = {1: 6, 3: 12, 5: 6}        # Table 1 units (nb^3/3 flops) of a whole tile update
+
+
+def subtask_class(op):
+    typ, kind, blk = op & 15, (op >> 24) & 3, (op >> 16) & 0xff
+    if typ in (7, 8, 9, 10):
+        return f"{SUBTASK_NAMES[typ]} {PANEL_KINDS.get(kind, '?')}"
+    return SUBTASK_NAMES.get(typ, f"type {typ}")
+
+
+def subtask_bytes_flops(op, nb, ib, w, esize):
+    """Algorithmic global-memory bytes (loads + stores of the tiles it stages) and flops of one
+    sub-task of the executor, from its op word (the blocks each sub-task moves: see kernels.cu)."""
+    typ, kind, strip, blk = op & 15, (op >> 24) & 3, (op >> 8) & 0xff, (op >> 16) & 0xff
+    c0 = blk * ib
+    if typ == 7:                          # PF(b): the block's columns of the panel (and pivot triangle)
+        rows = nb - c0 if kind == 0 else (nb if kind == 1 else c0 + ib)
+        elems = 2 * rows * ib + ib * ib + (0 if kind == 0 else ib * (ib + 1))
+        return elems * esize, None
+    if typ == 8:                          # PU(b, s): block b applied to column block s of the panel
+        rows = nb - c0 if kind == 0 else (nb if kind == 1 else c0 + ib)
+        elems = 2 * rows * ib + rows * ib + ib * ib + (0 if kind == 0 else 2 * ib * ib)
+        return elems * esize, None
+    if typ in (1, 3, 5):                  # update strip: all blocks of the tile on ncols columns
+        ncols = min(w, nb - strip * w)
+        nblk = nb // ib
+        vrows = sum((nb - b * ib) if typ == 1 else (nb if typ == 3 else (b + 1) * ib) for b in range(nblk))
+        elems = 2 * nb * ncols + vrows * ib + nblk * ib * ib + (0 if typ == 1 else 2 * nblk * ib * ncols)
+        return elems * esize, UPDATE_UNITS[typ] * nb * nb * ncols / 3.0
+    if typ == 6:
+        return 2 * nb * nb * esize, None
+    return 0, None
+
+
+def trace_report(h, nb, ib, esize, nsm, title, w=32):
+    """Markdown summary of the last traced launch: per sub-task class its count, time, share of the
+    busy time, algorithmic bytes and GB/s (flops and GFLOP/s for the update strips); SM occupancy;
+    and the critical chain (walking back from the last sub-task through the dependency that finished
+    last), split into sub-task time by class and waiting gaps."""
+    import numpy as np
+    tr = h.trace()
+    prog, deps = h.trace_program()
+    n = len(tr)
+    start, end, op = tr[:, 0].astype(np.float64), tr[:, 1].astype(np.float64), tr[:, 3].astype(np.int64)
+    dur = end - start
+    t0, t1 = start.min(), end.max()
+    cls = [subtask_class(int(o)) for o in op]
+    stats = {}
+    for y in range(n):
+        b, f = subtask_bytes_flops(int(op[y]), nb, ib, w, esize)
+        s = stats.setdefault(cls[y], [0, 0.0, 0.0, 0.0, 0.0])
+        s[0] += 1
+        s[1] += dur[y]
+        s[2] += b
+        s[3] += f or 0.0
+    busy = dur.sum()
+    lines = [f"### {title}", "",
+             f"launch span {1e-6 * (t1 - t0):.2f} ms, {n} sub-tasks, SMs busy {busy / (nsm * (t1 - t0)):.1%} "
+             f"of the span ({nsm} SMs)", "",
+             "| sub-task | count | total ms | share of busy | mean us | alg. bytes | GB/s | GFLOP/s |",
+             "|---|---|---|---|---|---|---|---|"]
+    for k in sorted(stats, key=lambda c: -stats[c][1]):
+        c, tot, by, fl, _ = stats[k]
+        lines.append(f"| {k} | {c} | {1e-6 * tot:.2f} | {tot / busy:.1%} | {1e-3 * tot / c:.1f} | "
+                     f"{by / c / 1e3:.0f} KB | {by / tot:.1f} | " + (f"{fl / tot:.1f} |" if fl else "- |"))
+    # critical chain
+    y = int(np.argmax(end))
+    chain_t, gaps, steps = {}, 0.0, 0
+    while True:
+        chain_t[cls[y]] = chain_t.get(cls[y], 0.0) + dur[y]
+        steps += 1
+        d0, d1 = int(prog[y, 5]), int(prog[y, 6])
+        ds = [int(d) for d in deps[d0:d1] if 0 <= int(d) < n]
+        if not ds:
+            gaps += start[y] - t0
+            break
+        p = max(ds, key=lambda d: end[d])
+        gaps += max(0.0, start[y] - end[p])
+        y = p
+    lines += ["", f"critical chain: {steps} sub-tasks, {1e-6 * (sum(chain_t.values()) + gaps):.2f} ms "
+                  f"= sub-task time {1e-6 * sum(chain_t.values()):.2f} ms + waiting gaps {1e-6 * gaps:.2f} ms", "",
+              "| on the chain | ms | share of span |", "|---|---|---|"]
+    for k in sorted(chain_t, key=lambda c: -chain_t[c]):
+        lines.append(f"| {k} | {1e-6 * chain_t[k]:.2f} | {chain_t[k] / (t1 - t0):.1%} |")
+    lines.append(f"| waiting gaps | {1e-6 * gaps:.2f} | {gaps / (t1 - t0):.1%} |")
+    return "\n".join(lines) + "\n"
 
 
 def metric_flops(m, n):
@@ -537,9 +631,22 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     h = G.Handle(device=local)
     h.set_option(G.OPT_TIMING, 1)
     peaks = measure_peaks(G, torch, local, f32)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    if args.batch_config:        # one fixed (nb, ib, tree) for every matrix; variant by critical path
+        fnb, fib, ftree = args.batch_config.split(",")
+        fixed = dict(nb=[int(fnb)] * len(As), ib=[int(fib)] * len(As), tree=[ftree] * len(As),
+                     variant=["auto"] * len(As))
+        cfgs = []
+        for m, n in shapes:
+            p, q = -(-m // int(fnb)), -(-n // int(fnb))
+            R = max(1, nsm * min(int(fnb), 32) * (2 if f32 else 1) // int(fnb))
+            cfgs.append((int(fnb), int(fib), G.TREES[ftree], G.bidiag_plan_choose_variant(p, q, G.TREES[ftree], R)[0]))
+    else:
+        fixed = {}
+        cfgs = [G.bidiag_autotune(m, n, nsm, 4 if f32 else 8) for m, n in shapes]
 
     def step():
-        res = h.band_batched(As)
+        res = h.band_batched(As, **fixed)
         h.sync()
         ms = h.last_exec_ms()
         for r in res:
@@ -570,7 +677,7 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
         barrier(world)
         t0 = time.perf_counter()
         dev = [x.to(device, non_blocking=True) for x in hosts]
-        res = h.band_batched(dev)
+        res = h.band_batched(dev, **fixed)
         bands = [r.band().cpu() for r in res]
         e2e_t.append(time.perf_counter() - t0)
         d2h = sum(x.numel() * x.element_size() for x in bands)
@@ -582,10 +689,13 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     if not e2e_t:
         d2h = 0
     exec_mean = statistics.mean(exec_ms)
-    cfgs = [G.bidiag_autotune(m, n, torch.cuda.get_device_properties(local).multi_processor_count) for m, n in shapes]
-    alg = sum(table1_flops(G, m, n, c[0], c[2], c[3], 1) for (m, n), c in zip(shapes, cfgs))
+    alg = sum(table1_flops(G, m, n, c[0], c[2], c[3], max(1, nsm * min(c[0], 32) * (2 if f32 else 1) // c[0]))
+              for (m, n), c in zip(shapes, cfgs))
     achieved = alg / (exec_mean * 1e-3) / 1e9
     peak, bound, src = roofline_peak(peaks, f32)
+    if args.batch_config:
+        config = dict(config, nb=int(fnb), ib=int(fib), tree=ftree, workload=config["workload"].replace(
+            "autotuned nb / ib / tree / variant per matrix", f"fixed nb={fnb} ib={fib} tree={ftree}, variant by critical path"))
     line = dict(base, config=config, dtype="f32" if f32 else "f64", value=value, ms_per_step=ms_per_step,
                 e2e={"value": world * flops / e2e_s / 1e12 if e2e_s else None, "unit": "TFLOP/s",
                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -617,6 +727,72 @@ def run_batched(args, w, base, config, world, rank, local, device, G, torch):
     return 0
 
 
+AUTOTUNE_CONFIGS = [(32, 8), (32, 16), (32, 32), (64, 8), (64, 16), (64, 32), (128, 8), (128, 16), (128, 32)]
+AUTOTUNE_CLASSES = ["PF GE", "PF TS", "PF TT", "PU GE", "PU TS", "PU TT", "UNMQR strip", "TSMQR strip",
+                    "TTMQR strip"]
+
+
+def calibrate_autotune(args, w, G, torch, local, device, path):
+    """Calibration table of the batched form's autotuner: mean execution time of each sub-task class
+    (panel factor / panel update per panel kind, update strip per kernel) for every candidate (nb, ib),
+    measured on the 512-matrix batch reduced with that (nb, ib) for all matrices, once with FlatTS (TS
+    kernels) and once with Greedy (TT kernels), traced.  Rows of this storage precision replace those
+    in `path` (a C include file compiled into the planner)."""
+    import numpy as np
+    f32 = args.precision == "f32"
+    dt = torch.float32 if f32 else torch.float64
+    esize = 4 if f32 else 8
+    shapes = batch_shapes(w["seeds"][0])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w["seeds"][0])
+    As = [torch.randn(n, m, dtype=dt, device=device, generator=gen).t() for m, n in shapes]
+    count = len(As)
+    h = G.Handle(device=local)
+    rows = []
+    for nb, ib in AUTOTUNE_CONFIGS:
+        durs = {c: [] for c in AUTOTUNE_CLASSES}
+        for tree in ("flatts", "greedy"):
+            cfg = dict(nb=[nb] * count, ib=[ib] * count, tree=[tree] * count, variant=["auto"] * count)
+            for r in h.band_batched(As, **cfg):      # warm-up (plans the batch)
+                r.free()
+            h.sync()
+            h.set_option(G.OPT_TRACE, 1)
+            res = h.band_batched(As, **cfg)
+            h.sync()
+            h.set_option(G.OPT_TRACE, 0)
+            tr = h.trace()
+            for r in res:
+                r.free()
+            for (t0, t1, _, op) in tr:
+                c = subtask_class(int(op))
+                if c in durs:
+                    durs[c].append(1e-3 * (t1 - t0))
+        rows.append((nb, ib, [float(np.mean(durs[c])) if durs[c] else 0.0 for c in AUTOTUNE_CLASSES],
+                     [len(durs[c]) for c in AUTOTUNE_CLASSES]))
+    h.close()
+    keep = []
+    if os.path.exists(path):
+        with open(path) as fh:
+            keep = [l for l in fh if l.startswith("{") and not l.startswith("{%d," % esize)]
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    with open(path, "w") as fh:
+        fh.write("// Autotuner calibration (generated): mean execution time in microseconds of each executor\n"
+                 "// sub-task class, {element bytes, nb, ib, {PF GE, PF TS, PF TT, PU GE, PU TS, PU TT,\n"
+                 "// UNMQR strip, TSMQR strip, TTMQR strip}}, measured on a GPU with %d SMs (%s) reducing the\n"
+                 "// 512-matrix batch (m ~ U[64, 1024], n ~ U[32, m], N(0,1), seed 6) with one (nb, ib) for all\n"
+                 "// matrices, FlatTS and Greedy, traced.  Written by\n"
+                 "//   python bench.py --workload batched512 [--precision f32] --calibrate-autotune <this file>\n"
+                 % (nsm, torch.cuda.get_device_name(local)))
+        for l in keep:
+            fh.write(l)
+        for nb, ib, us, _ in rows:
+            fh.write("{%d, %d, %d, {%s}},\n" % (esize, nb, ib, ", ".join("%.2f" % x for x in us)))
+    print(json.dumps({"calibrated": path, "esize": esize,
+                      "rows": [{"nb": nb, "ib": ib, "us": dict(zip(AUTOTUNE_CLASSES, us)),
+                                "samples": dict(zip(AUTOTUNE_CLASSES, cnt))} for nb, ib, us, cnt in rows]}))
+    return 0
+
+
 def workload_config(args, w, config):
     """The `config` object of both arms (ours and the reference) for the batched and the
     differentiation workloads; the single-matrix workloads keep the generic one."""
@@ -624,7 +800,7 @@ def workload_config(args, w, config):
     if w["kind"] == "grad":
         m, n = w["m"], w["n"]
         config = dict(config, workload=w["desc"].replace("FP64", "FP32 storage (3xTF32 updates)") if f32 else w["desc"],
-                      tree="greedy" if args.tree == "auto" else args.tree,
+                      tree=w.get("tree", "greedy") if args.tree == "auto" else args.tree,
                       l2=f"input {m * n * (4 if f32 else 8) / 2**20:.0f} MiB (the adjoint's working set, 3 copies "
                          "of A plus partial sums, exceeds the 129 MB L2; no flush)")
         config.pop("auto_resources", None)
@@ -656,6 +832,16 @@ def main():
     ap.add_argument("--cpu-max-tasks", type=int, default=None)
     ap.add_argument("--cpu-sample-batch", default=None)
     ap.add_argument("--cpu-sample-grad", default=None)
+    ap.add_argument("--calibrate-autotune", default=None,
+                    help="batched512 only: measure the autotuner's per-sub-task times for every candidate (nb, ib) "
+                         "and write them to this C include file (instead of the benchmark)")
+    ap.add_argument("--batch-config", default=None,
+                    help="batched512 only: nb,ib,tree for every matrix instead of the autotuner's choices")
+    ap.add_argument("--strip-width", type=int, default=None,
+                    help="column-strip width of the update sub-tasks (16, 32 or 64; default: the library's 32)")
+    ap.add_argument("--trace-summary", default=None,
+                    help="after the timed region, trace one more reduction and append its per-sub-task summary "
+                         "(markdown) to this file")
     ap.add_argument("--auto-resources", type=int, default=None,
                     help="R of the Auto tree (default: SMs * 32 / nb, twice that for FP32 storage, as the library chooses)")
     args = ap.parse_args()
@@ -754,6 +940,8 @@ def main():
         from paper_1611_06892_gb300 import build
         build.build()
     G.load_library()
+    if w["kind"] == "batch" and args.calibrate_autotune:
+        return calibrate_autotune(args, w, G, torch, local, device, args.calibrate_autotune)
     if w["kind"] == "batch":
         return run_batched(args, w, base, config, world, rank, local, device, G, torch)
     if w["kind"] == "grad":
@@ -765,6 +953,9 @@ def main():
     h = G.Handle(device=local)
     h.set_option(G.OPT_TIMING, 1)
     h.set_option(G.OPT_AUTO_RESOURCES, w["resources"])
+    if args.strip_width:
+        h.set_option(G.OPT_STRIP, args.strip_width)
+        config["strip_width"] = args.strip_width
     stream = h.stream
     peaks = measure_peaks(G, torch, local, f32)
 
@@ -817,6 +1008,16 @@ def main():
                                ab_host.data_ptr(), nb + 1)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.mean(e2e_t), world, device) if e2e_t else None
+    if args.trace_summary and rank == 0:
+        h.set_option(G.OPT_TRACE, 1)
+        r = h.band(A, nb, ib, args.tree, vcode)
+        h.sync()
+        r.free()
+        h.set_option(G.OPT_TRACE, 0)
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        title = f"{config['workload']}" + (f", R = {w['resources']}" if args.tree == "auto" else "")
+        with open(args.trace_summary, "a") as fh:
+            fh.write(trace_report(h, nb, ib, A.element_size(), nsm, title) + "\n")
 
     exec_mean = statistics.mean(exec_ms)
     alg = table1_flops(G, m, n, nb, G.TREES[args.tree], w.get("variant_used", vcode), w["resources"])

@@ -64,11 +64,16 @@ enum {
                                      tile updates that run at once when each spreads over nb / w SMs) */
   BIDIAG_OPT_DEBUG_UNSET_DEP = 3, /* 1: the next bidiag_band adds to its first task a dependency on a
                                      flag nothing sets, so that its wait runs out (failure-path test) */
-  BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16 or 32, default 32) */
+  BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16, 32 or 64, default 32) */
   BIDIAG_OPT_TIMING = 5,          /* 1: time the executor launch of each bidiag_band with CUDA events */
   BIDIAG_OPT_TRACE = 6,           /* 1: record a per-task trace of each bidiag_band (see bidiag_trace) */
-  BIDIAG_OPT_F32_UPDATES = 7      /* FP32 storage: 0 = updates as three TF32 tensor-core products (default),
+  BIDIAG_OPT_F32_UPDATES = 7,     /* FP32 storage: 0 = updates as three TF32 tensor-core products (default),
                                      1 = updates by FP32 FMA on the CUDA cores (FP32-exact products) */
+  BIDIAG_OPT_F32_SCALARS = 8      /* FP32 storage: each reflector's beta, tau and tail scale from alpha and
+                                     the tail's squared norm (always a compensated sum, FP64-level accuracy)
+                                     0 = in float-pair arithmetic, about 44 bits (default), 1 = in FP64.
+                                     Both give the FP32 values the reduction stores to within their
+                                     rounding; FP64 costs ~1.7K cycles of serial FP64 latency per column */
 };
 
 /* Task type codes of the canonical task list (GELQT etc. are the same codes in LQ phases). */
@@ -154,12 +159,14 @@ int bidiag_band_batched_f32(bidiag_handle h, int64_t count, const int64_t* m, co
                             const float* const* d_A, const int64_t* lda, const int* nb, const int* ib,
                             const int* tree, const int* variant, bidiag_result_t* out);
 
-/* Autotuner of the batched form (host only): for an m x n matrix of a batch on a device with nsm SMs,
- * picks nb in {32, 64, 128} (ib = 16 for nb = 32, else 32) minimising padded Table 1 work / (measured
- * efficiency of that tile size in batches) + critical path / (nsm / 8), the FlatTS tree (the other
- * matrices of the batch supply the parallelism) and the variant by critical path (Sec. 4.3.3).
- * Errors: -1 sizes, -3 nsm, -4 NULL output. */
-int bidiag_autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant);
+/* Autotuner of the batched form (host only): for an m x n matrix of a batch on a device with nsm SMs and
+ * storage of elem_bytes (8: FP64, 4: FP32), searches the calibrated tile sizes and inner blockings
+ * (nb in {32, 64, 128}, ib in {8, 16, 32}) and the FlatTS, Greedy and Auto trees (Sec. 3.3, Sec. 5), the
+ * variant by critical path (Sec. 4.3.3), minimising the time the matrix's sub-tasks keep SMs busy (mean
+ * sub-task times measured on a GB300, compiled into the library) plus its critical path with the same
+ * times over nsm / 8.  The paper tunes nb and ib by hand (Sec. 6.2); its Auto tree adapts the reduction
+ * tree to the resources (Sec. 5).  Errors: -1 sizes, -3 nsm, -4 elem_bytes, -5 NULL output. */
+int bidiag_autotune(int64_t m, int64_t n, int nsm, int elem_bytes, int* nb, int* ib, int* tree, int* variant);
 
 /*
  * Same reduction for host buffers: copies h_A (column-major, lda) to the device, reduces it, copies the
@@ -247,14 +254,22 @@ int bidiag_apply_p_f32(bidiag_handle h, bidiag_result_t r, int trans, int64_t nr
  * the reflector's construction from its pivot column.  The paper has no derivative; this is its exact
  * reverse mode, with a reflector of tau = 0 (a zero column, where the Householder map switches branch)
  * held constant.  The result must come from this handle and is not modified; FP64 results only
- * (FP32 ones: bidiag_band_backward_f32).  Device memory: two copies of the tiled matrix plus partial
- * sums (about nb^2 + nb ib elements per update strip of the reduction: 3.5 GB for 4096 x 1024 with
- * nb = 256), allocated and freed on the handle's stream.  Bitwise deterministic (no atomics).  Errors: -2 result, -3 d_abbar NULL, -4 ldab, -5 d_Abar NULL, -6 ldabar, -8 ldarec,
+ * (FP32 ones: bidiag_band_backward_f32).  Device memory (bidiag_backward_workspace gives the exact
+ * figure): two copies of the tiled matrix, the partial sums of the update adjoints (nb^2 + nb ib
+ * elements per update strip, in storage recycled once the panel's factor adjoint has consumed them:
+ * 1.0 GB for 4096 x 1024 and 6.8 GB for 8192^2 with nb = 256, FP64) and nb ib elements of scratch per
+ * executor CTA, allocated and freed on the handle's stream.  Bitwise deterministic (no atomics).
+ * Errors: -2 result, -3 d_abbar NULL, -4 ldab, -5 d_Abar NULL, -6 ldabar, -8 ldarec,
  * BIDIAG_ERR_UNSUPPORTED when nb / ib need more shared memory than a block has (nb = 256 needs
  * ib <= 32), BIDIAG_ERR_NOMEM, BIDIAG_ERR_CUDA.  Stream-ordered: call bidiag_sync before reading.
  */
 int bidiag_band_backward(bidiag_handle h, bidiag_result_t r, const double* d_abbar, int64_t ldab,
                          double* d_Abar, int64_t ldabar, double* d_Arec, int64_t ldarec);
+/* Device bytes one bidiag_band_backward(_f32) call on result r allocates (state and gradient tiles,
+ * partial-sum storage, panel-adjoint scratch), in *bytes.  Plans and uploads the adjoint program if this
+ * result's plan has none yet (the backward call then reuses it).  Errors: -1 h, -2 result, -3 bytes NULL,
+ * BIDIAG_ERR_UNSUPPORTED, BIDIAG_ERR_NOMEM, BIDIAG_ERR_CUDA. */
+int bidiag_backward_workspace(bidiag_handle h, bidiag_result_t r, int64_t* bytes);
 /* The same for a result with FP32 storage (band_f32 / band_batched_f32); the reflector derivatives
  * and the Householder-construction step are evaluated in FP64, the updates as in the forward. */
 int bidiag_band_backward_f32(bidiag_handle h, bidiag_result_t r, const float* d_abbar, int64_t ldab,
@@ -274,6 +289,14 @@ int bidiag_last_exec_ms(bidiag_handle h, float* ms);
  * *count records of 4 int64 in queue order: start and end (%globaltimer ns), SM id, and the task's op
  * word (type | orientation << 4 | strip << 8).  Copied to host `out` when cap >= *count. */
 int bidiag_trace(bidiag_handle h, int64_t* out, int64_t cap, int64_t* count);
+
+/* Device program of the last traced launch (host memory, for analysing its trace): *count sub-tasks
+ * of 8 int32 in queue order (the layout of bidiag_plan_program: op, x, a, c, tslot, dep_begin, dep_end,
+ * flags) and *ndeps dependency entries (queue positions).  Copied when cap >= *count and dcap >= *ndeps
+ * respectively.  Errors: -1 h, -4 count NULL, -7 ndeps NULL, BIDIAG_ERR_UNSUPPORTED before any traced
+ * launch. */
+int bidiag_trace_program(bidiag_handle h, int32_t* program, int64_t cap, int64_t* count, int32_t* deps,
+                         int64_t dcap, int64_t* ndeps);
 
 /* Text of the last failure on the handle ("" if none).  Valid until the next call on h. */
 const char* bidiag_last_error(bidiag_handle h);

@@ -31,6 +31,7 @@ OK, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_SCRATCH = 0, 1, 2, 3,
 NOALLOC_SCRATCH_BYTES = 8 << 20
 OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING, OPT_TRACE = 1, 2, 3, 4, 5, 6
 OPT_F32_UPDATES = 7
+OPT_F32_SCALARS = 8
 
 _lib = None
 
@@ -69,7 +70,7 @@ def load_library(path=LIB_PATH):
                                        P(vp)]),
         "bidiag_band_batched_f32": (cint, [vp, i64, P(i64), P(i64), P(vp), P(i64), P(cint), P(cint), P(cint),
                                            P(cint), P(vp)]),
-        "bidiag_autotune": (cint, [i64, i64, cint, P(cint), P(cint), P(cint), P(cint)]),
+        "bidiag_autotune": (cint, [i64, i64, cint, cint, P(cint), P(cint), P(cint), P(cint)]),
         "bidiag_result_band_f32": (cint, [vp, P(vp), P(i64), P(i64), P(cint)]),
         "bidiag_apply_q_f32": (cint, [vp, vp, cint, i64, vp, i64]),
         "bidiag_apply_p_f32": (cint, [vp, vp, cint, i64, vp, i64]),
@@ -84,6 +85,8 @@ def load_library(path=LIB_PATH):
         "bidiag_sync": (cint, [vp]),
         "bidiag_last_exec_ms": (cint, [vp, P(ctypes.c_float)]),
         "bidiag_trace": (cint, [vp, P(i64), i64, P(i64)]),
+        "bidiag_backward_workspace": (cint, [vp, vp, P(i64)]),
+        "bidiag_trace_program": (cint, [vp, P(i32), i64, P(i64), P(i32), i64, P(i64)]),
         "bidiag_measure_fp64_peaks": (cint, [cint, vp, P(ctypes.c_double), P(ctypes.c_double)]),
         "bidiag_last_error": (ctypes.c_char_p, [vp]),
         "bidiag_result_free": (cint, [vp]),
@@ -134,10 +137,11 @@ def bidiag_band_f32(h, m, n, d_A, lda, nb, ib, tree, variant):
     return r
 
 
-def bidiag_autotune(m, n, nsm):
-    """(nb, ib, tree, variant) the batched form's autotuner picks for an m x n matrix."""
+def bidiag_autotune(m, n, nsm, elem_bytes=8):
+    """(nb, ib, tree, variant) the batched form's autotuner picks for an m x n matrix (FP64 storage:
+    elem_bytes 8, FP32: 4)."""
     v = [ctypes.c_int() for _ in range(4)]
-    _check(None, load_library().bidiag_autotune(m, n, nsm, *[ctypes.byref(x) for x in v]))
+    _check(None, load_library().bidiag_autotune(m, n, nsm, elem_bytes, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
 
 
@@ -381,6 +385,18 @@ class Handle:
                                         ctypes.byref(cnt)))
         return out
 
+    def trace_program(self):
+        """Device program of the last traced launch: (sub-tasks (count x 8) int32, dependency array)."""
+        lib = load_library()
+        cnt, nd = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.h, lib.bidiag_trace_program(self.h, None, 0, ctypes.byref(cnt), None, 0, ctypes.byref(nd)))
+        prog = np.zeros((max(cnt.value, 1), 8), dtype=np.int32)
+        deps = np.zeros(max(nd.value, 1), dtype=np.int32)
+        I32 = ctypes.POINTER(ctypes.c_int32)
+        _check(self.h, lib.bidiag_trace_program(self.h, prog.ctypes.data_as(I32), cnt.value, ctypes.byref(cnt),
+                                                deps.ctypes.data_as(I32), nd.value, ctypes.byref(nd)))
+        return prog[:cnt.value], deps[:nd.value]
+
     def close(self):
         if self.h:
             bidiag_destroy(self.h)
@@ -477,6 +493,12 @@ class Result:
            ctypes.c_void_p(Arec.data_ptr()) if reconstruct else None, max(m, 1))
         self._grad_keep = Gc     # stream-ordered use: keep the input alive until the next call
         return (Abar, Arec) if reconstruct else Abar
+
+    def backward_workspace(self):
+        """Device bytes one backward() call allocates (plans the adjoint on first use)."""
+        b = ctypes.c_int64()
+        _check(self.handle.h, load_library().bidiag_backward_workspace(self.handle.h, self.r, ctypes.byref(b)))
+        return b.value
 
     def free(self):
         if self.r:

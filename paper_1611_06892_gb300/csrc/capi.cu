@@ -31,6 +31,7 @@ struct PlanDev {
   int32_t* d_deps = nullptr;
   int* d_done = nullptr;
   int nflags = 0;
+  int64_t ndeps = 0;           // entries of d_deps
   std::vector<int32_t> dump;   // canonical task list, 6 int32 per task
   ~PlanDev() {
     if (d_tasks) cudaFree(d_tasks);
@@ -106,10 +107,13 @@ struct bidiag_ctx {
   std::set<bidiag_result*> live;   // results made on this handle and not yet freed
   int tracing = 0;
   int f32_simt = 0;                // FP32 storage: updates by FFMA instead of 3xTF32 tensor-core products
+  int f32_scalars64 = 0;           // FP32 storage: reflector scalars in FP64 instead of float pairs
   int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
   std::map<std::tuple<int, int, int, int64_t>, int> splits;   // best three-step split per (p, q, tree, R)
   std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> batches;   // batch programs by shapes / options
   int64_t trace_cap = 0, trace_len = 0;
+  std::vector<bd::DevTask> trace_dev;   // device program of the last traced launch (queue order)
+  std::vector<int32_t> trace_deps;
 };
 
 struct bidiag_result {
@@ -157,6 +161,7 @@ int upload_program(bidiag_handle h, PlanDev& pd, const std::vector<bd::DevTask>&
                    int extra_flags) {
   const size_t nt = dev.size();
   pd.nflags = (int)nt + extra_flags;
+  pd.ndeps = (int64_t)deps.size();
   CK(h, cudaMalloc(&pd.d_tasks, std::max<size_t>(1, nt) * sizeof(bd::DevTask)));
   CK(h, cudaMalloc(&pd.d_deps, std::max<size_t>(1, deps.size()) * sizeof(int32_t)));
   CK(h, cudaMalloc(&pd.d_done, std::max<size_t>(1, pd.nflags) * sizeof(int)));
@@ -210,6 +215,7 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   prm.wait_ns = h->wait_ns;
   prm.esize = esize;
   prm.f32_simt = h->f32_simt;
+  prm.f32_scalars64 = h->f32_scalars64;
   prm.mats = d_mats;
   prm.nmats = nmats;
   prm.trace = nullptr;
@@ -222,6 +228,12 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
     }
     prm.trace = h->d_trace;
     h->trace_len = ntasks;
+    // keep the program this trace belongs to (its queue order and dependencies)
+    h->trace_dev.resize((size_t)ntasks);
+    h->trace_deps.resize((size_t)pd.ndeps);
+    CK(h, cudaMemcpy(h->trace_dev.data(), pd.d_tasks, sizeof(bd::DevTask) * (size_t)ntasks, cudaMemcpyDeviceToHost));
+    if (pd.ndeps)
+      CK(h, cudaMemcpy(h->trace_deps.data(), pd.d_deps, sizeof(int32_t) * (size_t)pd.ndeps, cudaMemcpyDeviceToHost));
   }
   CK(h, cudaMemsetAsync(pd.d_done, 0, sizeof(int) * (size_t)pd.nflags, h->stream));
   CK(h, cudaMemsetAsync(h->d_ctrl, 0, sizeof(int), h->stream));
@@ -506,21 +518,17 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
 // Adjoint of a reduction: dL/dA from dL/dB (band storage) by the reverse sweep over the result's
 // reflectors.  The working state starts as [B; 0] and the gradient as the band gradient, both tiled
 // like A; after the sweep they hold the reconstruction of A and dL/dA.
-template <typename E>
-int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t ldab, E* d_Abar, int64_t ldabar,
-                  E* d_Arec, int64_t ldarec) {
-  if (!h) return -1;
-  if (!r || !r->pd) return fail(h, -2, "result is NULL");
-  if (r->h != h) return fail(h, -2, "result belongs to another handle");
-  if (r->esize != (int)sizeof(E)) return fail(h, -2, "result has the other storage precision");
-  if (!d_abbar) return fail(h, -3, "band gradient is NULL");
-  if (ldab < r->nb + 1) return fail(h, -4, "ldab < nb + 1");
-  if (!d_Abar) return fail(h, -5, "A_bar is NULL");
-  if (ldabar < r->m) return fail(h, -6, "ldabar < m");
-  if (d_Arec && ldarec < r->m) return fail(h, -8, "ldarec < m");
-  CK(h, cudaSetDevice(h->device));
+// Adjoint program of a result (built and uploaded on first use, cached on its plan) and the sizes of
+// one adjoint call's device workspace.
+struct AdjointSizes {
+  int hw = 0;            // column chunk of the update adjoints
+  int red_ctas = 0;      // executor CTAs (each gets nb x ib elements of panel-adjoint scratch)
+  int64_t bytes = 0;     // state + gradient tiles, partial-slot storage, panel-adjoint scratch
+};
+
+int adjoint_setup(bidiag_handle h, bidiag_result_t r, int esize, AdjointSizes* z) {
   const bd::Plan& pl = r->pd->plan;
-  const int nb = r->nb, ib = r->ib, esize = (int)sizeof(E);
+  const int nb = r->nb, ib = r->ib;
   const int bi = esize == 8 ? 0 : 1;
   if (!r->pd->bwd[bi]) {
     auto bw = std::make_shared<BwdDev>();
@@ -541,8 +549,37 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
     r->pd->bwd[bi] = bw;
   }
   const BwdDev& bw = *r->pd->bwd[bi];
-  const int hw = bd::choose_bwd_chunk(nb, ib, bw.bp.strip_w, h->smem_optin, esize);
-  if (!hw) return fail(h, BIDIAG_ERR_UNSUPPORTED, "the adjoint of this tile size / inner blocking needs more shared memory");
+  z->hw = bd::choose_bwd_chunk(nb, ib, bw.bp.strip_w, h->smem_optin, esize);
+  if (!z->hw) return fail(h, BIDIAG_ERR_UNSUPPORTED, "the adjoint of this tile size / inner blocking needs more shared memory");
+  const size_t smem = bd::bwd_smem_bytes(nb, ib, z->hw, esize);
+  CK(h, bd::exec_set_smem(smem, esize, true));
+  z->red_ctas = h->nsm * std::max(1, bd::exec_max_ctas_per_sm(smem, esize, true));
+  const int64_t tiles = (int64_t)r->p * r->q + (r->tiles2 ? (int64_t)r->q * r->q : 0);
+  z->bytes = (int64_t)esize * (2 * tiles * nb * nb + std::max<int64_t>(1, bw.bp.slot_off.back()) +
+                               (int64_t)z->red_ctas * nb * ib);
+  return BIDIAG_OK;
+}
+
+template <typename E>
+int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t ldab, E* d_Abar, int64_t ldabar,
+                  E* d_Arec, int64_t ldarec) {
+  if (!h) return -1;
+  if (!r || !r->pd) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result belongs to another handle");
+  if (r->esize != (int)sizeof(E)) return fail(h, -2, "result has the other storage precision");
+  if (!d_abbar) return fail(h, -3, "band gradient is NULL");
+  if (ldab < r->nb + 1) return fail(h, -4, "ldab < nb + 1");
+  if (!d_Abar) return fail(h, -5, "A_bar is NULL");
+  if (ldabar < r->m) return fail(h, -6, "ldabar < m");
+  if (d_Arec && ldarec < r->m) return fail(h, -8, "ldarec < m");
+  CK(h, cudaSetDevice(h->device));
+  const bd::Plan& pl = r->pd->plan;
+  const int nb = r->nb, ib = r->ib, esize = (int)sizeof(E);
+  AdjointSizes z{};
+  int rc0 = adjoint_setup(h, r, esize, &z);
+  if (rc0) return rc0;
+  const BwdDev& bw = *r->pd->bwd[esize == 8 ? 0 : 1];
+  const int hw = z.hw;
   // Working state and gradient, tiled like the forward's buffers: S / G mirror the A tiles (p x q);
   // for R-BiDiag, S2 / G2 mirror the R copy (q x q).  Start: the band lives in the last buffer the
   // forward wrote (A tiles for BiDiag, the R copy for R-BiDiag); for R-BiDiag the A tiles' state is the
@@ -558,7 +595,7 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
   if (!rc && rb) rc = dev_alloc(h, &S2, (size_t)ntiles2 * tile_elems);
   if (!rc && rb) rc = dev_alloc(h, &G2, (size_t)ntiles2 * tile_elems);
   if (!rc) rc = dev_alloc(h, &part, (size_t)std::max<int64_t>(1, bw.bp.slot_off.back()));
-  if (!rc) rc = dev_alloc(h, &red, (size_t)std::max(1, pl.npanels) * tile_elems);
+  if (!rc) rc = dev_alloc(h, &red, (size_t)z.red_ctas * nb * ib);
   auto release = [&]() {
     for (E* x : {S, G, S2, G2, part, red})
       if (x) cudaFreeAsync(x, h->stream);
@@ -600,6 +637,7 @@ int backward_impl(bidiag_handle h, bidiag_result_t r, const E* d_abbar, int64_t 
   bp.nslots = (int32_t)(bw.bp.slot_off.size() - 1);
   bp.pinfo = bw.d_pinfo;
   bp.red = red;
+  bp.red_ctas = z.red_ctas;
   bp.hw = hw;
   bp.pu_split = bw.bp.pu_split;
   const void* bx[3] = {S2, G, G2};
@@ -676,7 +714,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
             o.tree = tree_in ? tree_in[b] : BIDIAG_AUTO;
             o.variant = var_in ? var_in[b] : BIDIAG_AUTO_VARIANT;
           } else {
-            bd::autotune(m[b], n[b], h->nsm, &o.nb, &o.ib, &o.tree, &o.variant);
+            bd::autotune(m[b], n[b], h->nsm, esize, &o.nb, &o.ib, &o.tree, &o.variant);
             if (tree_in) o.tree = tree_in[b];
             if (var_in) o.variant = var_in[b];
           }
@@ -886,7 +924,7 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
       h->debug_unset = value != 0;
       return BIDIAG_OK;
     case BIDIAG_OPT_STRIP:
-      if (value != 16 && value != 32) return -3;
+      if (value != 16 && value != 32 && value != 64) return -3;
       h->strip_w = (int)value;
       return BIDIAG_OK;
     case BIDIAG_OPT_TIMING:
@@ -898,6 +936,10 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
     case BIDIAG_OPT_F32_UPDATES:
       if (value != 0 && value != 1) return -3;
       h->f32_simt = (int)value;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_F32_SCALARS:
+      if (value != 0 && value != 1) return -3;
+      h->f32_scalars64 = (int)value;
       return BIDIAG_OK;
     default:
       return -2;
@@ -926,12 +968,13 @@ int bidiag_band_batched_f32(bidiag_handle h, int64_t count, const int64_t* m, co
   return band_batched_impl(h, count, m, n, d_A, lda, nb, ib, tree, variant, out);
 }
 
-int bidiag_autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant) {
+int bidiag_autotune(int64_t m, int64_t n, int nsm, int elem_bytes, int* nb, int* ib, int* tree, int* variant) {
   if (m < 1 || n < 1 || m < n) return -1;
   if (nsm < 1) return -3;
-  if (!nb || !ib || !tree || !variant) return -4;
+  if (elem_bytes != 4 && elem_bytes != 8) return -4;
+  if (!nb || !ib || !tree || !variant) return -5;
   try {
-    bd::autotune(m, n, nsm, nb, ib, tree, variant);
+    bd::autotune(m, n, nsm, elem_bytes, nb, ib, tree, variant);
   } catch (...) {
     return BIDIAG_ERR_NOMEM;
   }
@@ -1108,6 +1151,32 @@ int bidiag_last_exec_ms(bidiag_handle h, float* ms) {
   if (!ms) return -2;
   if (!h->timed || !h->ev[0]) return fail(h, BIDIAG_ERR_UNSUPPORTED, "timing was off for the last reduction");
   CK(h, cudaEventElapsedTime(ms, h->ev[0], h->ev[1]));
+  return BIDIAG_OK;
+}
+
+int bidiag_backward_workspace(bidiag_handle h, bidiag_result_t r, int64_t* bytes) {
+  if (!h) return -1;
+  if (!r || !r->pd) return fail(h, -2, "result is NULL");
+  if (r->h != h) return fail(h, -2, "result belongs to another handle");
+  if (!bytes) return -3;
+  CK(h, cudaSetDevice(h->device));
+  AdjointSizes z{};
+  const int rc = adjoint_setup(h, r, r->esize, &z);
+  if (rc) return rc;
+  *bytes = z.bytes;
+  return BIDIAG_OK;
+}
+
+int bidiag_trace_program(bidiag_handle h, int32_t* program, int64_t cap, int64_t* count, int32_t* deps, int64_t dcap,
+                         int64_t* ndeps) {
+  if (!h) return -1;
+  if (!count) return -4;
+  if (!ndeps) return -7;
+  *count = (int64_t)h->trace_dev.size();
+  *ndeps = (int64_t)h->trace_deps.size();
+  if (h->trace_dev.empty()) return fail(h, BIDIAG_ERR_UNSUPPORTED, "no traced reduction");
+  if (program && cap >= *count) std::memcpy(program, h->trace_dev.data(), sizeof(bd::DevTask) * (size_t)*count);
+  if (deps && dcap >= *ndeps && *ndeps) std::memcpy(deps, h->trace_deps.data(), sizeof(int32_t) * (size_t)*ndeps);
   return BIDIAG_OK;
 }
 

@@ -78,7 +78,7 @@ __host__ __device__ inline int rm_ld(int n, int esize) {
 // element type at offsets (in elements) that keep 16-byte alignment.
 struct Layout {
   int lp, lv, lc;            // col-major panel ld; row-major V ld; row-major C / W ld
-  int P, V, Cs, Ct, Rt, Tb, G, W, W2, total;
+  int P, V, Vh, Cs, Ct, Rt, Tb, G, W, W2, total;
 };
 // tau[<= 64], red[32]; the adjoint panel also uses three more arrays of 64 doubles
 constexpr int kHeaderDoubles = 64 + 32 + 3 * 64;
@@ -92,7 +92,7 @@ __host__ __device__ inline Layout layout_panel(int nb, int ib, int esize) {
   L.Rt = o;  o = align4(o + ib * ib);
   L.Tb = o;  o = align4(o + ib * ib);
   L.G = o;   o = align4(o + 2 * ib * ib);   // Gram matrix and a scratch block for T
-  L.V = L.Cs = L.Ct = L.W = L.W2 = -1;
+  L.V = L.Vh = L.Cs = L.Ct = L.W = L.W2 = -1;
   L.total = o;
   return L;
 }
@@ -108,6 +108,10 @@ __host__ __device__ inline Layout layout_update(int nb, int ib, int w, int esize
   L.Tb = o;  o = align4(o + ib * ib);
   L.W = o;   o = align4(o + ib * L.lc);
   L.W2 = o;  o = align4(o + ib * L.lc);
+  L.Vh = -1;
+  if (esize == 4) {          // FP32 storage: TF32 high parts of V (V itself then holds the low parts)
+    L.Vh = o;  o = align4(o + nb * L.lv);
+  }
   L.P = L.Rt = L.G = -1;
   L.total = o;
   return L;
@@ -118,7 +122,7 @@ __host__ __device__ inline Layout layout_update(int nb, int ib, int w, int esize
 // tails, state and gradient of one column block (column-major, ld lp), the top triangles and S.
 struct BwdLayout {
   int lc, lv, lp;
-  int Cs, Cg, Cts, Ctg, V, Tb, W, W2s, W2g, Ms, Mg, Rts, Rtg, Sb, Sc, total;
+  int Cs, Cg, Cts, Ctg, V, Vh, Tb, W, W2s, W2g, Ms, Mg, Rts, Rtg, Sb, Sc, total;
 };
 __host__ __device__ inline BwdLayout layout_bwd_update(int nb, int ib, int hw, int esize) {
   BwdLayout L{};
@@ -135,6 +139,10 @@ __host__ __device__ inline BwdLayout layout_bwd_update(int nb, int ib, int hw, i
   L.W = o;   o = align4(o + ib * L.lc);
   L.W2s = o; o = align4(o + ib * L.lc);
   L.W2g = o; o = align4(o + ib * L.lc);
+  L.Vh = -1;
+  if (esize == 4) {          // FP32 storage: TF32 high parts of V
+    L.Vh = o;  o = align4(o + nb * L.lv);
+  }
   L.Ms = L.Mg = L.Rts = L.Rtg = L.Sb = L.Sc = -1;
   L.total = o;
   return L;
@@ -151,7 +159,7 @@ __host__ __device__ inline BwdLayout layout_bwd_panel(int nb, int ib, int esize)
   L.Rtg = o; o = align4(o + ib * ib);
   L.Sb = o;  o = align4(o + ib * ib);
   L.Sc = o;  o = align4(o + (2 * ib + kThreads) * (8 / esize));   // doubles: reciprocals, row-sum partials
-  L.Cs = L.Cg = L.Cts = L.Ctg = L.Tb = L.W = L.W2s = L.W2g = -1;
+  L.Cs = L.Cg = L.Cts = L.Ctg = L.Tb = L.W = L.W2s = L.W2g = L.Vh = -1;
   L.total = o;
   return L;
 }
@@ -167,14 +175,34 @@ __device__ __forceinline__ E masked_ld(const E* g, int R, int C, int nb, int tr,
   return ldg(g + toff(R, C, nb, tr));
 }
 
+__device__ __forceinline__ uint32_t tf32_round(float x);
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo);
+
+// Stores v at index i of s, or (FP32 storage, hi != null) its TF32 high part at hi[i] and low part at
+// s[i] (the operands of the three-product tensor-core contraction).
+template <typename E>
+__device__ __forceinline__ void put(E* s, E* hi, int i, E v) {
+  if constexpr (sizeof(E) == 4) {
+    if (hi) {
+      uint32_t h, l;
+      split_tf32(v, h, l);
+      hi[i] = __uint_as_float(h);
+      s[i] = __uint_as_float(l);
+      return;
+    }
+  }
+  s[i] = v;
+}
+
 // Shared element (r, c) at s[r * rs + c * cs] <- oriented X(r0 + r, c0 + c).  M_UPPER zeroes entries
 // below the diagonal, M_UNITLOWER gives the unit lower trapezoid.  Lanes run along the contiguous
 // direction of global memory (rows for tr = 0, columns for tr = 1).  Blocks of at most 256 x 32 (every
 // block the sub-tasks move) issue all of a thread's loads (up to 32) before the first shared store, so
-// that one L2 latency covers the whole block.
+// that one L2 latency covers the whole block.  With hi != null (FP32) the block is stored split: TF32
+// high parts in hi, low parts in s (same indexing).
 template <typename E>
 __device__ void load_tile(E* s, int rs, int cs, const E* g, int nb, int tr, int r0, int c0, int rows, int cols,
-                          int mask) {
+                          int mask, E* hi = nullptr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (rows <= 256 && cols <= 32) {
     E v[32];
@@ -192,7 +220,7 @@ __device__ void load_tile(E* s, int rs, int cs, const E* g, int nb, int tr, int 
 #pragma unroll
         for (int kr = 0; kr < 8; ++kr) {
           const int c = warp + 8 * kc, r = lane + 32 * kr;
-          if (c < cols && r < rows) s[r * rs + c * cs] = v[kc * 8 + kr];
+          if (c < cols && r < rows) put(s, hi, r * rs + c * cs, v[kc * 8 + kr]);
         }
       }
     } else {     // r = warp + 8 kr, c = lane
@@ -204,7 +232,7 @@ __device__ void load_tile(E* s, int rs, int cs, const E* g, int nb, int tr, int 
 #pragma unroll
       for (int kr = 0; kr < 32; ++kr) {
         const int r = warp + 8 * kr;
-        if (lane < cols && r < rows) s[r * rs + lane * cs] = v[kr];
+        if (lane < cols && r < rows) put(s, hi, r * rs + lane * cs, v[kr]);
       }
     }
     return;
@@ -212,12 +240,12 @@ __device__ void load_tile(E* s, int rs, int cs, const E* g, int nb, int tr, int 
   if (!tr) {
     for (int c = warp; c < cols; c += kWarps) {
 #pragma unroll 4
-      for (int r = lane; r < rows; r += 32) s[r * rs + c * cs] = masked_ld(g, r0 + r, c0 + c, nb, tr, mask);
+      for (int r = lane; r < rows; r += 32) put(s, hi, r * rs + c * cs, masked_ld(g, r0 + r, c0 + c, nb, tr, mask));
     }
   } else {
 #pragma unroll 4
     for (int r = warp; r < rows; r += kWarps) {
-      for (int c = lane; c < cols; c += 32) s[r * rs + c * cs] = masked_ld(g, r0 + r, c0 + c, nb, tr, mask);
+      for (int c = lane; c < cols; c += 32) put(s, hi, r * rs + c * cs, masked_ld(g, r0 + r, c0 + c, nb, tr, mask));
     }
   }
 }
@@ -254,16 +282,83 @@ __device__ __forceinline__ E warp_sum(E v) {
 
 enum PanelMode : int { PM_GE = 0, PM_TS = 1, PM_TT = 2 };
 
+// Error-free transformations of FP32 numbers (the _rn intrinsics keep the compiler from contracting
+// them into FMAs): TwoSum (Knuth; Moller 1965) s + e = a + b exactly; FastTwoSum (Dekker 1971) the same
+// for |a| >= |b|.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// beta, tau and the tail scale 1 / (alpha - beta) of a reflector with FP32 storage, from alpha and the
+// tail's squared norm sh + sl (an unevaluated float pair), in float-pair arithmetic (about 44 bits):
+//   n2 = alpha^2 + sigma^2 (exact square by FMA), nrm = sqrt(n2) as y + (n2 - y^2) / (2 y) with y the
+//   rounded FP32 root (one Newton correction), beta = -sgn(alpha) nrm, d = alpha - beta (|d| = |alpha| +
+//   nrm, no cancellation), tau = (beta - alpha) / beta = 1 + |alpha| / nrm and 1 / d, each reciprocal as
+//   r0 (1 + e) with r0 the rounded FP32 reciprocal and e = 1 - x r0 its residual (one Newton step).
+// Returns the FP32 roundings of beta and tau and the scale as a float pair.  sigma^2 = 0: H = I.
+__device__ __forceinline__ void reflector_scalars_pair(float alpha, float sh, float sl, float& beta, float& tau,
+                                                       float& sch, float& scl) {
+  float s2h, s2l;
+  two_sum(sh, sl, s2h, s2l);
+  if (s2h == 0.0f) {
+    beta = alpha;
+    tau = 0.0f;
+    sch = scl = 0.0f;
+    return;
+  }
+  const float a2h = __fmul_rn(alpha, alpha), a2l = fmaf(alpha, alpha, -a2h);
+  float nh, nl;
+  two_sum(a2h, s2h, nh, nl);
+  nl = __fadd_rn(nl, __fadd_rn(a2l, s2l));
+  fast_two_sum(nh, nl, nh, nl);
+  const float y = __fsqrt_rn(nh);
+  const float res = __fadd_rn(fmaf(-y, y, nh), nl);             // n2 - y^2 (the FMA residual is exact)
+  float rh, rl;
+  fast_two_sum(y, __fmul_rn(res, __fmul_rn(0.5f, __frcp_rn(y))), rh, rl);
+  const bool neg = alpha < 0.0f;
+  const float bh = neg ? rh : -rh, bl = neg ? rl : -rl;
+  float dh, dl;
+  two_sum(alpha, -bh, dh, dl);
+  dl = __fsub_rn(dl, bl);
+  fast_two_sum(dh, dl, dh, dl);
+  const float q0 = __frcp_rn(rh);                                // 1 / nrm = q0 (1 + eq)
+  const float eq = __fsub_rn(fmaf(-rh, q0, 1.0f), __fmul_rn(rl, q0));
+  const float aa = fabsf(alpha);
+  const float ph = __fmul_rn(aa, q0);
+  const float pl = __fadd_rn(fmaf(aa, q0, -ph), __fmul_rn(ph, eq));
+  float th, tl;
+  fast_two_sum(1.0f, ph, th, tl);                                // |alpha| / nrm <= 1
+  tau = __fadd_rn(th, __fadd_rn(tl, pl));
+  const float r0 = __frcp_rn(dh);                                // 1 / d = r0 (1 + er)
+  const float er = __fsub_rn(fmaf(-dh, r0, 1.0f), __fmul_rn(dl, r0));
+  fast_two_sum(r0, __fmul_rn(r0, er), sch, scl);
+  beta = __fadd_rn(bh, bl);
+}
+
 // Unblocked factorization of kb panel columns held in P (ld lp).
 //  GE: reflector jj has alpha = P[jj, jj] and tail P[jj+1 .. rows-1, jj].
 //  TS: alpha = Rt[jj, jj] (top triangle), tail P[0 .. rows-1, jj].
 //  TT: as TS with tail P[0 .. min(rows, voff + jj + 1) - 1, jj] (the eliminated tile is a triangle).
-// The squared norm, beta, tau and the scaling of the tail are computed in FP64 whatever the storage.
+// FP64 storage: the squared norm, beta, tau and the scaling of the tail are computed in FP64.  FP32
+// storage: the squared norm is a compensated float-pair sum (FP64-level accuracy); beta, tau and the
+// scale follow in FP64 (pair_scalars false) or in float-pair arithmetic (pair_scalars true,
+// reflector_scalars_pair), both giving the FP32 values the reduction stores to within their rounding.
 template <typename E>
 __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, int lrt, int voff, double* tau_s,
-                             double* red) {
+                             double* red, bool pair_scalars = false) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* scale_s = tau_s + 96;          // 1 / (alpha - beta) of each reflector (header scratch)
+  // float-pair scalars (FP32 storage): tau and the scale pair per reflector (header doubles 160..255)
+  float* tauf_s = reinterpret_cast<float*>(tau_s + 160);
+  float* sch_s = tauf_s + 64;
+  float* scl_s = sch_s + 64;
+  const bool pairs = sizeof(E) == 4 && pair_scalars;
   auto tail = [&](int j, int& t0, int& t1) {
     if (mode == PM_GE) {
       t0 = j + 1;
@@ -292,6 +387,15 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
     tau_s[j] = tau;
     scale_s[j] = scale;
   };
+  auto scalars_pair = [&](int j, float sh, float sl) {
+    E* alpha_p = (mode == PM_GE) ? &P[j + j * lp] : &Rt[j + j * lrt];
+    float beta, tau, sch, scl;
+    reflector_scalars_pair((float)*alpha_p, sh, sl, beta, tau, sch, scl);
+    *alpha_p = (E)beta;
+    tauf_s[j] = tau;
+    sch_s[j] = sch;
+    scl_s[j] = scl;
+  };
   // The tails stay unscaled during the factorization (v = [1; scale x]): applying H_j to column c is
   // w = c_top + scale (x . c_tail), c_top -= tau w, c_tail -= (tau w scale) x, and the scaling of all
   // tails is one parallel pass at the end, off the critical chain.  Warp 0 applies H_jj to column jj + 1
@@ -300,18 +404,48 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
   if (warp == 0) {
     int t0, t1;
     tail(0, t0, t1);
-    double part = 0.0;
-    for (int r = t0 + lane; r < t1; r += 32) {
-      const double x = (double)P[r];
-      part += x * x;
+    if (pairs) {
+      float sh = 0.0f, sl = 0.0f;
+      for (int r = t0 + lane; r < t1; r += 32) {
+        const float x = (float)P[r];
+        const float p = __fmul_rn(x, x);
+        float s2, e2;
+        two_sum(sh, p, s2, e2);
+        sl = __fadd_rn(sl, __fadd_rn(e2, fmaf(x, x, -p)));
+        sh = s2;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(kFull, sh, o), ol = __shfl_xor_sync(kFull, sl, o);
+        float s2, e2;
+        two_sum(sh, oh, s2, e2);
+        sl = __fadd_rn(__fadd_rn(sl, ol), e2);
+        sh = s2;
+      }
+      if (lane == 0) scalars_pair(0, sh, sl);
+    } else {
+      double part = 0.0;
+      for (int r = t0 + lane; r < t1; r += 32) {
+        const double x = (double)P[r];
+        part += x * x;
+      }
+      part = warp_sum(part);
+      if (lane == 0) scalars(0, part);
     }
-    part = warp_sum(part);
-    if (lane == 0) scalars(0, part);
   }
   __syncthreads();
   for (int jj = 0; jj < kb; ++jj) {
-    const double tau = tau_s[jj];
-    const E se = (E)scale_s[jj];
+    // tau and the tail scale of reflector jj in the storage type (FP32 storage: rounded from the FP64
+    // values, or from the float-pair ones)
+    E tauE, se;
+    if (pairs) {
+      tauE = (E)tauf_s[jj];
+      se = (E)__fadd_rn(sch_s[jj], scl_s[jj]);
+    } else {
+      tauE = (E)tau_s[jj];
+      se = (E)scale_s[jj];
+    }
+    const bool refl = tauE != E(0);
     int t0, t1;
     tail(jj, t0, t1);
     if (warp == 0) {
@@ -333,15 +467,15 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
             sl += ((sh - (s2 - bb)) + (p - bb)) + e;
             sh = s2;
           };
-          if (tau != 0.0) {
+          if (refl) {
             float sum = 0.0f;
             for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
             sum = warp_sum(sum);
             float* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
             const float wv = *top + (float)se * sum;
             __syncwarp();
-            if (lane == 0) *top = *top - (float)tau * wv;
-            const float tw = (float)tau * wv * (float)se;
+            if (lane == 0) *top = *top - (float)tauE * wv;
+            const float tw = (float)tauE * wv * (float)se;
             for (int r = t0 + lane; r < t1; r += 32) {
               const float x = P[r + c * lp] - P[r + jj * lp] * tw;
               P[r + c * lp] = x;
@@ -359,17 +493,22 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
             sl = sl + ol + ((sh - (s2 - bb)) + (oh - bb));
             sh = s2;
           }
-          part = (double)sh + (double)sl;
+          if (pairs) {
+            __syncwarp();
+            if (lane == 0) scalars_pair(c, sh, sl);
+          } else {
+            part = (double)sh + (double)sl;
+          }
         } else {
-          if (tau != 0.0) {
+          if (refl) {
             E sum = E(0);
             for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
             sum = warp_sum(sum);
             E* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
             const E wv = *top + se * sum;
             __syncwarp();
-            if (lane == 0) *top = *top - (E)tau * wv;
-            const E tw = (E)tau * wv * se;
+            if (lane == 0) *top = *top - tauE * wv;
+            const E tw = tauE * wv * se;
             for (int r = t0 + lane; r < t1; r += 32) {
               const E x = P[r + c * lp] - P[r + jj * lp] * tw;
               P[r + c * lp] = x;
@@ -388,10 +527,10 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
           part = warp_sum(part);
         }
         __syncwarp();
-        if (lane == 0) scalars(c, part);
+        if (lane == 0 && !pairs) scalars(c, part);
       }
-    } else if (tau != 0.0) {
-      const E taue = (E)tau;
+    } else if (refl) {
+      const E taue = tauE;
       for (int c = jj + 2 + (warp - 1); c < kb; c += kWarps - 1) {
         E sum = E(0);
         for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
@@ -406,12 +545,22 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
     }
     __syncthreads();
   }
-  // scale the tails
+  // scale the tails (float-pair scalars: x (sh + sl) rounded once, by an FMA residual; their tau also
+  // goes to the FP64 array the T factor reads)
   for (int jj = warp; jj < kb; jj += kWarps) {
     int t0, t1;
     tail(jj, t0, t1);
-    const double sc = scale_s[jj];
-    for (int r = t0 + lane; r < t1; r += 32) P[r + jj * lp] = (E)((double)P[r + jj * lp] * sc);
+    if (pairs) {
+      const float sh = sch_s[jj], sl = scl_s[jj];
+      if (lane == 0) tau_s[jj] = (double)tauf_s[jj];
+      for (int r = t0 + lane; r < t1; r += 32) {
+        const float x = (float)P[r + jj * lp], p = __fmul_rn(x, sh);
+        P[r + jj * lp] = (E)__fadd_rn(p, fmaf(x, sl, fmaf(x, sh, -p)));
+      }
+    } else {
+      const double sc = scale_s[jj];
+      for (int r = t0 + lane; r < t1; r += 32) P[r + jj * lp] = (E)((double)P[r + jj * lp] * sc);
+    }
   }
   __syncthreads();
 }
@@ -521,13 +670,14 @@ __device__ void build_t(int mode, const E* P, int lp, int rows, int kb, int voff
 // Fragment layout (lane = 4 g + t): A (16 x 8, row) a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
 // B (8 x 8, col) b0 (t, g), b1 (t+4, g); C (16 x 8) c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
 // ---------------------------------------------------------------------------------------------
+// TF32 rounding of an FP32 value: round to nearest with ties away from zero to the 10 explicit mantissa
+// bits of TF32, i.e. add half the weight of the 13 dropped bits to the magnitude and clear them.  Done
+// on the integer units (the conversion instruction is a low-throughput one, and the split operands of
+// an update strip make it the bottleneck of the contraction).  Finite inputs only (tile data).
+__device__ __forceinline__ uint32_t tf32_round(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  uint32_t h, l;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  const float r = x - __uint_as_float(h);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
-  hi = h;
-  lo = l;
+  hi = tf32_round(x);
+  lo = tf32_round(x - __uint_as_float(hi));    // x - hi is exact in FP32
 }
 __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -539,10 +689,9 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint
 // The tensor core's FP32 accumulation truncates, so one k8-step's three products go into a fresh
 // accumulator that is then added to the running sum with a correctly rounded FP32 add: the truncation
 // error stays relative to one step's partial sum instead of growing with K.
-__device__ __forceinline__ void mma_3xtf32(float* acc, const float* a, const float* b) {
-  uint32_t ah[4], al[4], bh[2], bl[2];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
+// A operand already split (hi / lo TF32 words), B split here.
+__device__ __forceinline__ void mma_3xtf32(float* acc, const uint32_t* ah, const uint32_t* al, const float* b) {
+  uint32_t bh[2], bl[2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) split_tf32(b[i], bh[i], bl[i]);
   float part[4] = {0.f, 0.f, 0.f, 0.f};
@@ -552,6 +701,7 @@ __device__ __forceinline__ void mma_3xtf32(float* acc, const float* a, const flo
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc[i] += part[i];
 }
+
 
 // Block reflector application on row-major shared operands:
 //   W = op(T) (Ct + V^T C),  Ct -= W,  C -= V W
@@ -638,8 +788,9 @@ __device__ void apply_phase3_simt(const E* V, int lv, int vrows, int kb, E* C, i
 }
 
 // Tensor-core phase 1 (FP32): W[a][c] = Ct[a][c] + sum_r V[r][a] C[r][c]; M = kb, N = ncols, K = vrows.
-__device__ void apply_phase1_tc(const float* V, int lv, int vrows, int kb, const float* Ct, const float* C, int lc,
-                                int ncols, float* W) {
+// Vh / Vl: the TF32 high / low parts of V (split_v_tf32).
+__device__ void apply_phase1_tc(const float* Vh, const float* Vl, int lv, int vrows, int kb, const float* Ct,
+                                const float* C, int lc, int ncols, float* W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int mt_n = kb >> 4, nt_n = ncols >> 3;
   for (int tile = warp; tile < mt_n * nt_n; tile += kWarps) {
@@ -653,14 +804,13 @@ __device__ void apply_phase1_tc(const float* V, int lv, int vrows, int kb, const
     }
 #pragma unroll 4
     for (int k0 = 0; k0 < vrows; k0 += 8) {   // the three-product chains of 4 k-steps overlap
-      float a[4], b[2];
-      a[0] = V[(k0 + t) * lv + m0 + g];
-      a[1] = V[(k0 + t) * lv + m0 + g + 8];
-      a[2] = V[(k0 + t + 4) * lv + m0 + g];
-      a[3] = V[(k0 + t + 4) * lv + m0 + g + 8];
-      b[0] = C[(k0 + t) * lc + n0 + g];
-      b[1] = C[(k0 + t + 4) * lc + n0 + g];
-      mma_3xtf32(acc, a, b);
+      const int i0 = (k0 + t) * lv + m0 + g, i1 = (k0 + t + 4) * lv + m0 + g;
+      const uint32_t ah[4] = {__float_as_uint(Vh[i0]), __float_as_uint(Vh[i0 + 8]), __float_as_uint(Vh[i1]),
+                              __float_as_uint(Vh[i1 + 8])};
+      const uint32_t al[4] = {__float_as_uint(Vl[i0]), __float_as_uint(Vl[i0 + 8]), __float_as_uint(Vl[i1]),
+                              __float_as_uint(Vl[i1 + 8])};
+      const float b[2] = {C[(k0 + t) * lc + n0 + g], C[(k0 + t + 4) * lc + n0 + g]};
+      mma_3xtf32(acc, ah, al, b);
     }
     W[(m0 + g) * lc + n0 + 2 * t] = acc[0];
     W[(m0 + g) * lc + n0 + 2 * t + 1] = acc[1];
@@ -669,42 +819,66 @@ __device__ void apply_phase1_tc(const float* V, int lv, int vrows, int kb, const
   }
 }
 
-// Tensor-core phase 3 (FP32): C[r][c] -= sum_a V[r][a] W2[a][c]; M = vrows, N = ncols, K = kb.
-__device__ void apply_phase3_tc(const float* V, int lv, int vrows, int kb, float* C, int lc, int ncols,
-                                const float* W2) {
+// Tensor-core phase 3 (FP32): C[r][c] -= sum_a V[r][a] W2[a][c]; M = vrows, N = ncols, K = kb.  The
+// product is formed as V (-W2), so the split V parts serve unchanged (TF32 rounding is symmetric).
+__device__ void apply_phase3_tc(const float* Vh, const float* Vl, int lv, int vrows, int kb, float* C, int lc,
+                                int ncols, const float* W2) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int mt_n = vrows >> 4, nt_n = ncols >> 3;
-  for (int tile = warp; tile < mt_n * nt_n; tile += kWarps) {
-    const int m0 = (tile % mt_n) << 4, n0 = (tile / mt_n) << 3;
-    float* c0p = C + (m0 + g) * lc + n0 + 2 * t;
-    float* c1p = C + (m0 + g + 8) * lc + n0 + 2 * t;
-    float acc[4] = {c0p[0], c0p[1], c1p[0], c1p[1]};
+  const int mt_n = vrows >> 4, np_n = (ncols + 15) >> 4;      // m-tiles, pairs of n-tiles
+  // unit = one m-tile x two n-tiles: the A fragments of a k-step serve both n-tiles
+  for (int u = warp; u < mt_n * np_n; u += kWarps) {
+    const int m0 = (u % mt_n) << 4, n0 = (u / mt_n) << 4;
+    const bool two = n0 + 8 < ncols;
+    float* c00 = C + (m0 + g) * lc + n0 + 2 * t;
+    float* c10 = C + (m0 + g + 8) * lc + n0 + 2 * t;
+    float acc0[4] = {c00[0], c00[1], c10[0], c10[1]};
+    float acc1[4] = {0.f, 0.f, 0.f, 0.f};
+    if (two) {
+      acc1[0] = c00[8]; acc1[1] = c00[9]; acc1[2] = c10[8]; acc1[3] = c10[9];
+    }
 #pragma unroll 4
     for (int k0 = 0; k0 < kb; k0 += 8) {
-      float a[4], b[2];
-      a[0] = -V[(m0 + g) * lv + k0 + t];
-      a[1] = -V[(m0 + g + 8) * lv + k0 + t];
-      a[2] = -V[(m0 + g) * lv + k0 + t + 4];
-      a[3] = -V[(m0 + g + 8) * lv + k0 + t + 4];
-      b[0] = W2[(k0 + t) * lc + n0 + g];
-      b[1] = W2[(k0 + t + 4) * lc + n0 + g];
-      mma_3xtf32(acc, a, b);
+      const int i0 = (m0 + g) * lv + k0 + t, i1 = (m0 + g + 8) * lv + k0 + t;
+      const uint32_t ah[4] = {__float_as_uint(Vh[i0]), __float_as_uint(Vh[i1]), __float_as_uint(Vh[i0 + 4]),
+                              __float_as_uint(Vh[i1 + 4])};
+      const uint32_t al[4] = {__float_as_uint(Vl[i0]), __float_as_uint(Vl[i1]), __float_as_uint(Vl[i0 + 4]),
+                              __float_as_uint(Vl[i1 + 4])};
+      const float b0[2] = {-W2[(k0 + t) * lc + n0 + g], -W2[(k0 + t + 4) * lc + n0 + g]};
+      mma_3xtf32(acc0, ah, al, b0);
+      if (two) {
+        const float b1[2] = {-W2[(k0 + t) * lc + n0 + 8 + g], -W2[(k0 + t + 4) * lc + n0 + 8 + g]};
+        mma_3xtf32(acc1, ah, al, b1);
+      }
     }
-    c0p[0] = acc[0];
-    c0p[1] = acc[1];
-    c1p[0] = acc[2];
-    c1p[1] = acc[3];
+    c00[0] = acc0[0];
+    c00[1] = acc0[1];
+    c10[0] = acc0[2];
+    c10[1] = acc0[3];
+    if (two) {
+      c00[8] = acc1[0];
+      c00[9] = acc1[1];
+      c10[8] = acc1[2];
+      c10[9] = acc1[3];
+    }
   }
 }
 
+// FP32 storage applies a block on the tensor cores when the fragment shapes tile it exactly.
 template <typename E>
-__device__ void apply_rm(const E* V, int lv, int vrows, int kb, const E* Tb, bool notrans, E* Ct, E* C, int lc,
-                         int ncols, E* W, E* W2, bool simt) {
+__device__ __forceinline__ bool use_tc(bool simt, int kb, int vrows, int ncols) {
+  return sizeof(E) == 4 && !simt && (kb & 15) == 0 && (vrows & 15) == 0 && (ncols & 7) == 0;
+}
+
+// Vh != null (FP32 storage, V loaded split by load_tile): phases 1 and 3 on the tensor cores with V = TF32 low parts and
+// Vh = high parts; otherwise V holds the values and the phases run on the FMA units.
+template <typename E>
+__device__ void apply_rm(const E* V, const E* Vh, int lv, int vrows, int kb, const E* Tb, bool notrans, E* Ct, E* C,
+                         int lc, int ncols, E* W, E* W2) {
   constexpr bool kF32 = sizeof(E) == 4;
-  const bool tc = kF32 && !simt && (kb & 15) == 0 && (vrows & 15) == 0 && (ncols & 7) == 0;
+  const bool tc = kF32 && Vh != nullptr;
   // phase 1
   if constexpr (kF32) {
-    if (tc) apply_phase1_tc(V, lv, vrows, kb, Ct, C, lc, ncols, W);
+    if (tc) apply_phase1_tc(Vh, V, lv, vrows, kb, Ct, C, lc, ncols, W);
     else apply_phase1_simt(V, lv, vrows, kb, Ct, C, lc, ncols, W);
   } else {
     apply_phase1_simt(V, lv, vrows, kb, Ct, C, lc, ncols, W);
@@ -743,7 +917,7 @@ __device__ void apply_rm(const E* V, int lv, int vrows, int kb, const E* Tb, boo
   __syncthreads();
   // phase 3: C -= V W2
   if constexpr (kF32) {
-    if (tc) apply_phase3_tc(V, lv, vrows, kb, C, lc, ncols, W2);
+    if (tc) apply_phase3_tc(Vh, V, lv, vrows, kb, C, lc, ncols, W2);
     else apply_phase3_simt(V, lv, vrows, kb, C, lc, ncols, W2);
   } else {
     apply_phase3_simt(V, lv, vrows, kb, C, lc, ncols, W2);
@@ -758,7 +932,8 @@ __device__ void apply_rm(const E* V, int lv, int vrows, int kb, const E* Tb, boo
 // part of X (rows 0 .. b*ib + ib - 1).  The later column blocks are updated by PU sub-tasks.
 // ---------------------------------------------------------------------------------------------
 template <typename E>
-__device__ void task_panel_factor(unsigned char* smb, int kind, E* X, E* A, int tr, E* Tg, int nb, int ib, int b) {
+__device__ void task_panel_factor(unsigned char* smb, int kind, E* X, E* A, int tr, E* Tg, int nb, int ib, int b,
+                                  bool pair_scalars) {
   const Layout L = layout_panel(nb, ib, (int)sizeof(E));
   double* tau = reinterpret_cast<double*>(smb);
   double* red = tau + 64;
@@ -769,7 +944,7 @@ __device__ void task_panel_factor(unsigned char* smb, int kind, E* X, E* A, int 
     const int rows = nb - c0;
     load_tile(P, 1, L.lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
     __syncthreads();
-    factor_panel(PM_GE, P, L.lp, rows, kb, (E*)nullptr, 0, 0, tau, red);
+    factor_panel(PM_GE, P, L.lp, rows, kb, (E*)nullptr, 0, 0, tau, red, pair_scalars);
     build_t(PM_GE, P, L.lp, rows, kb, 0, tau, Tb, kb, G);
     store_tile(P, 1, L.lp, X, nb, tr, c0, c0, rows, kb, M_NONE);
   } else {
@@ -778,7 +953,7 @@ __device__ void task_panel_factor(unsigned char* smb, int kind, E* X, E* A, int 
     load_tile(Rt, 1, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
     load_tile(P, 1, L.lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
     __syncthreads();
-    factor_panel(kind, P, L.lp, vrows, kb, Rt, kb, c0, tau, red);
+    factor_panel(kind, P, L.lp, vrows, kb, Rt, kb, c0, tau, red, pair_scalars);
     build_t(kind, P, L.lp, vrows, kb, c0, tau, Tb, kb, G);
     store_tile(Rt, 1, kb, A, nb, tr, c0, c0, kb, kb, M_UPPER);
     store_tile(P, 1, L.lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
@@ -808,20 +983,32 @@ __device__ void task_update(unsigned char* smb, int type, const E* X, E* Cp, E* 
     int vrows;
     E* Cb;
     E* Ctop = nullptr;
+    // T's loads are issued first so that their latency overlaps the loads of V
+    E tv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = threadIdx.x + k * kThreads;
+      tv[k] = o < kb * kb ? ldg(Tg + (size_t)c0 * ib + o) : E(0);
+    }
+    vrows = (type == UNMQR) ? nb - c0 : ((type == TSMQR) ? nb : c0 + kb);
+    E* Vh = (L.Vh >= 0 && use_tc<E>(simt, kb, vrows, ncols)) ? sm + L.Vh : nullptr;
     if (type == UNMQR) {
-      vrows = nb - c0;
-      load_tile(V, L.lv, 1, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+      load_tile(V, L.lv, 1, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER, Vh);
       Cb = Cs + c0 * L.lc;
     } else {
-      vrows = (type == TSMQR) ? nb : c0 + kb;
-      load_tile(V, L.lv, 1, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER);
+      load_tile(V, L.lv, 1, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER, Vh);
       load_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
       Ctop = Ct;
       Cb = Cs;
     }
-    for (int o = threadIdx.x; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = threadIdx.x + k * kThreads;
+      if (o < kb * kb) Tb[o] = tv[k];
+    }
+    for (int o = threadIdx.x + 4 * kThreads; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
     __syncthreads();
-    apply_rm(V, L.lv, vrows, kb, Tb, notrans, Ctop, Cb, L.lc, ncols, W, W2, simt);
+    apply_rm(V, Vh, L.lv, vrows, kb, Tb, notrans, Ctop, Cb, L.lc, ncols, W, W2);
     if (Ctop) {
       store_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
       __syncthreads();
@@ -949,16 +1136,15 @@ __device__ void task_bwd_update(unsigned char* smb, int type, const E* X, E* Cp_
     for (int bb = 0; bb < nbk; ++bb) {
       const int b = blk1 - 1 - bb;
       const int c0 = b * ib, kb = ib;
-      int vrows;
       E *Cbs, *Cbg, *Tops = nullptr, *Topg = nullptr;
+      const int vrows = (type == UNMQR) ? nb - c0 : ((type == TSMQR) ? nb : c0 + kb);
+      E* Vh = (L.Vh >= 0 && use_tc<E>(simt, kb, vrows, nc)) ? sm + L.Vh : nullptr;
       if (type == UNMQR) {
-        vrows = nb - c0;
-        load_tile(V, lv, 1, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+        load_tile(V, lv, 1, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER, Vh);
         Cbs = Cs + c0 * lc;
         Cbg = Cg + c0 * lc;
       } else {
-        vrows = (type == TSMQR) ? nb : c0 + kb;
-        load_tile(V, lv, 1, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER);
+        load_tile(V, lv, 1, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER, Vh);
         load_tile(Cts, lc, 1, Cp_s, nb, tr, c0, col0 + ch, kb, nc, M_NONE);
         load_tile(Ctg, lc, 1, Cp_g, nb, tr, c0, col0 + ch, kb, nc, M_NONE);
         Tops = Cts;
@@ -968,8 +1154,8 @@ __device__ void task_bwd_update(unsigned char* smb, int type, const E* X, E* Cp_
       }
       for (int o = threadIdx.x; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
       __syncthreads();
-      apply_rm(V, lv, vrows, kb, Tb, true, Tops, Cbs, lc, nc, W, W2s, simt);
-      apply_rm(V, lv, vrows, kb, Tb, true, Topg, Cbg, lc, nc, W, W2g, simt);
+      apply_rm(V, Vh, lv, vrows, kb, Tb, true, Tops, Cbs, lc, nc, W, W2s);
+      apply_rm(V, Vh, lv, vrows, kb, Tb, true, Topg, Cbg, lc, nc, W, W2g);
       bwd_partial(Cbs, Cbg, lc, vrows, kb, nc, W2s, W2g, slot + (size_t)(b - blk0) * pstride,
                   slot + sbase + (size_t)(b - blk0) * kb * kb, ch > 0);
       if (Tops) {
@@ -1009,7 +1195,7 @@ __device__ void task_bwd_panel(unsigned char* smb, int kind, const E* X, E* A_s,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool ge = kind == PM_GE, tt = kind == PM_TT;
   const int vrows = ge ? nb - c0 : (kind == PM_TS ? nb : c0 + kb);
-  E* redb = red + (size_t)b * nb * ib;
+  E* redb = red;            // this CTA's nb x ib scratch
   if (ge) load_tile(V, 1, lp, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
   else load_tile(V, 1, lp, X, nb, tr, 0, c0, vrows, kb, tt ? M_UPPER : M_NONE);
   for (int k = threadIdx.x; k < kb; k += kThreads) tau[k] = (double)ldg(Tg + (size_t)c0 * ib + k + k * ib);
@@ -1354,7 +1540,8 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     switch (type) {
       case PF: {
         E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
-        if (ok && Tg && blk < nblk && kind <= PM_TT) task_panel_factor(smb, kind, X, A, tr, Tg, nb, ib, blk);
+        if (ok && Tg && blk < nblk && kind <= PM_TT)
+          task_panel_factor(smb, kind, X, A, tr, Tg, nb, ib, blk, prm.f32_scalars64 == 0);
         else ok = false;
         break;
       }
@@ -1397,7 +1584,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         E* Ag = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, grad_ref(t.a), ok);
         E* Xs = tile_ptr<E>(prm, mv, t.c, ok);
         E* Xg = tile_ptr<E>(prm, mv, grad_ref(t.c), ok);
-        if (ok && Tg && blk < nblk && kind <= PM_TT && bw.part && bw.red) {
+        if (ok && Tg && blk < nblk && kind <= PM_TT && bw.part && bw.red && (int)blockIdx.x < bw.red_ctas) {
           const int32_t* pi = bw.pinfo + 4 * t.tslot;
           // the update strips' sum comes from the reduced slot when the panel has one
           const int u0 = pi[3] >= 0 ? pi[3] : pi[0], nu = pi[3] >= 0 ? 1 : pi[1], pu0 = pi[2];
@@ -1407,7 +1594,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
             ok = false;
           } else {
             task_bwd_panel(smb, kind, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, blk, static_cast<const E*>(bw.part),
-                           bw.slot_off, u0, nu, pu0, pus, static_cast<E*>(bw.red) + (size_t)t.tslot * nb * nb);
+                           bw.slot_off, u0, nu, pu0, pus, static_cast<E*>(bw.red) + (size_t)blockIdx.x * nb * ib);
           }
         } else {
           ok = false;

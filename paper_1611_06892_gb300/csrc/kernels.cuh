@@ -38,7 +38,9 @@ struct BwdParams {
   int32_t nslots;
   const int32_t* pinfo;     // per panel task: first update slot, number of update slots, first PU slot,
                             // reduced slot (-1: none)
-  void* red;                // per panel task nb x nb: summed derivative of its reflector tails
+  void* red;                // per executor CTA nb x ib: scratch of a panel-block adjoint (the summed
+                            // derivative of its reflector tails, written and read by that sub-task)
+  int red_ctas;             // CTAs the scratch covers (the launch's grid)
   int hw;                   // column chunk of the update adjoints
   int pu_split;             // column pieces of a panel-block update adjoint (1 or 2)
 };
@@ -63,6 +65,7 @@ struct ExecParams {
   const MatInfo* mats;  // batched program: per-matrix parameters (null for one matrix)
   int nmats;
   int f32_simt;         // FP32 tiles only: 1 = updates by FP32 FFMA instead of three TF32 tensor-core products
+  int f32_scalars64;    // FP32 tiles only: 1 = reflector beta / tau / scale in FP64 instead of float pairs
   BwdParams bwd;        // adjoint program only
 };
 

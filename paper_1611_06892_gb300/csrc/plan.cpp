@@ -18,7 +18,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <deque>
 #include <functional>
+#include <map>
 #include <stdexcept>
 
 namespace bd {
@@ -901,6 +903,71 @@ void build_backward(const Plan& pl, BwdPlan& bp, bool split_strips) {
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return bottom[a] > bottom[b]; });
   std::vector<int32_t> pos(nnode);
   for (int32_t z = 0; z < nnode; ++z) pos[order[z]] = z;
+
+  // Partial-slot storage is recycled in queue order.  A panel's slots are read by its factor adjoints
+  // and reductions only; the factor adjoint of its block 0 follows all of them in the reversed DAG
+  // (BPF(b) waits for BPU(b, s), which waits for BPF(s), s > b; BPF(b) waits for its reductions and
+  // PU slots, the reductions for every update strip), so once that sub-task has run the panel's
+  // storage is free.  Walking the queue, each logical slot takes, at its first writer, the storage of
+  // its size released longest ago (or new storage), and every writer of that slot also waits for the
+  // releasing BPF(0), which is earlier in the queue: the order stays topological, each storage region
+  // has one owner at a time, and the sums keep their fixed order (the result is bitwise the same as
+  // with private slots).  Peak storage is what the queue order keeps live (8192^2 Auto, nb = 256:
+  // 6.8 GB instead of 222 GB).
+  {
+    const int32_t nlog = (int32_t)bp.slot_off.size() - 1;
+    std::vector<int64_t> ssize(nlog);
+    for (int32_t l = 0; l < nlog; ++l) ssize[l] = bp.slot_off[l + 1] - bp.slot_off[l];
+    std::vector<int32_t> slot_panel(nlog, -1);
+    const int npu_all = nblk * (nblk - 1) / 2 * pus;
+    for (int t = 0; t < pl.npanels; ++t) {
+      const int32_t* pi = &bp.pinfo[4 * t];
+      for (int32_t l = pi[0]; l < pi[0] + pi[1]; ++l) slot_panel[l] = t;
+      for (int32_t l = pi[2]; l < pi[2] + npu_all; ++l) slot_panel[l] = t;
+      if (pi[3] >= 0) slot_panel[pi[3]] = t;
+    }
+    std::vector<int64_t> phys(nlog, -1);
+    std::vector<int32_t> rel(nlog, -1);                    // node whose completion frees the storage
+    std::map<int64_t, std::deque<std::pair<int64_t, int32_t>>> free_list;   // size -> (offset, releasing node)
+    std::vector<std::vector<int32_t>> held(std::max(1, pl.npanels));
+    int64_t pool = 0;
+    for (int32_t z = 0; z < nnode; ++z) {
+      const int32_t y = order[z];
+      const DevTask& e = sub[y];
+      const int type = e.op & 15;
+      int32_t l = -1;
+      if (type == BUPD || type == BPU) l = e.flags;
+      else if (type == BRED) l = bp.pinfo[4 * e.tslot + 3];
+      if (l >= 0) {
+        if (l >= nlog || slot_panel[l] != e.tslot) throw std::logic_error("partial slot of another panel");
+        if (phys[l] < 0) {
+          auto& fl = free_list[ssize[l]];
+          if (!fl.empty()) {
+            phys[l] = fl.front().first;
+            rel[l] = fl.front().second;
+            fl.pop_front();
+          } else {
+            phys[l] = pool;
+            pool += ssize[l];
+          }
+          held[e.tslot].push_back(l);
+        }
+        if (rel[l] >= 0) rdeps[y].push_back(rel[l]);
+      }
+      if (type == BPF && ((e.op >> 16) & 0xff) == 0 && e.tslot >= 0 && e.tslot < pl.npanels) {
+        for (int32_t h : held[e.tslot]) free_list[ssize[h]].push_back({phys[h], y});
+        held[e.tslot].clear();
+      }
+    }
+    for (int32_t l = 0; l < nlog; ++l) {
+      if (phys[l] < 0) {   // never written (not expected): storage of its own
+        phys[l] = pool;
+        pool += ssize[l];
+      }
+      bp.slot_off[l] = phys[l];
+    }
+    bp.slot_off[nlog] = pool;
+  }
   bp.dev.resize(nnode);
   bp.fwd.resize(nnode);
   bp.deps.clear();
@@ -966,11 +1033,25 @@ void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>*
   }
 }
 
-void autotune(int64_t m, int64_t n, int nsm, int* nb_out, int* ib_out, int* tree_out, int* variant_out) {
-  // Per-tile-size cost in a batch, where the other matrices supply the parallelism: padded Table 1 work
-  // over the measured efficiency of that tile size (512 uneven matrices, m in [64, 1024], on a GB300:
-  // FlatTS batches of nb = 32 / 64 / 128 ran at 0.19 / 0.48 / 0.62 of the FP64 rate the nb = 128 batch
-  // reached), plus the matrix's critical path over the number of SMs it competes with.
+namespace {
+
+// Measured mean sub-task times of the executor, per storage precision and (nb, ib): see
+// autotune_table.inc for the command that writes them.  Classes: PF GE / TS / TT, PU GE / TS / TT,
+// UNMQR / TSMQR / TTMQR update strips.
+struct AutotuneRow {
+  int esize, nb, ib;
+  double us[9];
+};
+const AutotuneRow kAutotuneTable[] = {
+#include "autotune_table.inc"
+    {0, 0, 0, {0, 0, 0, 0, 0, 0, 0, 0, 0}},   // end marker
+};
+
+// Fallback model when the table has no row for this precision: padded Table 1 work over the relative
+// efficiency of the tile size in batches (FP64, GB300: FlatTS batches of nb = 32 / 64 / 128 ran at
+// 0.19 / 0.48 / 0.62 of the FP64 rate the nb = 128 batch reached), plus the critical path over the
+// number of SMs a matrix competes with; FlatTS, ib = 16 for nb = 32, else 32.
+void autotune_model(int64_t m, int64_t n, int nsm, int* nb_out, int* ib_out, int* tree_out, int* variant_out) {
   const int cands[3] = {32, 64, 128};
   const double eff[3] = {0.30, 0.75, 1.0};
   double best = -1.0;
@@ -979,8 +1060,7 @@ void autotune(int64_t m, int64_t n, int nsm, int* nb_out, int* ib_out, int* tree
     if (c > 0 && cands[c - 1] >= n) break;          // a larger tile would only add padding
     const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
     const int variant = choose_variant(p, q, FLATTS, 1, nullptr, nullptr);
-    const int tree = FLATTS;
-    const std::vector<Task> ts = make_tasks(p, q, tree, variant, 1);
+    const std::vector<Task> ts = make_tasks(p, q, FLATTS, variant, 1);
     int64_t work = 0, cp = 0;
     const int kw[7] = {4, 6, 6, 12, 2, 6, 0};
     for (const Task& t : ts) work += kw[t.type];
@@ -991,8 +1071,90 @@ void autotune(int64_t m, int64_t n, int nsm, int* nb_out, int* ib_out, int* tree
       best = cost;
       *nb_out = nb;
       *ib_out = nb == 32 ? 16 : 32;
-      *tree_out = tree;
+      *tree_out = FLATTS;
       *variant_out = variant;
+    }
+  }
+}
+
+}  // namespace
+
+void autotune(int64_t m, int64_t n, int nsm, int esize, int* nb_out, int* ib_out, int* tree_out, int* variant_out) {
+  // Candidates: every calibrated (nb, ib) of this precision x {FlatTS, Greedy, Auto}, the variant by
+  // critical path (Sec. 4.3.3).  A candidate's cost is the time its sub-tasks keep SMs busy (the
+  // calibrated times summed over its device program: a panel task is nb/ib factor sub-tasks and
+  // (nb/ib)(nb/ib - 1)/2 panel updates, an update task nb/w strips) plus its critical path with the same
+  // times over nsm / 8 (in a batch the other matrices supply the parallelism, so the busy time decides
+  // and the critical path only breaks near-ties).  The critical path is evaluated only for candidates
+  // within 10 % of the best busy time.
+  struct Cand {
+    int nb, ib, tree, variant;
+    double busy;
+    const AutotuneRow* row;
+  };
+  std::vector<Cand> cands;
+  int64_t smallest_fit = -1;   // smallest calibrated nb >= n: larger tiles would only add padding
+  for (const AutotuneRow* r = kAutotuneTable; r->esize; ++r)
+    if (r->esize == esize && r->nb >= n && (smallest_fit < 0 || r->nb < smallest_fit)) smallest_fit = r->nb;
+  for (const AutotuneRow* r = kAutotuneTable; r->esize; ++r) {
+    if (r->esize != esize || r->ib < 1 || r->nb % r->ib) continue;
+    if (smallest_fit > 0 && r->nb > smallest_fit) continue;
+    const int nb = r->nb, ib = r->ib, nblk = nb / ib;
+    const int w = std::min(nb, std::max(ib, 32 / ib * ib));     // the executor's default strip width
+    const int64_t R = std::max<int64_t>(1, (int64_t)nsm * w * (esize == 4 ? 2 : 1) / nb);
+    const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
+    const int nstrip = (nb + w - 1) / w;
+    for (int tree : {FLATTS, GREEDY, AUTO}) {
+      const int variant = choose_variant(p, q, tree, R, nullptr, nullptr);
+      double busy = 0.0;
+      for (const Task& t : make_tasks(p, q, tree, variant, R)) {
+        const int kind = t.type == GEQRT ? 0 : (t.type == TSQRT ? 1 : (t.type == TTQRT ? 2 : -1));
+        if (kind >= 0) busy += nblk * r->us[kind] + nblk * (nblk - 1) / 2 * r->us[3 + kind];
+        else if (t.type == UNMQR) busy += nstrip * r->us[6];
+        else if (t.type == TSMQR) busy += nstrip * r->us[7];
+        else if (t.type == TTMQR) busy += nstrip * r->us[8];
+      }
+      cands.push_back({nb, ib, tree, variant, busy, r});
+    }
+  }
+  if (cands.empty()) {
+    autotune_model(m, n, nsm, nb_out, ib_out, tree_out, variant_out);
+    return;
+  }
+  double best_busy = cands[0].busy;
+  for (const Cand& c : cands) best_busy = std::min(best_busy, c.busy);
+  double best = -1.0;
+  for (const Cand& c : cands) {
+    if (c.busy > 1.1 * best_busy) continue;
+    const int nb = c.nb, nblk = nb / c.ib;
+    const int w = std::min(nb, std::max(c.ib, 32 / c.ib * c.ib));
+    const int64_t R = std::max<int64_t>(1, (int64_t)nsm * w * (esize == 4 ? 2 : 1) / nb);
+    const int p = (int)((m + nb - 1) / nb), q = (int)((n + nb - 1) / nb);
+    const std::vector<Task> ts = make_tasks(p, q, c.tree, c.variant, R);
+    std::vector<std::vector<int32_t>> preds;
+    make_dag(ts, p, q, c.variant, &preds, nullptr, nullptr);
+    std::vector<double> fin(ts.size(), 0.0);
+    double cp = 0.0;
+    for (size_t x = 0; x < ts.size(); ++x) {
+      const Task& t = ts[x];
+      const int kind = t.type == GEQRT ? 0 : (t.type == TSQRT ? 1 : (t.type == TTQRT ? 2 : -1));
+      double wt = 0.0;
+      if (kind >= 0) wt = nblk * c.row->us[kind] + (nblk - 1) * c.row->us[3 + kind];   // the factor chain
+      else if (t.type == UNMQR) wt = c.row->us[6];
+      else if (t.type == TSMQR) wt = c.row->us[7];
+      else if (t.type == TTMQR) wt = c.row->us[8];
+      double st = 0.0;
+      for (int32_t d : preds[x]) st = std::max(st, fin[d]);
+      fin[x] = st + wt;
+      cp = std::max(cp, fin[x]);
+    }
+    const double cost = c.busy + cp * 8.0 / std::max(1, nsm);
+    if (best < 0 || cost < best) {
+      best = cost;
+      *nb_out = c.nb;
+      *ib_out = c.ib;
+      *tree_out = c.tree;
+      *variant_out = c.variant;
     }
   }
 }

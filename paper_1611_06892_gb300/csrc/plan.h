@@ -124,10 +124,10 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
 void merge_programs(const std::vector<const Plan*>& plans, std::vector<DevTask>* dev, std::vector<int32_t>* deps);
 
 // Tile size, inner blocking, tree and variant for one m x n matrix of a batch (the batched form's
-// autotuner).  nb in {32, 64, 128}; ib = 16 for nb = 32, else 32; FlatTS tree (in a batch the other
-// matrices provide the parallelism and the TS kernels are the most efficient); variant by critical
-// path.  nb minimises padded Table 1 work / eff(nb) + critical path / (SMs / 8), eff(nb) being the
-// measured relative efficiency of batches of that tile size.
-void autotune(int64_t m, int64_t n, int nsm, int* nb, int* ib, int* tree, int* variant);
+// autotuner), for FP64 (esize 8) or FP32 (esize 4) storage: a search over the calibrated (nb, ib) pairs
+// (nb in {32, 64, 128}, ib in {8, 16, 32}) and the FlatTS, Greedy and Auto trees, minimising the
+// calibrated busy time of the matrix's sub-tasks (plus its critical path over nsm / 8); the variant by
+// critical path.  Falls back to a Table 1 work model when the table has no row for the precision.
+void autotune(int64_t m, int64_t n, int nsm, int esize, int* nb, int* ib, int* tree, int* variant);
 
 }  // namespace bd

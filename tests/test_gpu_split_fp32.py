@@ -104,15 +104,50 @@ def test_split_fp32_nb256(handle, torch_mod):
     check(torch_mod, handle, A32, 256, 32, "greedy", "rbidiag")
 
 
-def test_split_fp32_tall_full_size(torch_mod):
-    """65536 x 1024 R-BiDiag (the tall workload): residual, orthogonality and singular values at 5e-6."""
+def test_split_fp32_scalar_modes(torch_mod):
+    """The reflector scalars (beta, tau, tail scale) of the FP32 path in float-pair arithmetic (default)
+    and in FP64 (BIDIAG_OPT_F32_SCALARS = 1): both meet the FP64-oracle checks, and their bands agree
+    to a few FP32 roundings (the two compute the same FP32 values up to rounding ties)."""
     torch = torch_mod
-    m, n, nb, ib = 65536, 1024, 256, 32
-    A = inputs.torch_gaussian(m, n, 4)
+    A32 = inputs.gaussian(600, 400, seed=9).astype(np.float32)
+    bands = []
+    for mode in (0, 1):
+        h = G.Handle()
+        h.set_option(G.OPT_AUTO_RESOURCES, 3)
+        h.set_option(G.OPT_F32_SCALARS, mode)
+        try:
+            check(torch, h, A32, 256, 32, "auto", "bidiag")
+            res = h.band(torch.from_numpy(np.asfortranarray(A32)).cuda(), 256, 32, "auto", "bidiag")
+            h.sync()
+            bands.append(res.band().cpu().numpy().astype(np.float64))
+            res.free()
+        finally:
+            h.close()
+    nA = np.linalg.norm(A32.astype(np.float64))
+    assert np.abs(bands[0] - bands[1]).max() <= 64 * 2.0 ** -24 * nA
+
+
+@pytest.mark.parametrize("m,n,tree,variant,seed", [(65536, 1024, "greedy", "rbidiag", 4),
+                                                   (65536, 2048, "auto", "rbidiag", 5),
+                                                   (8192, 8192, "auto", "bidiag", 2)],
+                         ids=("tall1024", "tall2048", "square8192"))
+def test_split_fp32_full_size(torch_mod, m, n, tree, variant, seed):
+    """The split form at the bench's sizes, each result's accuracy against FP64 stated and checked at
+    5e-6: singular values of B against those of the (FP32-rounded) A relative to sigma_1, the residual
+    ||A P X - Q B X|| / (||A|| ||X||) and the orthogonality round trip ||Q^T Q Y - Y|| / ||Y|| through
+    the FP32 apply entry points (two applications, each within 5e-6).  Inputs: N(0,1) for the tall shapes, U diag(s) V^T with s geometric
+    from 1 to 1e-8 for the square one."""
+    torch = torch_mod
+    nb, ib = 256, 32
+    if m == n:
+        A = inputs.torch_prescribed_singular_values(m, n, inputs.geometric_sv(n), seed, seed + 1)
+    else:
+        A = inputs.torch_gaussian(m, n, seed)
     A32 = A.float().t().contiguous().t()
+    del A
     h = G.Handle()
     try:
-        res = h.band(A32, nb, ib, "greedy", "rbidiag")
+        res = h.band(A32, nb, ib, tree, variant)
         h.sync()
         ab = res.band().double()
         B = torch.zeros((n, n), dtype=torch.float64, device="cuda")
@@ -124,7 +159,7 @@ def test_split_fp32_tall_full_size(torch_mod):
         A64 = A32.double()
         sa = torch.linalg.svdvals(A64)
         sb = torch.linalg.svdvals(B)
-        assert (sa - sb).abs().max().item() <= TOL * sa[0].item()
+        err_sv = (sa - sb).abs().max().item() / sa[0].item()
         gen = torch.Generator(device="cuda")
         gen.manual_seed(5)
         X = torch.randn((n, 4), dtype=torch.float32, device="cuda", generator=gen)
@@ -134,10 +169,18 @@ def test_split_fp32_tall_full_size(torch_mod):
         h.sync()
         Y = torch.zeros((4, m), dtype=torch.float32, device="cuda").t()
         Y[:n] = (B @ X.double()).float()
+        Y0 = Y.clone()
         res.apply_q(Y, 0)
         h.sync()
-        err = torch.linalg.norm(A64 @ Z.t().double() - Y.double()).item()
-        assert err <= TOL * torch.linalg.norm(A64).item() * torch.linalg.norm(X.double()).item()
+        err_res = torch.linalg.norm(A64 @ Z.t().double() - Y.double()).item() / (
+            torch.linalg.norm(A64).item() * torch.linalg.norm(X.double()).item())
+        res.apply_q(Y, 1)
+        h.sync()
+        err_orth = torch.linalg.norm((Y - Y0).double()).item() / torch.linalg.norm(Y0.double()).item()
+        print(f"\nsplit-FP32 accuracy {m}x{n} {tree} {variant}: sigma {err_sv:.2e}, residual {err_res:.2e}, "
+              f"orthogonality {err_orth:.2e}")
+        # the round trip is two FP32 applications, each held to the target
+        assert err_sv <= TOL and err_res <= TOL and err_orth <= 2 * TOL
         res.free()
     finally:
         h.close()

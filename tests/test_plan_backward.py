@@ -9,6 +9,9 @@
 * Panels with at least eight update strips get a reduced slot: reduction sub-tasks, which follow every
   update strip of the panel, sum the strips' partials block by block over row chunks that tile the
   block's rows, and the factor sub-task of a block follows its reductions.
+* Slot storage is recycled: logical slots that share storage have the same size and range, distinct
+  storage ranges never overlap, and for consecutive owners of one range every reader and writer of the
+  earlier owner precedes every writer of the later one in the DAG.
 """
 import numpy as np
 import pytest
@@ -147,11 +150,15 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
                 assert f["flags"] == t[2] + (b * nblk - b * (b + 1) // 2 + (s - b - 1)) * pus + f["half"]
     # reductions: (panel, block) -> chunk -> sub-task; each follows every update strip of its panel
     red = {}
+    readers, writers = {}, {sl: [y] for sl, y in writer.items()}
     for y in range(nsub):
         f = fields(prog[y])
         if f["typ"] != BRED:
             continue
         t = pinfo[f["tslot"]]
+        writers.setdefault(int(t[3]), []).append(y)
+        for sl in range(t[0], t[0] + t[1]):
+            readers.setdefault(sl, []).append(y)
         assert t[3] >= 0 and t[1] >= RED_MIN
         chunks = red.setdefault((f["tslot"], f["blk"]), {})
         assert f["strip"] not in chunks
@@ -173,20 +180,45 @@ def check_backward(m, n, nb, ib, tree, variant, strip_w, state=True):
             assert sorted(chunks) == list(range(-(-vrows // rows)))
             for z in chunks.values():
                 assert (anc[y] >> z) & 1, f"factor sub-task {y} before its reduction {z}"
-            reads = []
+            reads = [int(t[3])]
             nred += b == 0
         else:
             reads = list(range(t[0], t[0] + t[1]))
         reads += [t[2] + (b * nblk - b * (b + 1) // 2 + (s - b - 1)) * pus + hh for s in range(b + 1, nblk)
                   for hh in range(pus)]
         for sl in reads:
+            readers.setdefault(sl, []).append(y)
+            if sl == t[3]:          # its block's reductions precede it (checked above)
+                continue
             assert sl in writer and (anc[y] >> writer[sl]) & 1, f"slot {sl} not written before its reader {y}"
     assert not red, "a reduction without its factor sub-task"
-    # slot offsets: increasing, sizes nb^2 + nb ib (update strips, reduced slots) and nb ib + ib^2
-    # (panel-block updates)
-    sizes = np.diff(slot_off)
-    assert set(sizes.tolist()) <= {nb * nb + nb * ib, nb * ib + ib * ib}
     assert len(writer) + nred == len(slot_off) - 1
+    # slot storage: sizes nb^2 + nb ib (update strips, reduced slots) and nb ib + ib^2 (panel-block
+    # updates); logical slots sharing storage are its consecutive owners (in the order of their first
+    # writers), each owner's readers and writers precede the next owner's writers
+    nlog = len(slot_off) - 1
+    size = np.zeros(nlog, dtype=np.int64)
+    npu = nblk * (nblk - 1) // 2 * pus
+    for t in pinfo:
+        size[t[0]:t[0] + t[1]] = nb * nb + nb * ib
+        size[t[2]:t[2] + npu] = nb * ib + ib * ib
+        if t[3] >= 0:
+            size[t[3]] = nb * nb + nb * ib
+    assert (size > 0).all()
+    groups = {}
+    for sl in range(nlog):
+        groups.setdefault(int(slot_off[sl]), []).append(sl)
+    ends = sorted((off, off + int(size[g[0]])) for off, g in groups.items())
+    for (o0, e0), (o1, _) in zip(ends, ends[1:]):
+        assert e0 <= o1, "storage ranges overlap"
+    assert ends[-1][1] <= slot_off[-1]
+    for off, g in groups.items():
+        assert len({int(size[sl]) for sl in g}) == 1
+        g = sorted(g, key=lambda sl: min(writers[sl]))
+        for a, b in zip(g, g[1:]):
+            for wy in writers[b]:
+                for z in writers[a] + readers.get(a, []):
+                    assert (anc[wy] >> z) & 1, f"storage at {off}: owner {a} (sub-task {z}) not before {b} ({wy})"
     return nsub
 
 
@@ -240,3 +272,20 @@ def test_adjoint_program_reductions(tree, variant):
     assert check_backward(300, 64, 32, 8, tree, variant, strip_w=16) > 0
     # nb = 256, ib = 32: 64-row chunks, four per block (slot and order checks only)
     assert check_backward(1600, 512, 256, 32, tree, variant, strip_w=32, state=False) > 0
+
+
+def test_checker_catches_shared_live_storage(monkeypatch):
+    """Give two update strips of the same panel (independent sub-tasks, both live until the panel's
+    factor adjoints) the same storage: the storage check must report it."""
+    real = G.bidiag_plan_backward
+
+    def broken(*args, **kw):
+        prog, fwd, deps, slot_off, pinfo, wb = real(*args, **kw)
+        slot_off = slot_off.copy()
+        t = next(t for t in pinfo if t[1] >= 2)
+        slot_off[t[0] + 1] = slot_off[t[0]]
+        return prog, fwd, deps, slot_off, pinfo, wb
+
+    monkeypatch.setattr(G, "bidiag_plan_backward", broken)
+    with pytest.raises(AssertionError):
+        check_backward(100, 40, 8, 4, 0, 1, strip_w=4)

@@ -115,12 +115,21 @@ def test_choose_variant_follows_critical_paths():
 
 
 def test_autotune_choices():
-    """The batched form's autotuner returns a supported configuration for every shape."""
-    for (m, n) in ((32, 1), (64, 32), (100, 100), (1024, 1024), (1024, 200), (4096, 1024), (70000, 64)):
-        nb, ib, tree, variant = G.bidiag_autotune(m, n, 152)
-        assert (nb, ib) in ((32, 16), (64, 32), (128, 32))
-        assert tree == T.FLATTS and variant in (T.BIDIAG, T.RBIDIAG)
-        assert nb < 2 * max(32, n)          # never more than one size above the matrix's width
+    """The batched form's autotuner searches the calibrated (nb, ib) pairs and the FlatTS / Greedy / Auto
+    trees: its choice is one of those candidates, the variant is the one with the shorter critical path
+    for that tree (Sec. 4.3.3), no tile is larger than needed to cover the matrix's width, and each
+    storage precision has its own calibration."""
+    cands = {(nb, ib) for nb in (32, 64, 128) for ib in (8, 16, 32) if ib <= nb}
+    for es in (8, 4):
+        for (m, n) in ((32, 1), (64, 32), (100, 100), (1024, 1024), (1024, 200), (4096, 1024), (70000, 64)):
+            nb, ib, tree, variant = G.bidiag_autotune(m, n, 152, es)
+            assert (nb, ib) in cands and tree in (T.FLATTS, T.GREEDY, T.AUTO)
+            assert nb < 2 * max(32, n)          # never more than one size above the matrix's width
+            w = min(nb, max(ib, 32 // ib * ib))
+            R = max(1, 152 * w * (2 if es == 4 else 1) // nb)
+            assert variant == G.bidiag_plan_choose_variant(-(-m // nb), -(-n // nb), tree, R)[0]
+    with pytest.raises(G.BidiagError):
+        G.bidiag_autotune(100, 100, 152, 2)
 
 
 def test_three_step_planner_matches_oracle():
