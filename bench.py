@@ -221,9 +221,12 @@ def trace_report(h, nb, ib, esize, nsm, title, w=32):
         s[2] += b
         s[3] += f or 0.0
     busy = dur.sum()
+    tc5 = int(((op >> 32) & 1).sum())
+    nupd = int(sum(1 for o in op if (int(o) & 15) in (1, 3, 5, 8)))
     lines = [f"### {title}", "",
              f"launch span {1e-6 * (t1 - t0):.2f} ms, {n} sub-tasks, SMs busy {busy / (nsm * (t1 - t0)):.1%} "
-             f"of the span ({nsm} SMs)", "",
+             f"of the span ({nsm} SMs)" + (f"; {tc5} of {nupd} update sub-tasks ran C -= V W on tcgen05"
+                                           if tc5 else ""), "",
              "| sub-task | count | total ms | share of busy | mean us | alg. bytes | GB/s | GFLOP/s |",
              "|---|---|---|---|---|---|---|---|"]
     for k in sorted(stats, key=lambda c: -stats[c][1]):
@@ -837,6 +840,8 @@ def main():
                          "and write them to this C include file (instead of the benchmark)")
     ap.add_argument("--batch-config", default=None,
                     help="batched512 only: nb,ib,tree for every matrix instead of the autotuner's choices")
+    ap.add_argument("--f32-updates", type=int, default=None,
+                    help="FP32 storage: 0 = tcgen05 + warp-level tensor cores (default), 1 = FFMA, 2 = warp-level only")
     ap.add_argument("--strip-width", type=int, default=None,
                     help="column-strip width of the update sub-tasks (16, 32 or 64; default: the library's 32)")
     ap.add_argument("--trace-summary", default=None,
@@ -956,6 +961,9 @@ def main():
     if args.strip_width:
         h.set_option(G.OPT_STRIP, args.strip_width)
         config["strip_width"] = args.strip_width
+    if args.f32_updates is not None:
+        h.set_option(G.OPT_F32_UPDATES, args.f32_updates)
+        config["f32_updates"] = args.f32_updates
     stream = h.stream
     peaks = measure_peaks(G, torch, local, f32)
 

@@ -60,15 +60,19 @@ enum {
 /* Options for bidiag_set_option. */
 enum {
   BIDIAG_OPT_WAIT_LIMIT_NS = 1,   /* bound of every device-side dependency wait, ns (default 2e10) */
-  BIDIAG_OPT_AUTO_RESOURCES = 2,  /* "nbcores" R of the Auto tree (default: SMs * w / nb, the number of
-                                     tile updates that run at once when each spreads over nb / w SMs) */
+  BIDIAG_OPT_AUTO_RESOURCES = 2,  /* "nbcores" R of the Auto tree (default: SMs * w / nb with w = 32, the
+                                     number of tile updates that run at once when each spreads over
+                                     nb / w SMs; FP32 storage SMs * 64 / nb) */
   BIDIAG_OPT_DEBUG_UNSET_DEP = 3, /* 1: the next bidiag_band adds to its first task a dependency on a
                                      flag nothing sets, so that its wait runs out (failure-path test) */
-  BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16, 32 or 64, default 32) */
+  BIDIAG_OPT_STRIP = 4,           /* column-strip width of the update tasks (16, 32 or 64; default 32, and
+                                     64 for a one-matrix reduction with FP32 storage) */
   BIDIAG_OPT_TIMING = 5,          /* 1: time the executor launch of each bidiag_band with CUDA events */
   BIDIAG_OPT_TRACE = 6,           /* 1: record a per-task trace of each bidiag_band (see bidiag_trace) */
-  BIDIAG_OPT_F32_UPDATES = 7,     /* FP32 storage: 0 = updates as three TF32 tensor-core products (default),
-                                     1 = updates by FP32 FMA on the CUDA cores (FP32-exact products) */
+  BIDIAG_OPT_F32_UPDATES = 7,     /* FP32 storage: 0 = updates as three TF32 tensor-core products, the
+                                     C -= V W product on tcgen05 (one matrix; default), 1 = updates by FP32
+                                     FMA on the CUDA cores (FP32-exact products), 2 = three TF32 products on
+                                     the warp-level MMA only */
   BIDIAG_OPT_F32_SCALARS = 8      /* FP32 storage: each reflector's beta, tau and tail scale from alpha and
                                      the tail's squared norm (always a compensated sum, FP64-level accuracy)
                                      0 = in float-pair arithmetic, about 44 bits (default), 1 = in FP64.
@@ -287,7 +291,9 @@ int bidiag_last_exec_ms(bidiag_handle h, float* ms);
 
 /* Per-task trace of the last bidiag_band enqueued with BIDIAG_OPT_TRACE on (call after bidiag_sync):
  * *count records of 4 int64 in queue order: start and end (%globaltimer ns), SM id, and the task's op
- * word (type | orientation << 4 | strip << 8).  Copied to host `out` when cap >= *count. */
+ * word (type | orientation << 4 | strip << 8, as bidiag_plan_program) in the low 32 bits, bit 32 set
+ * when an FP32-storage update ran its C -= V W product on tcgen05.  Copied to host `out` when
+ * cap >= *count. */
 int bidiag_trace(bidiag_handle h, int64_t* out, int64_t cap, int64_t* count);
 
 /* Device program of the last traced launch (host memory, for analysing its trace): *count sub-tasks

@@ -100,7 +100,7 @@ struct bidiag_ctx {
   uint64_t wait_ns = 20000000000ull;
   int64_t auto_res = -1;
   int debug_unset = 0;
-  int strip_w = 32;
+  int strip_w = 0;                 // update strip width; 0: 64 for one FP32-storage matrix, else 32
   int timing = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool timed = false;
@@ -173,12 +173,12 @@ int upload_program(bidiag_handle h, PlanDev& pd, const std::vector<bd::DevTask>&
 // Resources R of the Auto tree (Sec. 5 "nbcores"): the number of workers that each take one tile
 // task.  A tile update is spread over nb / w SMs (one column strip each), so the default is
 // SMs * w / nb for FP64 storage.  With FP32 storage the updates are about ten times faster while the
-// panels are not, so more, smaller groups (twice the R) pay: 8192^2 takes 190 ms with 2 SMs w / nb
-// against 232 ms with SMs w / nb (FP64: 1398 vs 1386 ms, and 4096^2 prefers the smaller R).
-// BIDIAG_OPT_AUTO_RESOURCES overrides it.
+// panels are not, so more, smaller groups pay: SMs * 64 / nb (twice the FP64 value at w = 32; with the
+// 64-column FP32 strips the same R): 8192^2 took 190 ms with it against 232 ms with SMs * 32 / nb
+// (FP64: 1398 vs 1386 ms, and 4096^2 prefers the smaller R).  BIDIAG_OPT_AUTO_RESOURCES overrides it.
 int64_t resources_of(bidiag_handle h, int nb, int w, int esize) {
   if (h->auto_res > 0) return h->auto_res;
-  return std::max<int64_t>(1, (int64_t)h->nsm * w * (esize == 4 ? 2 : 1) / nb);
+  return std::max<int64_t>(1, (int64_t)h->nsm * (esize == 4 ? 64 : w) / nb);
 }
 
 // Executor launch of a program held in pd with the given buffers.
@@ -216,6 +216,16 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   prm.esize = esize;
   prm.f32_simt = h->f32_simt;
   prm.f32_scalars64 = h->f32_scalars64;
+  prm.umma_cols = 0;
+  if (esize == 4 && !bwd && !d_mats && h->f32_simt == 0 && per_sm == 1 && nb % 16 == 0 && (ib == 16 || ib == 32) &&
+      w <= 64) {
+    // TMEM for the tcgen05 phase: one accumulator of N = max(w, ib) (rounded to 16) columns per 128-row
+    // chunk of the tile and per k-step of 8, allocated as a power of two of at least 32 columns
+    const int need = ((nb + 127) / 128) * (ib / 8) * ((std::max(w, ib) + 15) / 16 * 16);
+    int cols = 32;
+    while (cols < need) cols *= 2;
+    if (cols <= 512) prm.umma_cols = cols;
+  }
   prm.mats = d_mats;
   prm.nmats = nmats;
   prm.trace = nullptr;
@@ -244,8 +254,11 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   return BIDIAG_OK;
 }
 
+// Strip width of a one-matrix reduction: with FP32 storage 64 columns by default (each inner block of
+// V staged in shared memory then serves twice the columns; 8192^2: 162 -> 150 ms), else 32.
 int choose_strip(bidiag_handle h, int nb, int ib, int esize, int* w) {
-  *w = bd::choose_strip_width(nb, ib, h->strip_w, h->smem_optin, esize);
+  const int pref = h->strip_w > 0 ? h->strip_w : (esize == 4 ? 64 : 32);
+  *w = bd::choose_strip_width(nb, ib, pref, h->smem_optin, esize);
   if (*w) return BIDIAG_OK;
   return fail(h, BIDIAG_ERR_UNSUPPORTED, "tile size / inner blocking need more shared memory than the device has");
 }
@@ -726,7 +739,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
             bad[(size_t)b] = -9;
             continue;
           }
-          o.w = bd::choose_strip_width(o.nb, o.ib, h->strip_w, h->smem_optin, esize);
+          o.w = bd::choose_strip_width(o.nb, o.ib, h->strip_w > 0 ? h->strip_w : 32, h->smem_optin, esize);
           if (!o.w) {
             bad[(size_t)b] = BIDIAG_ERR_UNSUPPORTED;
             continue;
@@ -934,7 +947,7 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
       h->tracing = value != 0;
       return BIDIAG_OK;
     case BIDIAG_OPT_F32_UPDATES:
-      if (value != 0 && value != 1) return -3;
+      if (value < 0 || value > 2) return -3;
       h->f32_simt = (int)value;
       return BIDIAG_OK;
     case BIDIAG_OPT_F32_SCALARS:

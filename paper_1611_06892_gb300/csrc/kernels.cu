@@ -78,11 +78,12 @@ __host__ __device__ inline int rm_ld(int n, int esize) {
 // element type at offsets (in elements) that keep 16-byte alignment.
 struct Layout {
   int lp, lv, lc;            // col-major panel ld; row-major V ld; row-major C / W ld
-  int P, V, Vh, Cs, Ct, Rt, Tb, G, W, W2, total;
+  int P, V, Vh, B, Cs, Ct, Rt, Tb, G, W, W2, total;
 };
 // tau[<= 64], red[32]; the adjoint panel also uses three more arrays of 64 doubles
 constexpr int kHeaderDoubles = 64 + 32 + 3 * 64;
 __host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
+__host__ __device__ inline int align32(int x) { return (x + 31) & ~31; }
 __host__ __device__ inline Layout layout_panel(int nb, int ib, int esize) {
   Layout L{};
   L.lp = odd_ld(nb);
@@ -92,7 +93,7 @@ __host__ __device__ inline Layout layout_panel(int nb, int ib, int esize) {
   L.Rt = o;  o = align4(o + ib * ib);
   L.Tb = o;  o = align4(o + ib * ib);
   L.G = o;   o = align4(o + 2 * ib * ib);   // Gram matrix and a scratch block for T
-  L.V = L.Vh = L.Cs = L.Ct = L.W = L.W2 = -1;
+  L.V = L.Vh = L.B = L.Cs = L.Ct = L.W = L.W2 = -1;
   L.total = o;
   return L;
 }
@@ -103,14 +104,16 @@ __host__ __device__ inline Layout layout_update(int nb, int ib, int w, int esize
   L.lc = rm_ld(w, esize);
   int o = 0;
   L.Cs = o;  o = align4(o + nb * L.lc);
-  L.Ct = o;  o = align4(o + ib * L.lc);
-  L.V = o;   o = align4(o + nb * L.lv);
+  L.Ct = o;  o = align32(o + ib * L.lc);
+  L.V = o;   o = align32(o + nb * L.lv);     // MMA operand regions start on 128-byte boundaries
   L.Tb = o;  o = align4(o + ib * ib);
   L.W = o;   o = align4(o + ib * L.lc);
-  L.W2 = o;  o = align4(o + ib * L.lc);
-  L.Vh = -1;
-  if (esize == 4) {          // FP32 storage: TF32 high parts of V (V itself then holds the low parts)
-    L.Vh = o;  o = align4(o + nb * L.lv);
+  L.W2 = o;  o = align32(o + ib * L.lc);
+  L.Vh = L.B = -1;
+  if (esize == 4) {          // FP32 storage: TF32 high parts of V (V itself then holds the low parts),
+                             // and the split -W2 operand of the tcgen05 phase (2 x ib x up to 64 rows)
+    L.Vh = o;  o = align32(o + nb * L.lv);
+    L.B = o;   o = align32(o + 2 * ib * ((w > ib ? w : ib) + 15) / 16 * 16);
   }
   L.P = L.Rt = L.G = -1;
   L.total = o;
@@ -926,6 +929,229 @@ __device__ void apply_rm(const E* V, const E* Vh, int lv, int vrows, int kb, con
 }
 
 // ---------------------------------------------------------------------------------------------
+// Phase 3 of an FP32-storage block application on the 5th-generation tensor cores (tcgen05, kind::tf32):
+// P = V (-W2) with V (vrows x kb) and -W2 (kb x ncols) split into TF32 high / low parts in shared memory
+// in the K-major core-matrix layout (8 rows x 16 bytes per core matrix; element (row, k) at
+// (row / 8) SBO + (k / 4) 128 B + (row % 8) 16 B + (k % 4) 4 B, SBO = kb / 4 x 128 B), the products
+// accumulated in TMEM.  As in the warp-level form, each k-step of 8 gets its own accumulator holding its
+// three products (lo hi, hi lo, hi hi), and the epilogue adds the k-steps to C with rounded FP32 adds in
+// increasing k.  One thread issues the MMAs (M = 128 rows per chunk, N = ncols rounded up to 16) and
+// commits them to an mbarrier; every thread waits (bounded), then each warp reads its 32 TMEM lanes.
+// ---------------------------------------------------------------------------------------------
+struct Umma {
+  uint32_t tmem;      // TMEM base address of this CTA's allocation
+  uint32_t mbar;      // shared-memory address of the completion mbarrier
+  uint32_t phase;     // parity of the next completion
+  uint32_t ncols_alloc;
+  int failed;         // a completion wait ran out (the MMAs may still be in flight)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading-dimension byte offset >> 4
+// (16-29: the step between core matrices along K), stride-dimension byte offset >> 4 (32-45: the step
+// between 8-row groups), descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (7-9 and 10-12 = 2), both
+// K-major, N >> 3 (17-22), M >> 4 (24-28).
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+// Bounded wait for the mbarrier phase with the given parity; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = gtime();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (gtime() - t0 > limit_ns) return false;
+  }
+}
+// 32 consecutive TMEM columns of this warp's 32 lanes into v (one column per register).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Core-matrix index (in floats) of element (row, k) of a K-major operand with kb columns of K.
+__device__ __forceinline__ int core_idx(int row, int k, int kb) {
+  return (row >> 3) * (kb << 3) + ((k >> 2) << 5) + ((row & 7) << 2) + (k & 3);
+}
+
+// V block (oriented X(r0 + r, c0 + a), r < vrows, a < kb <= 32, masked as load_tile) into the core-matrix
+// layout, split: TF32 high parts in Vh, low parts in Vl.  All of a thread's loads are issued first.
+__device__ void load_v_core(float* Vl, float* Vh, const float* g, int nb, int tr, int r0, int c0, int vrows, int kb,
+                            int mask) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float v[32];
+  if (!tr) {   // a = warp + 8 ka, r = lane + 32 kr
+#pragma unroll
+    for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+      for (int kr = 0; kr < 8; ++kr) {
+        const int a = warp + 8 * ka, r = lane + 32 * kr;
+        v[ka * 8 + kr] = (a < kb && r < vrows) ? masked_ld(g, r0 + r, c0 + a, nb, tr, mask) : 0.0f;
+      }
+#pragma unroll
+    for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+      for (int kr = 0; kr < 8; ++kr) {
+        const int a = warp + 8 * ka, r = lane + 32 * kr;
+        if (a < kb && r < vrows) put(Vl, Vh, core_idx(r, a, kb), v[ka * 8 + kr]);
+      }
+  } else {     // r = warp + 8 kr, a = lane
+#pragma unroll
+    for (int kr = 0; kr < 32; ++kr) {
+      const int r = warp + 8 * kr;
+      v[kr] = (lane < kb && r < vrows) ? masked_ld(g, r0 + r, c0 + lane, nb, tr, mask) : 0.0f;
+    }
+#pragma unroll
+    for (int kr = 0; kr < 32; ++kr) {
+      const int r = warp + 8 * kr;
+      if (lane < kb && r < vrows) put(Vl, Vh, core_idx(r, lane, kb), v[kr]);
+    }
+  }
+}
+
+// Phase 1 (warp-level tensor cores) reading V from the core-matrix layout: W = Ct + V^T C, with the C
+// strip column-major (leading dimension ldc) and Ct, W row-major (lc).
+__device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows, int kb, const float* Ct,
+                                     const float* C, int ldc, int lc, int ncols, float* W) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int mt_n = kb >> 4, nt_n = ncols >> 3;
+  for (int tile = warp; tile < mt_n * nt_n; tile += kWarps) {
+    const int m0 = (tile % mt_n) << 4, n0 = (tile / mt_n) << 3;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (Ct) {
+      acc[0] = Ct[(m0 + g) * lc + n0 + 2 * t];
+      acc[1] = Ct[(m0 + g) * lc + n0 + 2 * t + 1];
+      acc[2] = Ct[(m0 + g + 8) * lc + n0 + 2 * t];
+      acc[3] = Ct[(m0 + g + 8) * lc + n0 + 2 * t + 1];
+    }
+#pragma unroll 4
+    for (int k0 = 0; k0 < vrows; k0 += 8) {
+      const int i00 = core_idx(k0 + t, m0 + g, kb), i01 = core_idx(k0 + t, m0 + g + 8, kb);
+      const int i10 = core_idx(k0 + t + 4, m0 + g, kb), i11 = core_idx(k0 + t + 4, m0 + g + 8, kb);
+      const uint32_t ah[4] = {__float_as_uint(Vh[i00]), __float_as_uint(Vh[i01]), __float_as_uint(Vh[i10]),
+                              __float_as_uint(Vh[i11])};
+      const uint32_t al[4] = {__float_as_uint(Vl[i00]), __float_as_uint(Vl[i01]), __float_as_uint(Vl[i10]),
+                              __float_as_uint(Vl[i11])};
+      const float b[2] = {C[(k0 + t) + (n0 + g) * ldc], C[(k0 + t + 4) + (n0 + g) * ldc]};
+      mma_3xtf32(acc, ah, al, b);
+    }
+    W[(m0 + g) * lc + n0 + 2 * t] = acc[0];
+    W[(m0 + g) * lc + n0 + 2 * t + 1] = acc[1];
+    W[(m0 + g + 8) * lc + n0 + 2 * t] = acc[2];
+    W[(m0 + g + 8) * lc + n0 + 2 * t + 1] = acc[3];
+  }
+}
+
+// The whole block application W = op(T) (Ct + V^T C), Ct -= W, C -= V W with V in the core-matrix layout
+// (load_v_core) and the C strip column-major (ldc; one row per lane in the epilogue is then free of bank
+// conflicts): phase 1 on the warp-level tensor cores, phase 2 on the FMA units, phase 3 with tcgen05.
+// Bh / Bl: kb x 64 floats each for the split -W2 operand.  Returns false if the MMA completion wait ran
+// out (the error word is then set and C is left as it was).
+__device__ bool apply_rm_umma(const float* Vh, const float* Vl, int vrows, int kb, const float* Tb, bool notrans,
+                              float* Ct, float* C, int ldc, int lc, int ncols, float* W, float* W2, float* Bh,
+                              float* Bl, Umma& um, const ExecParams& prm) {
+  apply_phase1_tc_core(Vh, Vl, vrows, kb, Ct, C, ldc, lc, ncols, W);
+  __syncthreads();
+  // phase 2: W2 = op(T) W, Ct -= W2 (as apply_rm), and -W2 into the B operand (ncols rows of K = kb)
+  const int npad = (ncols + 15) & ~15;
+  for (int u = threadIdx.x; u < ncols * kb; u += kThreads) {
+    const int c = u % ncols, a = u / ncols;
+    float s = 0.f;
+    if (!notrans) {
+      for (int t = 0; t <= a; ++t) s = fmaf(Tb[t + a * kb], W[t * lc + c], s);
+    } else {
+      for (int t = a; t < kb; ++t) s = fmaf(Tb[a + t * kb], W[t * lc + c], s);
+    }
+    W2[a * lc + c] = s;
+    if (Ct) Ct[a * lc + c] -= s;
+    put(Bl, Bh, core_idx(c, a, kb), -s);
+  }
+  for (int u = threadIdx.x; u < (npad - ncols) * kb; u += kThreads) {   // zero rows of the padded N
+    const int c = ncols + u / kb, a = u % kb;
+    Bl[core_idx(c, a, kb)] = 0.f;
+    Bh[core_idx(c, a, kb)] = 0.f;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy smem writes -> MMA reads
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int nks = kb >> 3, mch = (vrows + 127) >> 7;
+  if (threadIdx.x == 0) {
+    const uint32_t sbo = (uint32_t)(kb >> 2) * 128u, idesc = umma_idesc_tf32(128, npad);
+    const uint32_t vh = smem_u32(Vh), vl = smem_u32(Vl), bh = smem_u32(Bh), bl = smem_u32(Bl);
+    for (int mc = 0; mc < mch; ++mc)
+      for (int ks = 0; ks < nks; ++ks) {
+        const uint32_t d = um.tmem + (uint32_t)((mc * nks + ks) * npad);
+        const uint32_t ao = (uint32_t)mc * 16u * sbo + (uint32_t)ks * 256u, bo = (uint32_t)ks * 256u;
+        umma_tf32(d, umma_desc(vl + ao, 128, sbo), umma_desc(bh + bo, 128, sbo), idesc, 0);
+        umma_tf32(d, umma_desc(vh + ao, 128, sbo), umma_desc(bl + bo, 128, sbo), idesc, 1);
+        umma_tf32(d, umma_desc(vh + ao, 128, sbo), umma_desc(bh + bo, 128, sbo), idesc, 1);
+      }
+    umma_commit(um.mbar);
+  }
+  const bool ok = __syncthreads_and(mbar_wait(um.mbar, um.phase, prm.wait_ns) ? 1 : 0) != 0;
+  um.phase ^= 1u;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicCAS(prm.err, 0, DERR_TIMEOUT);
+    um.failed = 1;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, mc = warp >> 2, q = warp & 3;
+  if (ok && mc < mch) {
+    const int r = mc * 128 + q * 32 + lane;
+    for (int cg = 0; cg < ncols; cg += 32) {
+      float acc[32], part[32];
+      const int nc = min(32, ncols - cg);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = (r < vrows && j < nc) ? C[r + (cg + j) * ldc] : 0.f;
+      for (int ks = 0; ks < nks; ++ks) {
+        tmem_ld32(um.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((mc * nks + ks) * npad + cg), part);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] += part[j];
+      }
+      if (r < vrows) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nc) C[r + (cg + j) * ldc] = acc[j];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  return ok;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Panel factor sub-task PF(b): factors inner block b (columns b*ib .. b*ib + ib - 1) of a panel task
 // and writes its reflectors in place and its T block.  GE: rows b*ib .. nb-1 of tile X.  TS: the
 // triangle of pivot tile A's diagonal block b over all rows of X.  TT: the same triangle over the upper
@@ -1015,6 +1241,66 @@ __device__ void task_update(unsigned char* smb, int type, const E* X, E* Cp, E* 
     }
   }
   store_tile(Cs + row_lo * L.lc, L.lc, 1, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
+}
+
+// FP32-storage update (strip or panel-block update, as task_update) with phase 3 on tcgen05: V blocks are
+// staged in the core-matrix layout.  Used when the CTA holds TMEM for it (ExecParams::umma_cols) and the
+// shapes fit (ib 16 or 32, 32 or 64 columns: the epilogue reads TMEM 32 columns at a time); returns
+// false when it does not apply (the caller then runs task_update).
+__device__ bool task_update_umma(unsigned char* smb, int type, const float* X, float* Cp, float* C, int tr,
+                                 bool notrans, const float* Tg, int nb, int ib, int w, int blk0, int blk1, int col0,
+                                 int ncols, Umma& um, const ExecParams& prm) {
+  const int kb = ib;
+  const int npad = (ncols + 15) & ~15;
+  if (um.ncols_alloc == 0 || (kb != 16 && kb != 32) || (nb & 15) || (ncols & 31) || ncols > 64 ||
+      ((nb + 127) >> 7) * (kb >> 3) * npad > (int)um.ncols_alloc)
+    return false;
+  const Layout L = layout_update(nb, ib, w, 4);
+  // the C strip column-major with ldc = nb + 4 (fits the row-major region of nb x lc floats)
+  const int ldc = nb + 4;
+  if ((size_t)ldc * ncols > (size_t)nb * L.lc) return false;
+  float* sm = reinterpret_cast<float*>(smb + kHeaderDoubles * sizeof(double));
+  float *Cs = sm + L.Cs, *Ct = sm + L.Ct, *Vl = sm + L.V, *Vh = sm + L.Vh, *Tb = sm + L.Tb, *W = sm + L.W;
+  float *W2 = sm + L.W2, *Bl = sm + L.B, *Bh = Bl + kb * npad;
+  if ((smem_u32(Vl) | smem_u32(Vh) | smem_u32(Bl) | smem_u32(Bh)) & 127) return false;
+  const int row_lo = (type == UNMQR) ? blk0 * ib : 0;
+  const int row_hi = (type == TTMQR) ? blk1 * ib : nb;
+  load_tile(Cs + row_lo, 1, ldc, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
+  const int nbk = blk1 - blk0;
+  for (int bb = 0; bb < nbk; ++bb) {
+    const int b = notrans ? blk1 - 1 - bb : blk0 + bb;
+    const int c0 = b * ib;
+    float tv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = threadIdx.x + k * kThreads;
+      tv[k] = o < kb * kb ? ldg(Tg + (size_t)c0 * ib + o) : 0.f;
+    }
+    const int vrows = (type == UNMQR) ? nb - c0 : ((type == TSMQR) ? nb : c0 + kb);
+    float *Cb, *Ctop = nullptr;
+    if (type == UNMQR) {
+      load_v_core(Vl, Vh, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
+      Cb = Cs + c0;
+    } else {
+      load_v_core(Vl, Vh, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER);
+      load_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
+      Ctop = Ct;
+      Cb = Cs;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = threadIdx.x + k * kThreads;
+      if (o < kb * kb) Tb[o] = tv[k];
+    }
+    __syncthreads();
+    apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, Ctop, Cb, ldc, L.lc, ncols, W, W2, Bh, Bl, um, prm);
+    if (Ctop) {
+      store_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
+      __syncthreads();
+    }
+  }
+  store_tile(Cs + row_lo, 1, ldc, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1459,10 +1745,35 @@ __device__ __forceinline__ int32_t grad_ref(int32_t ref) {
 // Taking tasks in queue order makes the scheme deadlock-free whatever the number of resident CTAs.
 template <typename E, bool kBwd>
 __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm) {
-  extern __shared__ __align__(16) unsigned char smb[];
+  extern __shared__ __align__(128) unsigned char smb[];
   __shared__ int s_idx;
   __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_tmem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // FP32 storage: TMEM columns for the tcgen05 phase of the updates, held for the whole launch (the host
+  // enables it only with one CTA per SM, so the allocation never waits), and the MMA completion barrier
+  Umma um{0u, 0u, 0u, 0u, 0};
+  if constexpr (sizeof(E) == 4 && !kBwd) {
+    if (prm.umma_cols > 0) {
+      if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"((uint32_t)prm.umma_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+      }
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      um.tmem = s_tmem;
+      um.mbar = smem_u32(&s_mbar);
+      um.ncols_alloc = (uint32_t)prm.umma_cols;
+    }
+  }
   for (;;) {
     if (threadIdx.x == 0) {
       s_idx = (ld_relaxed(prm.err) != 0) ? prm.ntasks : atomicAdd(prm.head, 1);
@@ -1515,6 +1826,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     const int blk = (t.op >> 16) & 0xff;
     const int kind = (t.op >> 24) & 3;
     bool ok = true;
+    bool on_tc5 = false;      // the update ran its C -= V W product on tcgen05 (recorded in the trace)
     MatView mv;
     if (prm.mats) {
       const int mat = (t.flags >> 8) & 0xffffff;
@@ -1548,11 +1860,19 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
       case PU: {
         E* A = (kind == PM_GE) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
         const int utype = kind == PM_GE ? UNMQR : (kind == PM_TS ? TSMQR : TTMQR);
-        if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT)
-          task_update(smb, utype, X, A, X, tr, false, Tg, nb, ib, wst, blk, blk + 1, strip * ib, ib,
-                      prm.f32_simt != 0);
-        else
+        if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT) {
+          bool done = false;
+          if constexpr (sizeof(E) == 4)
+            if (prm.f32_simt == 0)
+              done = task_update_umma(smb, utype, X, A, X, tr, false, Tg, nb, ib, wst, blk, blk + 1, strip * ib, ib,
+                                      um, prm);
+          on_tc5 = done;
+          if (!done)
+            task_update(smb, utype, X, A, X, tr, false, Tg, nb, ib, wst, blk, blk + 1, strip * ib, ib,
+                        prm.f32_simt == 1);
+        } else {
           ok = false;
+        }
         break;
       }
       case UNMQR:
@@ -1561,11 +1881,19 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         E* A = (type == UNMQR) ? nullptr : tile_ptr<E>(prm, mv, t.a, ok);
         E* C = tile_ptr<E>(prm, mv, t.c, ok);
         const int col0 = strip * wst;
-        if (ok && Tg && col0 < nb)
-          task_update(smb, type, X, A, C, tr, notrans, Tg, nb, ib, wst, 0, nblk, col0, min(wst, nb - col0),
-                      prm.f32_simt != 0);
-        else
+        if (ok && Tg && col0 < nb) {
+          bool done = false;
+          if constexpr (sizeof(E) == 4)
+            if (prm.f32_simt == 0)
+              done = task_update_umma(smb, type, X, A, C, tr, notrans, Tg, nb, ib, wst, 0, nblk, col0,
+                                      min(wst, nb - col0), um, prm);
+          on_tc5 = done;
+          if (!done)
+            task_update(smb, type, X, A, C, tr, notrans, Tg, nb, ib, wst, 0, nblk, col0, min(wst, nb - col0),
+                        prm.f32_simt == 1);
+        } else {
           ok = false;
+        }
         break;
       }
       case COPY: {
@@ -1612,7 +1940,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         if (ok && Tg && blk < strip && strip < nblk && kind <= PM_TT && bw.part && t.flags >= 0 &&
             t.flags < bw.nslots && (pus == 1 || pus == 2) && half < pus && pw * pus == ib)
           task_bwd_update(smb, utype, X, As, Xs, Ag, Xg, tr, Tg, nb, ib, bw.hw, blk, blk + 1, strip * ib + half * pw,
-                          pw, static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
+                          pw, static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt == 1);
         else
           ok = false;
         break;
@@ -1627,7 +1955,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         const int col0 = strip * wst;
         if (ok && Tg && col0 < nb && kind <= 2 && bw.part && t.flags >= 0 && t.flags < bw.nslots)
           task_bwd_update(smb, utype, X, Cps, Cs, Cpg, Cg, tr, Tg, nb, ib, bw.hw, 0, nblk, col0, min(wst, nb - col0),
-                          static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt != 0);
+                          static_cast<E*>(bw.part) + bw.slot_off[t.flags], prm.f32_simt == 1);
         else
           ok = false;
         break;
@@ -1681,8 +2009,19 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
         rec[0] = (int64_t)t_start;
         rec[1] = (int64_t)gtime();
         rec[2] = smid;
-        rec[3] = t.op;
+        rec[3] = (int64_t)(uint32_t)t.op | ((int64_t)on_tc5 << 32);
       }
+    }
+  }
+  if constexpr (sizeof(E) == 4 && !kBwd) {
+    if (prm.umma_cols > 0) {
+      // every MMA was waited for, except after a wait that ran out: wait (bounded) once more for it
+      if (um.failed) mbar_wait(um.mbar, um.phase ^ 1u, prm.wait_ns);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(um.tmem), "r"(um.ncols_alloc)
+                     : "memory");
     }
   }
 }

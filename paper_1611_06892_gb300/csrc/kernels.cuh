@@ -64,7 +64,9 @@ struct ExecParams {
   int esize;            // 8: FP64 tiles; 4: FP32 tiles (split-precision updates)
   const MatInfo* mats;  // batched program: per-matrix parameters (null for one matrix)
   int nmats;
-  int f32_simt;         // FP32 tiles only: 1 = updates by FP32 FFMA instead of three TF32 tensor-core products
+  int f32_simt;         // FP32 tiles only: 0 = three-TF32 tensor-core updates (tcgen05 where umma_cols > 0),
+                        // 1 = updates by FP32 FFMA, 2 = three-TF32 updates on the warp-level MMA only
+  int umma_cols;        // FP32 forward program: TMEM columns each CTA allocates for the tcgen05 phase (0: none)
   int f32_scalars64;    // FP32 tiles only: 1 = reflector beta / tau / scale in FP64 instead of float pairs
   BwdParams bwd;        // adjoint program only
 };

@@ -127,6 +127,33 @@ def test_split_fp32_scalar_modes(torch_mod):
     assert np.abs(bands[0] - bands[1]).max() <= 64 * 2.0 ** -24 * nA
 
 
+def test_split_fp32_update_modes(torch_mod):
+    """The FP32-storage updates with the C -= V W product on tcgen05 (default, one matrix, 64-column
+    strips), on the warp-level tensor cores only (BIDIAG_OPT_F32_UPDATES = 2) and by FFMA (= 1): each meets
+    the FP64-oracle checks; the trace shows that the default really ran updates on tcgen05 and the other
+    modes none; the two three-TF32 forms agree to a few FP32 roundings."""
+    torch = torch_mod
+    A32 = inputs.gaussian(700, 520, seed=21).astype(np.float32)
+    nA = np.linalg.norm(A32.astype(np.float64))
+    bands = {}
+    for mode in (0, 2, 1):
+        h = G.Handle()
+        h.set_option(G.OPT_AUTO_RESOURCES, 3)
+        h.set_option(G.OPT_F32_UPDATES, mode)
+        try:
+            check(torch, h, A32, 256, 32, "auto", "bidiag")
+            h.set_option(G.OPT_TRACE, 1)
+            res = h.band(torch.from_numpy(np.asfortranarray(A32)).cuda(), 256, 32, "auto", "bidiag")
+            h.sync()
+            bands[mode] = res.band().cpu().numpy().astype(np.float64)
+            res.free()
+            tc5 = int(((h.trace()[:, 3] >> 32) & 1).sum())
+            assert (tc5 > 0) == (mode == 0), (mode, tc5)
+        finally:
+            h.close()
+    assert np.abs(bands[0] - bands[2]).max() <= 64 * 2.0 ** -24 * nA
+
+
 @pytest.mark.parametrize("m,n,tree,variant,seed", [(65536, 1024, "greedy", "rbidiag", 4),
                                                    (65536, 2048, "auto", "rbidiag", 5),
                                                    (8192, 8192, "auto", "bidiag", 2)],
