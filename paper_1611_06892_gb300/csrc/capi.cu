@@ -187,8 +187,22 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
              const bd::MatInfo* d_mats = nullptr, int nmats = 0, size_t smem_batch = 0,
              const void* const* bx = nullptr, const int64_t* nx = nullptr, const bd::BwdParams* bwd = nullptr) {
   if (ntasks == 0) return BIDIAG_OK;
-  const size_t smem = d_mats ? smem_batch
-                             : (bwd ? bd::bwd_smem_bytes(nb, ib, bwd->hw, esize) : bd::exec_smem_bytes(nb, ib, w, esize));
+  size_t smem = d_mats ? smem_batch : (bwd ? bd::bwd_smem_bytes(nb, ib, bwd->hw, esize) : bd::exec_smem_bytes(nb, ib, w, esize));
+  // tcgen05 updates (FP32 forward, one CTA per SM): TMEM for one accumulator of N = max(w, ib) (rounded to
+  // 16) columns per 128-row chunk of the tile and per k-step of 8, allocated as a power of two of at
+  // least 32 columns, and the shared memory of that path's layout
+  int umma_cols = 0;
+  if (esize == 4 && !bwd && !d_mats && h->f32_simt == 0 && nb % 16 == 0 && ib == 32 && w <= 64) {
+    const int need = ((nb + 127) / 128) * (ib / 8) * ((std::max(w, ib) + 15) / 16 * 16);
+    int cols = 32;
+    while (cols < need) cols *= 2;
+    const size_t su = std::max(smem, bd::umma_smem_bytes(nb, ib, w));
+    if (cols <= 512 && su <= h->smem_optin && bd::exec_set_smem(su, esize, false) == cudaSuccess &&
+        bd::exec_max_ctas_per_sm(su, esize, false) == 1) {
+      umma_cols = cols;
+      smem = su;
+    }
+  }
   CK(h, bd::exec_set_smem(smem, esize, bwd != nullptr));
   const int per_sm = std::max(1, bd::exec_max_ctas_per_sm(smem, esize, bwd != nullptr));
   bd::ExecParams prm{};
@@ -216,16 +230,7 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   prm.esize = esize;
   prm.f32_simt = h->f32_simt;
   prm.f32_scalars64 = h->f32_scalars64;
-  prm.umma_cols = 0;
-  if (esize == 4 && !bwd && !d_mats && h->f32_simt == 0 && per_sm == 1 && nb % 16 == 0 && (ib == 16 || ib == 32) &&
-      w <= 64) {
-    // TMEM for the tcgen05 phase: one accumulator of N = max(w, ib) (rounded to 16) columns per 128-row
-    // chunk of the tile and per k-step of 8, allocated as a power of two of at least 32 columns
-    const int need = ((nb + 127) / 128) * (ib / 8) * ((std::max(w, ib) + 15) / 16 * 16);
-    int cols = 32;
-    while (cols < need) cols *= 2;
-    if (cols <= 512) prm.umma_cols = cols;
-  }
+  prm.umma_cols = umma_cols;
   prm.mats = d_mats;
   prm.nmats = nmats;
   prm.trace = nullptr;

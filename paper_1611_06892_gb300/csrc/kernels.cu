@@ -106,7 +106,7 @@ __host__ __device__ inline Layout layout_update(int nb, int ib, int w, int esize
   L.Cs = o;  o = align4(o + nb * L.lc);
   L.Ct = o;  o = align32(o + ib * L.lc);
   L.V = o;   o = align32(o + nb * L.lv);     // MMA operand regions start on 128-byte boundaries
-  L.Tb = o;  o = align4(o + ib * ib);
+  L.Tb = o;  o = align4(o + ib * (ib + 4));  // T (ld ib, or ib + 4 in the tcgen05 path)
   L.W = o;   o = align4(o + ib * L.lc);
   L.W2 = o;  o = align32(o + ib * L.lc);
   L.Vh = L.B = -1;
@@ -197,47 +197,54 @@ __device__ __forceinline__ void put(E* s, E* hi, int i, E v) {
   s[i] = v;
 }
 
+// Up to 256 x 32 elements: all of a thread's loads (up to 32) are issued before the first shared store, so
+// that one L2 latency covers the whole block.  Lanes run along the contiguous direction of global memory.
+template <typename E>
+__device__ __forceinline__ void load_block32(E* s, int rs, int cs, const E* g, int nb, int tr, int r0, int c0,
+                                             int rows, int cols, int mask, E* hi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  E v[32];
+  if (!tr) {   // c = warp + 8 kc, r = lane + 32 kr
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+#pragma unroll
+      for (int kr = 0; kr < 8; ++kr) {
+        const int c = warp + 8 * kc, r = lane + 32 * kr;
+        v[kc * 8 + kr] = (c < cols && r < rows) ? masked_ld(g, r0 + r, c0 + c, nb, tr, mask) : E(0);
+      }
+    }
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+#pragma unroll
+      for (int kr = 0; kr < 8; ++kr) {
+        const int c = warp + 8 * kc, r = lane + 32 * kr;
+        if (c < cols && r < rows) put(s, hi, r * rs + c * cs, v[kc * 8 + kr]);
+      }
+    }
+  } else {     // r = warp + 8 kr, c = lane
+#pragma unroll
+    for (int kr = 0; kr < 32; ++kr) {
+      const int r = warp + 8 * kr;
+      v[kr] = (lane < cols && r < rows) ? masked_ld(g, r0 + r, c0 + lane, nb, tr, mask) : E(0);
+    }
+#pragma unroll
+    for (int kr = 0; kr < 32; ++kr) {
+      const int r = warp + 8 * kr;
+      if (lane < cols && r < rows) put(s, hi, r * rs + lane * cs, v[kr]);
+    }
+  }
+}
+
 // Shared element (r, c) at s[r * rs + c * cs] <- oriented X(r0 + r, c0 + c).  M_UPPER zeroes entries
-// below the diagonal, M_UNITLOWER gives the unit lower trapezoid.  Lanes run along the contiguous
-// direction of global memory (rows for tr = 0, columns for tr = 1).  Blocks of at most 256 x 32 (every
-// block the sub-tasks move) issue all of a thread's loads (up to 32) before the first shared store, so
-// that one L2 latency covers the whole block.  With hi != null (FP32) the block is stored split: TF32
-// high parts in hi, low parts in s (same indexing).
+// below the diagonal, M_UNITLOWER gives the unit lower trapezoid.  Blocks of at most 256 x 32 go through
+// load_block32.  With hi != null (FP32) the block is stored split: TF32 high parts in hi, low parts in s
+// (same indexing).
 template <typename E>
 __device__ void load_tile(E* s, int rs, int cs, const E* g, int nb, int tr, int r0, int c0, int rows, int cols,
                           int mask, E* hi = nullptr) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (rows <= 256 && cols <= 32) {
-    E v[32];
-    if (!tr) {   // c = warp + 8 kc, r = lane + 32 kr
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-#pragma unroll
-        for (int kr = 0; kr < 8; ++kr) {
-          const int c = warp + 8 * kc, r = lane + 32 * kr;
-          v[kc * 8 + kr] = (c < cols && r < rows) ? masked_ld(g, r0 + r, c0 + c, nb, tr, mask) : E(0);
-        }
-      }
-#pragma unroll
-      for (int kc = 0; kc < 4; ++kc) {
-#pragma unroll
-        for (int kr = 0; kr < 8; ++kr) {
-          const int c = warp + 8 * kc, r = lane + 32 * kr;
-          if (c < cols && r < rows) put(s, hi, r * rs + c * cs, v[kc * 8 + kr]);
-        }
-      }
-    } else {     // r = warp + 8 kr, c = lane
-#pragma unroll
-      for (int kr = 0; kr < 32; ++kr) {
-        const int r = warp + 8 * kr;
-        v[kr] = (lane < cols && r < rows) ? masked_ld(g, r0 + r, c0 + lane, nb, tr, mask) : E(0);
-      }
-#pragma unroll
-      for (int kr = 0; kr < 32; ++kr) {
-        const int r = warp + 8 * kr;
-        if (lane < cols && r < rows) put(s, hi, r * rs + lane * cs, v[kr]);
-      }
-    }
+    load_block32(s, rs, cs, g, nb, tr, r0, c0, rows, cols, mask, hi);
     return;
   }
   if (!tr) {
@@ -1004,41 +1011,6 @@ __device__ __forceinline__ int core_idx(int row, int k, int kb) {
   return (row >> 3) * (kb << 3) + ((k >> 2) << 5) + ((row & 7) << 2) + (k & 3);
 }
 
-// V block (oriented X(r0 + r, c0 + a), r < vrows, a < kb <= 32, masked as load_tile) into the core-matrix
-// layout, split: TF32 high parts in Vh, low parts in Vl.  All of a thread's loads are issued first.
-__device__ void load_v_core(float* Vl, float* Vh, const float* g, int nb, int tr, int r0, int c0, int vrows, int kb,
-                            int mask) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float v[32];
-  if (!tr) {   // a = warp + 8 ka, r = lane + 32 kr
-#pragma unroll
-    for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-      for (int kr = 0; kr < 8; ++kr) {
-        const int a = warp + 8 * ka, r = lane + 32 * kr;
-        v[ka * 8 + kr] = (a < kb && r < vrows) ? masked_ld(g, r0 + r, c0 + a, nb, tr, mask) : 0.0f;
-      }
-#pragma unroll
-    for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-      for (int kr = 0; kr < 8; ++kr) {
-        const int a = warp + 8 * ka, r = lane + 32 * kr;
-        if (a < kb && r < vrows) put(Vl, Vh, core_idx(r, a, kb), v[ka * 8 + kr]);
-      }
-  } else {     // r = warp + 8 kr, a = lane
-#pragma unroll
-    for (int kr = 0; kr < 32; ++kr) {
-      const int r = warp + 8 * kr;
-      v[kr] = (lane < kb && r < vrows) ? masked_ld(g, r0 + r, c0 + lane, nb, tr, mask) : 0.0f;
-    }
-#pragma unroll
-    for (int kr = 0; kr < 32; ++kr) {
-      const int r = warp + 8 * kr;
-      if (lane < kb && r < vrows) put(Vl, Vh, core_idx(r, lane, kb), v[kr]);
-    }
-  }
-}
-
 // Phase 1 (warp-level tensor cores) reading V from the core-matrix layout: W = Ct + V^T C, with the C
 // strip column-major (leading dimension ldc) and Ct, W row-major (lc).
 __device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows, int kb, const float* Ct,
@@ -1073,6 +1045,7 @@ __device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows
 }
 
 // The whole block application W = op(T) (Ct + V^T C), Ct -= W, C -= V W with V in the core-matrix layout
+// (Tb: op(T) column-major with leading dimension kb + 4, see phase 2)
 // (load_v_core) and the C strip column-major (ldc; one row per lane in the epilogue is then free of bank
 // conflicts): phase 1 on the warp-level tensor cores, phase 2 on the FMA units, phase 3 with tcgen05.
 // Bh / Bl: kb x 64 floats each for the split -W2 operand.  Returns false if the MMA completion wait ran
@@ -1082,19 +1055,36 @@ __device__ bool apply_rm_umma(const float* Vh, const float* Vl, int vrows, int k
                               float* Bl, Umma& um, const ExecParams& prm) {
   apply_phase1_tc_core(Vh, Vl, vrows, kb, Ct, C, ldc, lc, ncols, W);
   __syncthreads();
-  // phase 2: W2 = op(T) W, Ct -= W2 (as apply_rm), and -W2 into the B operand (ncols rows of K = kb)
+  // phase 2: S = op(T) W, then Ct -= S and -S, split, into the B operand of the tcgen05 phase (ncols rows
+  // of K = kb, core-matrix layout).  Tb holds op(T) (T^T for Q^T, T for Q) column-major with leading
+  // dimension kb + 4, its zeros included; a thread forms 4 consecutive rows a0..a0+3 of one column c, so
+  // that op(T)(a0..a0+3, t) is one float4 and the 4 split values are one 16-byte store per part.  Each
+  // sum runs in increasing t over the triangle's range (the extra terms multiply stored zeros).
   const int npad = (ncols + 15) & ~15;
-  for (int u = threadIdx.x; u < ncols * kb; u += kThreads) {
-    const int c = u % ncols, a = u / ncols;
-    float s = 0.f;
-    if (!notrans) {
-      for (int t = 0; t <= a; ++t) s = fmaf(Tb[t + a * kb], W[t * lc + c], s);
-    } else {
-      for (int t = a; t < kb; ++t) s = fmaf(Tb[a + t * kb], W[t * lc + c], s);
+  {
+    const int lt = kb + 4, lg = 31 - __clz(ncols);            // ncols in {32, 64}
+    for (int u = threadIdx.x; u < ncols * (kb >> 2); u += kThreads) {
+      const int c = u & (ncols - 1), a0 = (u >> lg) << 2;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const int tlo = notrans ? a0 : 0, thi = notrans ? kb : a0 + 4;
+      for (int t = tlo; t < thi; ++t) {
+        const float wv = W[t * lc + c];
+        const float4 tv = *reinterpret_cast<const float4*>(Tb + a0 + t * lt);
+        acc[0] = fmaf(tv.x, wv, acc[0]);
+        acc[1] = fmaf(tv.y, wv, acc[1]);
+        acc[2] = fmaf(tv.z, wv, acc[2]);
+        acc[3] = fmaf(tv.w, wv, acc[3]);
+      }
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (Ct) Ct[(a0 + k) * lc + c] -= acc[k];
+        split_tf32(-acc[k], hi[k], lo[k]);
+      }
+      const int bi = core_idx(c, a0, kb);
+      *reinterpret_cast<uint4*>(Bh + bi) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(Bl + bi) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
-    W2[a * lc + c] = s;
-    if (Ct) Ct[a * lc + c] -= s;
-    put(Bl, Bh, core_idx(c, a, kb), -s);
   }
   for (int u = threadIdx.x; u < (npad - ncols) * kb; u += kThreads) {   // zero rows of the padded N
     const int c = ncols + u / kb, a = u % kb;
@@ -1243,57 +1233,147 @@ __device__ void task_update(unsigned char* smb, int type, const E* X, E* Cp, E* 
   store_tile(Cs + row_lo * L.lc, L.lc, 1, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
 }
 
-// FP32-storage update (strip or panel-block update, as task_update) with phase 3 on tcgen05: V blocks are
-// staged in the core-matrix layout.  Used when the CTA holds TMEM for it (ExecParams::umma_cols) and the
-// shapes fit (ib 16 or 32, 32 or 64 columns: the epilogue reads TMEM 32 columns at a time); returns
-// false when it does not apply (the caller then runs task_update).
+// Shared-memory layout of the tcgen05 update path (FP32 storage): the C strip column-major (ldc = nb + 4),
+// Ct and W row-major (lc), V split into TF32 high / low parts in the core-matrix layout, a staging
+// buffer for the next block's raw V (column-major ld nb, or row-major ld ib + 4 for transposed tiles),
+// op(T) (ld ib + 4) and the split -op(T) W operand.  Offsets in floats.
+struct UmmaLayout {
+  int ldc, lc, Cs, Ct, Vl, Vh, Vr, Tb, W, B, total;
+};
+__host__ __device__ inline UmmaLayout layout_umma(int nb, int ib, int w) {
+  UmmaLayout L{};
+  const int wc = w > ib ? w : ib;
+  L.ldc = nb + 4;
+  L.lc = rm_ld(wc, 4);
+  int o = 0;
+  L.Cs = o;  o = align32(o + L.ldc * wc);
+  L.Ct = o;  o = align32(o + ib * L.lc);
+  L.Vl = o;  o = align32(o + nb * ib);
+  L.Vh = o;  o = align32(o + nb * ib);
+  L.Vr = o;  o = align32(o + nb * (ib + 4));
+  L.Tb = o;  o = align32(o + ib * (ib + 4));
+  L.W = o;   o = align32(o + ib * L.lc);
+  L.B = o;   o = align32(o + 2 * ib * ((wc + 15) / 16 * 16));
+  L.total = o;
+  return L;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Starts the copy of V block (oriented X(r0 + r, c0 + a), r < vrows, a < kb) into the staging buffer Vr in
+// 16-byte pieces (one commit group): column-major (ld nb) for tr = 0, row-major (ld kb + 4) for tr = 1.
+__device__ void prefetch_v(float* Vr, const float* X, int nb, int tr, int r0, int c0, int vrows, int kb) {
+  const int nch = (vrows * kb) >> 2;
+  for (int q = threadIdx.x; q < nch; q += kThreads) {
+    if (!tr) {
+      const int rq = vrows >> 2, a = q / rq, r = (q % rq) << 2;
+      cp_async16(Vr + a * nb + r, X + (r0 + r) + (size_t)(c0 + a) * nb);
+    } else {
+      const int aq = kb >> 2, r = q / aq, a = (q % aq) << 2;
+      cp_async16(Vr + r * (kb + 4) + a, X + (size_t)(r0 + r) * nb + c0 + a);
+    }
+  }
+  cp_async_commit();
+}
+
+// Staged V block -> TF32 high / low parts in the core-matrix layout, with the mask of load_tile applied in
+// oriented coordinates (R = r0 + r, C = c0 + a).  A thread handles 4 consecutive a of one row: one
+// 16-byte core row per part.
+__device__ void split_v_core(const float* Vr, float* Vl, float* Vh, int nb, int tr, int r0, int c0, int vrows,
+                             int kb, int mask) {
+  const int nq = kb >> 2;
+  for (int u = threadIdx.x; u < vrows * nq; u += kThreads) {
+    const int r = u % vrows, a0 = (u / vrows) << 2;
+    float x[4];
+    if (tr) {
+      const float4 v = *reinterpret_cast<const float4*>(Vr + r * (kb + 4) + a0);
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = Vr[(a0 + k) * nb + r];
+    }
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int R = r0 + r, C = c0 + a0 + k;
+      if (mask == M_UPPER && R > C) x[k] = 0.f;
+      if (mask == M_UNITLOWER && R <= C) x[k] = (R == C) ? 1.f : 0.f;
+      split_tf32(x[k], hi[k], lo[k]);
+    }
+    const int ci = core_idx(r, a0, kb);
+    *reinterpret_cast<uint4*>(Vh + ci) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(Vl + ci) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+// FP32-storage update (strip or panel-block update, as task_update) with phase 3 on tcgen05; the next
+// block's V is copied (cp.async) while the current block is applied.  Used when the CTA holds TMEM for it
+// (ExecParams::umma_cols) and the shapes fit (ib 32, 32 or 64 columns: the epilogue reads TMEM 32
+// columns at a time); returns false when it does not apply (the caller then runs task_update).
 __device__ bool task_update_umma(unsigned char* smb, int type, const float* X, float* Cp, float* C, int tr,
                                  bool notrans, const float* Tg, int nb, int ib, int w, int blk0, int blk1, int col0,
                                  int ncols, Umma& um, const ExecParams& prm) {
   const int kb = ib;
   const int npad = (ncols + 15) & ~15;
-  if (um.ncols_alloc == 0 || (kb != 16 && kb != 32) || (nb & 15) || (ncols & 31) || ncols > 64 ||
+  if (um.ncols_alloc == 0 || kb != 32 || (nb & 15) || (ncols & 31) || ncols > 64 || ncols > (w > ib ? w : ib) ||
       ((nb + 127) >> 7) * (kb >> 3) * npad > (int)um.ncols_alloc)
     return false;
-  const Layout L = layout_update(nb, ib, w, 4);
-  // the C strip column-major with ldc = nb + 4 (fits the row-major region of nb x lc floats)
-  const int ldc = nb + 4;
-  if ((size_t)ldc * ncols > (size_t)nb * L.lc) return false;
+  const UmmaLayout L = layout_umma(nb, ib, w);
   float* sm = reinterpret_cast<float*>(smb + kHeaderDoubles * sizeof(double));
-  float *Cs = sm + L.Cs, *Ct = sm + L.Ct, *Vl = sm + L.V, *Vh = sm + L.Vh, *Tb = sm + L.Tb, *W = sm + L.W;
-  float *W2 = sm + L.W2, *Bl = sm + L.B, *Bh = Bl + kb * npad;
+  float *Cs = sm + L.Cs, *Ct = sm + L.Ct, *Vl = sm + L.Vl, *Vh = sm + L.Vh, *Vr = sm + L.Vr, *Tb = sm + L.Tb;
+  float *W = sm + L.W, *Bl = sm + L.B, *Bh = Bl + kb * npad;
   if ((smem_u32(Vl) | smem_u32(Vh) | smem_u32(Bl) | smem_u32(Bh)) & 127) return false;
+  const int ldc = L.ldc;
   const int row_lo = (type == UNMQR) ? blk0 * ib : 0;
   const int row_hi = (type == TTMQR) ? blk1 * ib : nb;
-  load_tile(Cs + row_lo, 1, ldc, C, nb, tr, row_lo, col0, row_hi - row_lo, ncols, M_NONE);
   const int nbk = blk1 - blk0;
+  auto blk_of = [&](int bb) { return notrans ? blk1 - 1 - bb : blk0 + bb; };
+  auto rows_of = [&](int c0) { return (type == UNMQR) ? nb - c0 : ((type == TSMQR) ? nb : c0 + kb); };
+  auto r0_of = [&](int c0) { return (type == UNMQR) ? c0 : 0; };
+  {
+    const int c0 = blk_of(0) * ib;
+    prefetch_v(Vr, X, nb, tr, r0_of(c0), c0, rows_of(c0), kb);
+  }
+  load_tile(Cs + row_lo, 1, ldc, C, nb, tr, row_lo, col0, row_hi - row_lo, min(ncols, 32), M_NONE);
+  if (ncols > 32)
+    load_tile(Cs + row_lo + 32 * ldc, 1, ldc, C, nb, tr, row_lo, col0 + 32, row_hi - row_lo, ncols - 32, M_NONE);
   for (int bb = 0; bb < nbk; ++bb) {
-    const int b = notrans ? blk1 - 1 - bb : blk0 + bb;
-    const int c0 = b * ib;
+    const int b = blk_of(bb);
+    const int c0 = b * ib, vrows = rows_of(c0);
     float tv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int o = threadIdx.x + k * kThreads;
       tv[k] = o < kb * kb ? ldg(Tg + (size_t)c0 * ib + o) : 0.f;
     }
-    const int vrows = (type == UNMQR) ? nb - c0 : ((type == TSMQR) ? nb : c0 + kb);
+    cp_async_wait_all();
+    __syncthreads();                       // this block's V is in the staging buffer
+    split_v_core(Vr, Vl, Vh, nb, tr, r0_of(c0), c0, vrows, kb,
+                 type == UNMQR ? M_UNITLOWER : (type == TSMQR ? M_NONE : M_UPPER));
     float *Cb, *Ctop = nullptr;
     if (type == UNMQR) {
-      load_v_core(Vl, Vh, X, nb, tr, c0, c0, vrows, kb, M_UNITLOWER);
       Cb = Cs + c0;
     } else {
-      load_v_core(Vl, Vh, X, nb, tr, 0, c0, vrows, kb, type == TSMQR ? M_NONE : M_UPPER);
-      load_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
+      load_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, min(ncols, 32), M_NONE);
+      if (ncols > 32) load_tile(Ct + 32, L.lc, 1, Cp, nb, tr, c0, col0 + 32, kb, ncols - 32, M_NONE);
       Ctop = Ct;
       Cb = Cs;
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int o = threadIdx.x + k * kThreads;
-      if (o < kb * kb) Tb[o] = tv[k];
+    for (int k = 0; k < 4; ++k) {   // op(T) column-major, ld kb + 4: T(r, c) is op(T)(r, c) or op(T)(c, r)
+      const int o = threadIdx.x + k * kThreads, r = o % kb, c = o / kb;
+      if (o < kb * kb) Tb[notrans ? r + c * (kb + 4) : c + r * (kb + 4)] = tv[k];
     }
-    __syncthreads();
-    apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, Ctop, Cb, ldc, L.lc, ncols, W, W2, Bh, Bl, um, prm);
+    __syncthreads();                       // the staging buffer is free again
+    if (bb + 1 < nbk) {
+      const int cn = blk_of(bb + 1) * ib;
+      prefetch_v(Vr, X, nb, tr, r0_of(cn), cn, rows_of(cn), kb);
+    }
+    apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, Ctop, Cb, ldc, L.lc, ncols, W, W, Bh, Bl, um, prm);
     if (Ctop) {
       store_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
       __syncthreads();
@@ -2184,6 +2264,10 @@ cudaError_t extract_t(const E* tiles, int64_t rows_t, int nb, int64_t n, E* ab, 
 size_t exec_smem_bytes(int nb, int ib, int w, int esize) {
   const Layout a = layout_panel(nb, ib, esize), b = layout_update(nb, ib, w, esize);
   return kHeaderDoubles * sizeof(double) + (size_t)esize * (size_t)(a.total > b.total ? a.total : b.total);
+}
+
+size_t umma_smem_bytes(int nb, int ib, int w) {
+  return kHeaderDoubles * sizeof(double) + sizeof(float) * (size_t)layout_umma(nb, ib, w).total;
 }
 
 size_t bwd_smem_bytes(int nb, int ib, int hw, int esize) {

@@ -73,6 +73,8 @@ struct ExecParams {
 
 // Shared memory (bytes) the executor needs for (nb, ib, w) and element size esize (8 or 4).
 size_t exec_smem_bytes(int nb, int ib, int w, int esize);
+// Dynamic shared memory of the FP32 forward executor when its updates take the tcgen05 path (ib 32).
+size_t umma_smem_bytes(int nb, int ib, int w);
 // Column-strip width of the update sub-tasks: a multiple of ib, at most nb, as close to `preferred`
 // as the shared-memory limit allows; 0 if even w = ib does not fit.
 int choose_strip_width(int nb, int ib, int preferred, size_t smem_limit, int esize);
