@@ -77,7 +77,15 @@ enum {
                                      the tail's squared norm (always a compensated sum, FP64-level accuracy)
                                      0 = in float-pair arithmetic, about 44 bits (default), 1 = in FP64.
                                      Both give the FP32 values the reduction stores to within their
-                                     rounding; FP64 costs ~1.7K cycles of serial FP64 latency per column */
+                                     rounding; FP64 costs ~1.7K cycles of serial FP64 latency per column */,
+  BIDIAG_OPT_WINDOW = 9           /* executor look-ahead, -1..1024: a CTA looking for work scans this many
+                                     queue entries from the head and takes the first whose dependencies
+                                     are done; only when none is ready does it take the head's entry and
+                                     wait for it.  0 = strict queue order; -1 (default) = 512 for a
+                                     one-matrix FP64 BiDiag reduction, else 0 (measured on 8192^2 and
+                                     4096^2: 2.8 / 3.2 % faster; FP32 storage, R-BiDiag and batches are
+                                     not faster).  Results do not depend on it: the program orders every
+                                     access to shared data, the window only changes timing */
 };
 
 /* Task type codes of the canonical task list (GELQT etc. are the same codes in LQ phases). */

@@ -32,6 +32,7 @@ NOALLOC_SCRATCH_BYTES = 8 << 20
 OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMING, OPT_TRACE = 1, 2, 3, 4, 5, 6
 OPT_F32_UPDATES = 7
 OPT_F32_SCALARS = 8
+OPT_WINDOW = 9
 
 _lib = None
 

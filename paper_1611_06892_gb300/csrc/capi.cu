@@ -108,6 +108,7 @@ struct bidiag_ctx {
   int tracing = 0;
   int f32_simt = 0;                // FP32 storage: updates by FFMA instead of 3xTF32 tensor-core products
   int f32_scalars64 = 0;           // FP32 storage: reflector scalars in FP64 instead of float pairs
+  int window = -1;                 // executor look-ahead (queue entries scanned); -1: by precision and variant
   int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
   std::map<std::tuple<int, int, int, int64_t>, int> splits;   // best three-step split per (p, q, tree, R)
   std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> batches;   // batch programs by shapes / options
@@ -185,7 +186,8 @@ int64_t resources_of(bidiag_handle h, int nb, int w, int esize) {
 int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n0, void* b1, int64_t n1, void* b2,
              int64_t n2, void* T, int npanels, int nb, int ib, int w, int esize, bool timed = false,
              const bd::MatInfo* d_mats = nullptr, int nmats = 0, size_t smem_batch = 0,
-             const void* const* bx = nullptr, const int64_t* nx = nullptr, const bd::BwdParams* bwd = nullptr) {
+             const void* const* bx = nullptr, const int64_t* nx = nullptr, const bd::BwdParams* bwd = nullptr,
+             int auto_window = 0) {
   if (ntasks == 0) return BIDIAG_OK;
   size_t smem = d_mats ? smem_batch : (bwd ? bd::bwd_smem_bytes(nb, ib, bwd->hw, esize) : bd::exec_smem_bytes(nb, ib, w, esize));
   // tcgen05 updates (FP32 forward, one CTA per SM): TMEM for one accumulator of N = max(w, ib) (rounded to
@@ -230,6 +232,7 @@ int run_exec(bidiag_handle h, const PlanDev& pd, int ntasks, void* b0, int64_t n
   prm.esize = esize;
   prm.f32_simt = h->f32_simt;
   prm.f32_scalars64 = h->f32_scalars64;
+  prm.window = h->window >= 0 ? h->window : auto_window;
   prm.umma_cols = umma_cols;
   prm.mats = d_mats;
   prm.nmats = nmats;
@@ -516,7 +519,8 @@ int band_impl(bidiag_handle h, int64_t m, int64_t n, const E* d_A, int64_t lda, 
   }
   rc = run_exec(h, *pd, (int)pd->plan.dev.size(), r->tiles, (int64_t)r->p * r->q, r->tiles2,
                 r->tiles2 ? (int64_t)r->q * r->q : 0, nullptr, 0, r->T, pd->plan.npanels, nb, ib, w, (int)sizeof(E),
-                timed);
+                timed, nullptr, 0, 0, nullptr, nullptr, nullptr,
+                (sizeof(E) == 8 && !r->tiles2) ? bd::kWindowF64BiDiag : 0);
   h->timed = timed;
   if (rc) return bail(rc);
   if (tiles2 && variant != BIDIAG_RBIDIAG) {
@@ -958,6 +962,10 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
     case BIDIAG_OPT_F32_SCALARS:
       if (value != 0 && value != 1) return -3;
       h->f32_scalars64 = (int)value;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_WINDOW:
+      if (value < -1 || value > 1024) return -3;
+      h->window = (int)value;
       return BIDIAG_OK;
     default:
       return -2;

@@ -1234,11 +1234,12 @@ __device__ void task_update(unsigned char* smb, int type, const E* X, E* Cp, E* 
 }
 
 // Shared-memory layout of the tcgen05 update path (FP32 storage): the C strip column-major (ldc = nb + 4),
-// Ct and W row-major (lc), V split into TF32 high / low parts in the core-matrix layout, a staging
-// buffer for the next block's raw V (column-major ld nb, or row-major ld ib + 4 for transposed tiles),
-// op(T) (ld ib + 4) and the split -op(T) W operand.  Offsets in floats.
+// Ct and W row-major (lc), V split into TF32 high / low parts in the core-matrix layout, op(T) (ld ib + 4),
+// the split -op(T) W operand, and staging buffers that receive the next block's raw V (column-major ld nb,
+// or row-major ld ib + 4 for transposed tiles), T (ib x ib, as stored) and Ct (column-major ld ib + 4, or
+// row-major lc for transposed tiles) while the current block is applied.  Offsets in floats.
 struct UmmaLayout {
-  int ldc, lc, Cs, Ct, Vl, Vh, Vr, Tb, W, B, total;
+  int ldc, lc, Cs, Ct, Vl, Vh, Vr, Tb, W, B, Tr, Cr, total;
 };
 __host__ __device__ inline UmmaLayout layout_umma(int nb, int ib, int w) {
   UmmaLayout L{};
@@ -1254,12 +1255,17 @@ __host__ __device__ inline UmmaLayout layout_umma(int nb, int ib, int w) {
   L.Tb = o;  o = align32(o + ib * (ib + 4));
   L.W = o;   o = align32(o + ib * L.lc);
   L.B = o;   o = align32(o + 2 * ib * ((wc + 15) / 16 * 16));
+  L.Tr = o;  o = align32(o + ib * ib);
+  L.Cr = o;  o = align32(o + max(wc * (ib + 4), ib * L.lc));
   L.total = o;
   return L;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -1277,7 +1283,43 @@ __device__ void prefetch_v(float* Vr, const float* X, int nb, int tr, int r0, in
       cp_async16(Vr + r * (kb + 4) + a, X + (size_t)(r0 + r) * nb + c0 + a);
     }
   }
-  cp_async_commit();
+}
+
+// Starts the copies of a block's T (kb x kb, contiguous) into Tr and of Ct = oriented Cp(c0 + r, col0 + c),
+// r < kb, c < ncols, into Cr: column-major ld kb + 4 for tr = 0 (16-byte pieces along r), row-major ld lc
+// for tr = 1 (pieces along c).
+__device__ void prefetch_t_ct(float* Tr, const float* T, float* Cr, const float* Cp, int nb, int tr, int c0, int col0,
+                              int kb, int ncols, int lc) {
+  for (int q = threadIdx.x; q < (kb * kb) >> 2; q += kThreads) cp_async16(Tr + 4 * q, T + 4 * q);
+  if (!Cp) return;
+  const int nch = (kb * ncols) >> 2;
+  for (int q = threadIdx.x; q < nch; q += kThreads) {
+    if (!tr) {
+      const int rq = kb >> 2, c = q / rq, r = (q % rq) << 2;
+      cp_async16(Cr + c * (kb + 4) + r, Cp + (c0 + r) + (size_t)(col0 + c) * nb);
+    } else {
+      const int cq = ncols >> 2, r = q / cq, c = (q % cq) << 2;
+      cp_async16(Cr + r * lc + c, Cp + (size_t)(c0 + r) * nb + col0 + c);
+    }
+  }
+}
+
+// Starts the copy of the C strip (oriented C(r, col0 + c), r0 <= r < r1, c < ncols) into Cs column-major
+// (ld ldc): 16-byte pieces along r for tr = 0, 4-byte pieces (coalesced along c) for tr = 1.
+__device__ void prefetch_c(float* Cs, int ldc, const float* C, int nb, int tr, int r0, int r1, int col0, int ncols) {
+  const int rows = r1 - r0;
+  if (!tr) {
+    const int rq = rows >> 2;
+    for (int q = threadIdx.x; q < rq * ncols; q += kThreads) {
+      const int c = q / rq, r = r0 + ((q % rq) << 2);
+      cp_async16(Cs + c * ldc + r, C + r + (size_t)(col0 + c) * nb);
+    }
+  } else {
+    for (int q = threadIdx.x; q < rows * ncols; q += kThreads) {
+      const int c = q % ncols, r = r0 + q / ncols;
+      cp_async4(Cs + c * ldc + r, C + (size_t)r * nb + col0 + c);
+    }
+  }
 }
 
 // Staged V block -> TF32 high / low parts in the core-matrix layout, with the mask of load_tile applied in
@@ -1325,57 +1367,46 @@ __device__ bool task_update_umma(unsigned char* smb, int type, const float* X, f
   const UmmaLayout L = layout_umma(nb, ib, w);
   float* sm = reinterpret_cast<float*>(smb + kHeaderDoubles * sizeof(double));
   float *Cs = sm + L.Cs, *Ct = sm + L.Ct, *Vl = sm + L.Vl, *Vh = sm + L.Vh, *Vr = sm + L.Vr, *Tb = sm + L.Tb;
-  float *W = sm + L.W, *Bl = sm + L.B, *Bh = Bl + kb * npad;
+  float *W = sm + L.W, *Bl = sm + L.B, *Bh = Bl + kb * npad, *Tr = sm + L.Tr, *Cr = sm + L.Cr;
   if ((smem_u32(Vl) | smem_u32(Vh) | smem_u32(Bl) | smem_u32(Bh)) & 127) return false;
-  const int ldc = L.ldc;
+  const int ldc = L.ldc, lc = L.lc;
   const int row_lo = (type == UNMQR) ? blk0 * ib : 0;
   const int row_hi = (type == TTMQR) ? blk1 * ib : nb;
   const int nbk = blk1 - blk0;
+  const bool top = type != UNMQR;   // TSMQR / TTMQR: the pivot tile's rows of the block are updated too
   auto blk_of = [&](int bb) { return notrans ? blk1 - 1 - bb : blk0 + bb; };
   auto rows_of = [&](int c0) { return (type == UNMQR) ? nb - c0 : ((type == TSMQR) ? nb : c0 + kb); };
   auto r0_of = [&](int c0) { return (type == UNMQR) ? c0 : 0; };
-  {
-    const int c0 = blk_of(0) * ib;
+  auto prefetch_block = [&](int c0) {
     prefetch_v(Vr, X, nb, tr, r0_of(c0), c0, rows_of(c0), kb);
-  }
-  load_tile(Cs + row_lo, 1, ldc, C, nb, tr, row_lo, col0, row_hi - row_lo, min(ncols, 32), M_NONE);
-  if (ncols > 32)
-    load_tile(Cs + row_lo + 32 * ldc, 1, ldc, C, nb, tr, row_lo, col0 + 32, row_hi - row_lo, ncols - 32, M_NONE);
+    prefetch_t_ct(Tr, Tg + (size_t)c0 * ib, Cr, top ? Cp : nullptr, nb, tr, c0, col0, kb, ncols, lc);
+    cp_async_commit();
+  };
+  prefetch_c(Cs, ldc, C, nb, tr, row_lo, row_hi, col0, ncols);
+  prefetch_block(blk_of(0) * ib);
   for (int bb = 0; bb < nbk; ++bb) {
     const int b = blk_of(bb);
     const int c0 = b * ib, vrows = rows_of(c0);
-    float tv[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int o = threadIdx.x + k * kThreads;
-      tv[k] = o < kb * kb ? ldg(Tg + (size_t)c0 * ib + o) : 0.f;
-    }
     cp_async_wait_all();
-    __syncthreads();                       // this block's V is in the staging buffer
+    __syncthreads();                       // this block's V, T, Ct (and the C strip) are staged
     split_v_core(Vr, Vl, Vh, nb, tr, r0_of(c0), c0, vrows, kb,
                  type == UNMQR ? M_UNITLOWER : (type == TSMQR ? M_NONE : M_UPPER));
-    float *Cb, *Ctop = nullptr;
-    if (type == UNMQR) {
-      Cb = Cs + c0;
-    } else {
-      load_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, min(ncols, 32), M_NONE);
-      if (ncols > 32) load_tile(Ct + 32, L.lc, 1, Cp, nb, tr, c0, col0 + 32, kb, ncols - 32, M_NONE);
-      Ctop = Ct;
-      Cb = Cs;
+    for (int o = threadIdx.x; o < kb * kb; o += kThreads) {   // op(T) column-major, ld kb + 4
+      const int r = o % kb, c = o / kb;
+      Tb[notrans ? r + c * (kb + 4) : c + r * (kb + 4)] = Tr[o];
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {   // op(T) column-major, ld kb + 4: T(r, c) is op(T)(r, c) or op(T)(c, r)
-      const int o = threadIdx.x + k * kThreads, r = o % kb, c = o / kb;
-      if (o < kb * kb) Tb[notrans ? r + c * (kb + 4) : c + r * (kb + 4)] = tv[k];
+    if (top) {
+      for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
+        const int r = o % kb, c = o / kb;
+        Ct[r * lc + c] = tr ? Cr[r * lc + c] : Cr[c * (kb + 4) + r];
+      }
     }
-    __syncthreads();                       // the staging buffer is free again
-    if (bb + 1 < nbk) {
-      const int cn = blk_of(bb + 1) * ib;
-      prefetch_v(Vr, X, nb, tr, r0_of(cn), cn, rows_of(cn), kb);
-    }
-    apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, Ctop, Cb, ldc, L.lc, ncols, W, W, Bh, Bl, um, prm);
-    if (Ctop) {
-      store_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
+    __syncthreads();                       // the staging buffers are free again
+    if (bb + 1 < nbk) prefetch_block(blk_of(bb + 1) * ib);
+    apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, top ? Ct : nullptr, top ? Cs : Cs + c0, ldc, lc, ncols, W, W,
+                  Bh, Bl, um, prm);
+    if (top) {
+      store_tile(Ct, lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
       __syncthreads();
     }
   }
@@ -1820,9 +1851,70 @@ __device__ __forceinline__ int32_t grad_ref(int32_t ref) {
   return (ref < 0 || buf < 2 || buf > 3) ? -1 : ref + (2 << 28);
 }
 
-// Persistent dataflow executor: CTAs take sub-tasks from a queue in topological priority order,
-// wait (bounded) until the sub-tasks they depend on are done, run them and publish completion.
-// Taking tasks in queue order makes the scheme deadlock-free whatever the number of resident CTAs.
+// Next sub-task of a CTA (warp 0; the result is valid in lane 0).  Each sub-task's flag word is 0 while
+// unclaimed, 2 once a CTA has claimed it and 1 when it is done.  First the CTA scans the `window` queue
+// entries from the head and claims the first one whose dependencies are all done (it then runs without
+// waiting); the head moves over a prefix found claimed.  If none is ready, it takes the head's entry
+// (atomic increment, skipping entries claimed out of order) and waits for it.  Deadlock-free whatever
+// the number of resident CTAs: a waiting CTA holds the lowest entry it could get in queue order, so
+// everything before it is claimed, and the lowest unfinished claimed sub-task always has its
+// dependencies done.  Returns ntasks when the queue is exhausted or the error word is set.
+__device__ int next_task(const ExecParams& prm) {
+  const int lane = threadIdx.x & 31;
+  const int n = prm.ntasks;
+  int err = 0;
+  if (lane == 0) err = ld_relaxed(prm.err);
+  if (__shfl_sync(kFull, err, 0) != 0) return n;   // warp-uniform exit
+  for (int base = 0; base < prm.window; base += 32) {
+    int h = 0;
+    if (lane == 0) h = ld_relaxed(prm.head);
+    h = __shfl_sync(kFull, h, 0);   // one head value for the whole warp
+    if (h >= n) return n;
+    const int i = h + base + lane;
+    int st = 1;
+    bool ready = false;
+    if (i < n && base + lane < prm.window) {
+      st = ld_relaxed(prm.done + i);
+      if (st == 0) {
+        const DevTask& t = prm.tasks[i];
+        const int d0 = t.dep_begin, d1 = t.dep_end;
+        ready = true;
+        for (int d = d0; d < d1; ++d) {
+          const int dep = prm.deps[d];
+          if (dep < 0 || dep >= prm.nflags || ld_acquire(prm.done + dep) != 1) { ready = false; break; }
+        }
+      }
+    }
+    if (base == 0) {   // move the head over entries already claimed
+      const unsigned open = __ballot_sync(kFull, st == 0);
+      const int skip = open ? __ffs(open) - 1 : 32;
+      if (lane == 0 && skip > 0 && h + skip <= n) atomicCAS(prm.head, h, h + skip);
+    }
+    unsigned rm = __ballot_sync(kFull, ready);
+    while (rm) {
+      const int l = __ffs(rm) - 1;
+      int got = 0;
+      if (lane == l) got = atomicCAS(prm.done + i, 0, 2) == 0;
+      got = __shfl_sync(kFull, got, l);
+      if (got) return __shfl_sync(kFull, i, l);
+      rm &= rm - 1;
+    }
+  }
+  int idx = n;
+  if (lane == 0) {
+    for (;;) {
+      if (ld_relaxed(prm.err) != 0) { idx = n; break; }
+      idx = atomicAdd(prm.head, 1);
+      if (idx >= n) { idx = n; break; }
+      if (atomicCAS(prm.done + idx, 0, 2) == 0) break;
+    }
+  }
+  return idx;
+}
+
+// Persistent dataflow executor: CTAs take sub-tasks from a queue in topological priority order
+// (next_task), wait (bounded) until the sub-tasks they depend on are done, run them and publish
+// completion.
 template <typename E, bool kBwd>
 __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm) {
   extern __shared__ __align__(128) unsigned char smb[];
@@ -1855,9 +1947,12 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
     }
   }
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_idx = (ld_relaxed(prm.err) != 0) ? prm.ntasks : atomicAdd(prm.head, 1);
-      s_abort = 0;
+    if (warp == 0) {
+      const int nt = next_task(prm);
+      if (lane == 0) {
+        s_idx = nt;
+        s_abort = 0;
+      }
     }
     __syncthreads();
     const int idx = s_idx;
@@ -1874,7 +1969,7 @@ __global__ void __launch_bounds__(kThreads, 1) exec_kernel(const ExecParams prm)
           break;
         }
         const uint64_t t0 = gtime();
-        while (ld_acquire(prm.done + dep) == 0) {
+        while (ld_acquire(prm.done + dep) != 1) {
           if (ld_relaxed(prm.err) != 0) { bad = 3; break; }
           if (gtime() - t0 > prm.wait_ns) {
             if (atomicCAS(prm.err, 0, DERR_TIMEOUT) == 0) {

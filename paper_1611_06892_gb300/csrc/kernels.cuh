@@ -45,6 +45,11 @@ struct BwdParams {
   int pu_split;             // column pieces of a panel-block update adjoint (1 or 2)
 };
 
+// Executor look-ahead of one-matrix FP64 BiDiag reductions (queue entries scanned for a ready sub-task):
+// 8192^2 1374 -> 1336 ms, 4096^2 232 -> 224 ms against strict queue order; FP32 storage, R-BiDiag and
+// batches were not faster with it and keep strict order.
+constexpr int kWindowF64BiDiag = 512;
+
 struct ExecParams {
   const DevTask* tasks;
   const int32_t* deps;
@@ -68,6 +73,7 @@ struct ExecParams {
                         // 1 = updates by FP32 FFMA, 2 = three-TF32 updates on the warp-level MMA only
   int umma_cols;        // FP32 forward program: TMEM columns each CTA allocates for the tcgen05 phase (0: none)
   int f32_scalars64;    // FP32 tiles only: 1 = reflector beta / tau / scale in FP64 instead of float pairs
+  int window;           // queue entries from the head a CTA scans for a ready sub-task (0: strict queue order)
   BwdParams bwd;        // adjoint program only
 };
 

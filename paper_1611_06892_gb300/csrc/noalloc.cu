@@ -178,6 +178,7 @@ extern "C" int bidiag_band_noalloc(int64_t m, int64_t n, const double* d_A, int6
     const char* wl = std::getenv("BIDIAG_WAIT_LIMIT_NS");
     prm.wait_ns = wl ? std::strtoull(wl, nullptr, 10) : 20000000000ull;
     prm.esize = 8;
+    prm.window = tiles2 ? 0 : bd::kWindowF64BiDiag;
     if ((e = bd::exec_set_smem(smem, 8)) != cudaSuccess) return cuda_status(e);
     int per_sm = bd::exec_max_ctas_per_sm(smem, 8);
     if (per_sm < 1) per_sm = 1;

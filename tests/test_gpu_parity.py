@@ -162,6 +162,39 @@ def test_determinism(handle, torch_mod):
     assert torch_mod.equal(r1, r2)
 
 
+@pytest.mark.parametrize("m,n,nb,ib,tree,variant,dtype", [
+    (1536, 1536, 256, 32, "auto", "bidiag", "f64"),
+    (1536, 1536, 256, 32, "flatts", "bidiag", "f64"),
+    (1792, 1280, 256, 32, "greedy", "rbidiag", "f64"),
+    (700, 500, 32, 8, "auto", "bidiag", "f64"),
+    (1536, 1536, 256, 32, "auto", "bidiag", "f32"),
+])
+def test_window_does_not_change_results(torch_mod, m, n, nb, ib, tree, variant, dtype):
+    """The executor's look-ahead (out-of-order claims of ready sub-tasks) changes only timing: the
+    band is bitwise the same with strict queue order and with several windows."""
+    A = inputs.gaussian(m, n, seed=57)
+    dA = to_dev(torch_mod, A)
+    if dtype == "f32":
+        dA = dA.float().t().contiguous().t()
+    bands = {}
+    for window in (0, 32, 512, 1024):
+        h = G.Handle()
+        h.set_option(G.OPT_AUTO_RESOURCES, R_AUTO)
+        h.set_option(G.OPT_WINDOW, window)
+        res = h.band(dA, nb, ib, tree, variant)
+        h.sync()
+        bands[window] = res.band().cpu()
+        res.free()
+        h.close()
+    for window in (32, 512, 1024):
+        assert torch_mod.equal(bands[window], bands[0]), window
+    if dtype == "f64":
+        ref = OB.bidiag_band(A, nb, ib, TREES[tree], T.BIDIAG if variant == "bidiag" else T.RBIDIAG,
+                             resources=R_AUTO) if m * n <= 1 << 20 else None
+        if ref is not None:
+            assert np.abs(bands[0].numpy() - ref["ab"]).max() <= 1e-12 * np.linalg.norm(A)
+
+
 def test_host_entry_point(handle, torch_mod):
     """bidiag_band_host (host buffers, copies inside) gives the same band as the device entry point."""
     A = inputs.gaussian(160, 96, seed=41)
@@ -194,10 +227,13 @@ def test_argument_errors(handle, torch_mod):
                            ctypes.byref(r)) == G.ERR_UNSUPPORTED
 
 
-def test_wait_timeout_is_reported(handle, torch_mod):
+@pytest.mark.parametrize("window", [0, -1, 64])
+def test_wait_timeout_is_reported(handle, torch_mod, window):
     """Failure path without a GPU fault: a dependency on a flag nothing sets makes the bounded wait
-    run out; bidiag_sync reports BIDIAG_ERR_TIMEOUT and the handle keeps working."""
+    run out; bidiag_sync reports BIDIAG_ERR_TIMEOUT and the handle keeps working (strict queue order
+    and look-ahead scheduling)."""
     h = G.Handle()
+    h.set_option(G.OPT_WINDOW, window)
     h.set_option(G.OPT_WAIT_LIMIT_NS, 50_000_000)
     h.set_option(G.OPT_DEBUG_UNSET_DEP, 1)
     A = to_dev(torch_mod, inputs.gaussian(64, 48, seed=5))
