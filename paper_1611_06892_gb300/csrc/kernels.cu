@@ -1016,17 +1016,26 @@ __device__ __forceinline__ int core_idx(int row, int k, int kb) {
 __device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows, int kb, const float* Ct,
                                      const float* C, int ldc, int lc, int ncols, float* W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int mt_n = kb >> 4, nt_n = ncols >> 3;
-  for (int tile = warp; tile < mt_n * nt_n; tile += kWarps) {
+  const int mt_n = kb >> 4, nt_n = ncols >> 3, ntile = mt_n * nt_n;
+  // kb = 32 (mt_n = 2 divides kWarps): tiles warp and warp + 8 share their 16 reflectors, so their V
+  // fragments are read once per k-step; each tile keeps its own accumulation order
+  for (int tile = warp; tile < ntile; tile += 2 * kWarps) {
     const int m0 = (tile % mt_n) << 4, n0 = (tile / mt_n) << 3;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int tile2 = tile + kWarps;
+    const bool two = tile2 < ntile;
+    const int n1 = two ? (tile2 / mt_n) << 3 : n0;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f};
     if (Ct) {
       acc[0] = Ct[(m0 + g) * lc + n0 + 2 * t];
       acc[1] = Ct[(m0 + g) * lc + n0 + 2 * t + 1];
       acc[2] = Ct[(m0 + g + 8) * lc + n0 + 2 * t];
       acc[3] = Ct[(m0 + g + 8) * lc + n0 + 2 * t + 1];
+      acc2[0] = Ct[(m0 + g) * lc + n1 + 2 * t];
+      acc2[1] = Ct[(m0 + g) * lc + n1 + 2 * t + 1];
+      acc2[2] = Ct[(m0 + g + 8) * lc + n1 + 2 * t];
+      acc2[3] = Ct[(m0 + g + 8) * lc + n1 + 2 * t + 1];
     }
-#pragma unroll 4
+#pragma unroll 2
     for (int k0 = 0; k0 < vrows; k0 += 8) {
       const int i00 = core_idx(k0 + t, m0 + g, kb), i01 = core_idx(k0 + t, m0 + g + 8, kb);
       const int i10 = core_idx(k0 + t + 4, m0 + g, kb), i11 = core_idx(k0 + t + 4, m0 + g + 8, kb);
@@ -1036,11 +1045,21 @@ __device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows
                               __float_as_uint(Vl[i11])};
       const float b[2] = {C[(k0 + t) + (n0 + g) * ldc], C[(k0 + t + 4) + (n0 + g) * ldc]};
       mma_3xtf32(acc, ah, al, b);
+      if (two) {
+        const float b2[2] = {C[(k0 + t) + (n1 + g) * ldc], C[(k0 + t + 4) + (n1 + g) * ldc]};
+        mma_3xtf32(acc2, ah, al, b2);
+      }
     }
     W[(m0 + g) * lc + n0 + 2 * t] = acc[0];
     W[(m0 + g) * lc + n0 + 2 * t + 1] = acc[1];
     W[(m0 + g + 8) * lc + n0 + 2 * t] = acc[2];
     W[(m0 + g + 8) * lc + n0 + 2 * t + 1] = acc[3];
+    if (two) {
+      W[(m0 + g) * lc + n1 + 2 * t] = acc2[0];
+      W[(m0 + g) * lc + n1 + 2 * t + 1] = acc2[1];
+      W[(m0 + g + 8) * lc + n1 + 2 * t] = acc2[2];
+      W[(m0 + g + 8) * lc + n1 + 2 * t + 1] = acc2[3];
+    }
   }
 }
 
@@ -1273,15 +1292,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Starts the copy of V block (oriented X(r0 + r, c0 + a), r < vrows, a < kb) into the staging buffer Vr in
 // 16-byte pieces (one commit group): column-major (ld nb) for tr = 0, row-major (ld kb + 4) for tr = 1.
 __device__ void prefetch_v(float* Vr, const float* X, int nb, int tr, int r0, int c0, int vrows, int kb) {
-  const int nch = (vrows * kb) >> 2;
-  for (int q = threadIdx.x; q < nch; q += kThreads) {
-    if (!tr) {
-      const int rq = vrows >> 2, a = q / rq, r = (q % rq) << 2;
-      cp_async16(Vr + a * nb + r, X + (r0 + r) + (size_t)(c0 + a) * nb);
-    } else {
-      const int aq = kb >> 2, r = q / aq, a = (q % aq) << 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!tr) {   // warp per column, lanes along the rows (kb = 32: 4 columns per warp)
+    for (int a = warp; a < kb; a += kWarps)
+      for (int r = lane << 2; r < vrows; r += 128) cp_async16(Vr + a * nb + r, X + (r0 + r) + (size_t)(c0 + a) * nb);
+  } else {     // 8 threads per row of kb = 32 columns
+    const int a = (threadIdx.x & 7) << 2;
+    for (int r = threadIdx.x >> 3; r < vrows; r += kThreads >> 3)
       cp_async16(Vr + r * (kb + 4) + a, X + (size_t)(r0 + r) * nb + c0 + a);
-    }
   }
 }
 
@@ -1292,13 +1310,14 @@ __device__ void prefetch_t_ct(float* Tr, const float* T, float* Cr, const float*
                               int kb, int ncols, int lc) {
   for (int q = threadIdx.x; q < (kb * kb) >> 2; q += kThreads) cp_async16(Tr + 4 * q, T + 4 * q);
   if (!Cp) return;
-  const int nch = (kb * ncols) >> 2;
+  const int nch = (kb * ncols) >> 2;            // kb = 32, ncols 32 or 64
+  const int lq = ncols == 64 ? 4 : 3;           // log2(ncols / 4)
   for (int q = threadIdx.x; q < nch; q += kThreads) {
     if (!tr) {
-      const int rq = kb >> 2, c = q / rq, r = (q % rq) << 2;
+      const int c = q >> 3, r = (q & 7) << 2;
       cp_async16(Cr + c * (kb + 4) + r, Cp + (c0 + r) + (size_t)(col0 + c) * nb);
     } else {
-      const int cq = ncols >> 2, r = q / cq, c = (q % cq) << 2;
+      const int r = q >> lq, c = (q & ((1 << lq) - 1)) << 2;
       cp_async16(Cr + r * lc + c, Cp + (size_t)(c0 + r) * nb + col0 + c);
     }
   }
@@ -1307,18 +1326,13 @@ __device__ void prefetch_t_ct(float* Tr, const float* T, float* Cr, const float*
 // Starts the copy of the C strip (oriented C(r, col0 + c), r0 <= r < r1, c < ncols) into Cs column-major
 // (ld ldc): 16-byte pieces along r for tr = 0, 4-byte pieces (coalesced along c) for tr = 1.
 __device__ void prefetch_c(float* Cs, int ldc, const float* C, int nb, int tr, int r0, int r1, int col0, int ncols) {
-  const int rows = r1 - r0;
-  if (!tr) {
-    const int rq = rows >> 2;
-    for (int q = threadIdx.x; q < rq * ncols; q += kThreads) {
-      const int c = q / rq, r = r0 + ((q % rq) << 2);
-      cp_async16(Cs + c * ldc + r, C + r + (size_t)(col0 + c) * nb);
-    }
-  } else {
-    for (int q = threadIdx.x; q < rows * ncols; q += kThreads) {
-      const int c = q % ncols, r = r0 + q / ncols;
-      cp_async4(Cs + c * ldc + r, C + (size_t)r * nb + col0 + c);
-    }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!tr) {   // warp per column, lanes along the rows
+    for (int c = warp; c < ncols; c += kWarps)
+      for (int r = r0 + (lane << 2); r < r1; r += 128) cp_async16(Cs + c * ldc + r, C + r + (size_t)(col0 + c) * nb);
+  } else {     // warp per row, lanes along the columns
+    for (int r = r0 + warp; r < r1; r += kWarps)
+      for (int c = lane; c < ncols; c += 32) cp_async4(Cs + c * ldc + r, C + (size_t)r * nb + col0 + c);
   }
 }
 
@@ -1327,9 +1341,9 @@ __device__ void prefetch_c(float* Cs, int ldc, const float* C, int nb, int tr, i
 // 16-byte core row per part.
 __device__ void split_v_core(const float* Vr, float* Vl, float* Vh, int nb, int tr, int r0, int c0, int vrows,
                              int kb, int mask) {
-  const int nq = kb >> 2;
-  for (int u = threadIdx.x; u < vrows * nq; u += kThreads) {
-    const int r = u % vrows, a0 = (u / vrows) << 2;
+  // kb = 32: warp w takes columns a0 = 4 w .. 4 w + 3, lanes along the rows
+  const int a0 = (threadIdx.x >> 5) << 2;
+  for (int r = threadIdx.x & 31; r < vrows; r += 32) {
     float x[4];
     if (tr) {
       const float4 v = *reinterpret_cast<const float4*>(Vr + r * (kb + 4) + a0);
@@ -1391,13 +1405,13 @@ __device__ bool task_update_umma(unsigned char* smb, int type, const float* X, f
     __syncthreads();                       // this block's V, T, Ct (and the C strip) are staged
     split_v_core(Vr, Vl, Vh, nb, tr, r0_of(c0), c0, vrows, kb,
                  type == UNMQR ? M_UNITLOWER : (type == TSMQR ? M_NONE : M_UPPER));
-    for (int o = threadIdx.x; o < kb * kb; o += kThreads) {   // op(T) column-major, ld kb + 4
-      const int r = o % kb, c = o / kb;
+    for (int o = threadIdx.x; o < kb * kb; o += kThreads) {   // op(T) column-major, ld kb + 4 (kb = 32)
+      const int r = o & 31, c = o >> 5;
       Tb[notrans ? r + c * (kb + 4) : c + r * (kb + 4)] = Tr[o];
     }
     if (top) {
       for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
-        const int r = o % kb, c = o / kb;
+        const int r = o & 31, c = o >> 5;
         Ct[r * lc + c] = tr ? Cr[r * lc + c] : Cr[c * (kb + 4) + r];
       }
     }
