@@ -85,7 +85,12 @@ enum {
                                      one-matrix FP64 BiDiag reduction, else 0 (measured on 8192^2 and
                                      4096^2: 2.8 / 3.2 % faster; FP32 storage, R-BiDiag and batches are
                                      not faster).  Results do not depend on it: the program orders every
-                                     access to shared data, the window only changes timing */
+                                     access to shared data, the window only changes timing */,
+  BIDIAG_OPT_PRIORITY = 10        /* queue order of the device program, by bottom level (longest weighted
+                                     path to the end) with sub-task weights 1 = Table 1 flops times the
+                                     measured time per flop of each sub-task kind (default), 0 = flops
+                                     alone (FP32-storage panel factors twice).  Results do not depend on
+                                     it */
 };
 
 /* Task type codes of the canonical task list (GELQT etc. are the same codes in LQ phases). */

@@ -33,6 +33,7 @@ OPT_WAIT_LIMIT_NS, OPT_AUTO_RESOURCES, OPT_DEBUG_UNSET_DEP, OPT_STRIP, OPT_TIMIN
 OPT_F32_UPDATES = 7
 OPT_F32_SCALARS = 8
 OPT_WINDOW = 9
+OPT_PRIORITY = 10
 
 _lib = None
 

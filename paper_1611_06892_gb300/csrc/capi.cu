@@ -52,7 +52,7 @@ struct BwdDev {
   }
 };
 
-using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int, int>;   // ..., strip width, esize
+using PlanKey = std::tuple<int64_t, int64_t, int, int, int, int, int64_t, int, int, int>;   // ..., strip width, esize, priority weights
 
 // Everything about a batch that depends only on its shapes and options: per-matrix configurations and
 // plans, the storage layout and the merged device program (cached on the handle, reused by later calls
@@ -109,6 +109,7 @@ struct bidiag_ctx {
   int f32_simt = 0;                // FP32 storage: updates by FFMA instead of 3xTF32 tensor-core products
   int f32_scalars64 = 0;           // FP32 storage: reflector scalars in FP64 instead of float pairs
   int window = -1;                 // executor look-ahead (queue entries scanned); -1: by precision and variant
+  int prio = 1;                    // priority weights of the device program: 1 calibrated per kind, 0 flops
   int64_t* d_trace = nullptr;      // per-task trace of the last traced reduction
   std::map<std::tuple<int, int, int, int64_t>, int> splits;   // best three-step split per (p, q, tree, R)
   std::map<std::vector<int64_t>, std::shared_ptr<BatchPlan>> batches;   // batch programs by shapes / options
@@ -275,7 +276,7 @@ int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, in
              std::shared_ptr<PlanDev>* out) {
   const int64_t R = resources_of(h, nb, w, esize);
   const bool debug = h->debug_unset != 0;
-  PlanKey key{m, n, nb, ib, tree, variant, R, w, esize};
+  PlanKey key{m, n, nb, ib, tree, variant, R, w, esize, h->prio};
   if (!debug) {
     auto it = h->cache.find(key);
     if (it != h->cache.end()) {
@@ -285,7 +286,7 @@ int get_plan(bidiag_handle h, int64_t m, int64_t n, int nb, int ib, int tree, in
   }
   auto pd = std::make_shared<PlanDev>();
   try {
-    bd::build_plan(pd->plan, m, n, nb, ib, tree, variant, R, w, esize);
+    bd::build_plan(pd->plan, m, n, nb, ib, tree, variant, R, w, esize, h->prio);
   } catch (const std::bad_alloc&) {
     return fail(h, BIDIAG_ERR_NOMEM, "host allocation failed while planning");
   } catch (const std::exception& e) {
@@ -703,6 +704,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
   key.push_back(esize);
   key.push_back(h->strip_w);
   key.push_back(h->auto_res);
+  key.push_back(h->prio);
   key.push_back(count);
   for (int64_t b = 0; b < count; ++b) {
     key.push_back(m[b]);
@@ -757,7 +759,7 @@ int band_batched_impl(bidiag_handle h, int64_t count, const int64_t* m, const in
           const int64_t R = resources_of(h, o.nb, o.w, esize);
           if (o.variant == BIDIAG_AUTO_VARIANT) o.variant = bd::choose_variant(p, q, o.tree, R, nullptr, nullptr);
           o.pd = std::make_shared<PlanDev>();
-          bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w, esize);
+          bd::build_plan(o.pd->plan, m[b], n[b], o.nb, o.ib, o.tree, o.variant, R, o.w, esize, h->prio);
           dump_tasks(o.pd->plan.tasks, o.pd->dump);
         } catch (const std::bad_alloc&) {
           bad[(size_t)b] = BIDIAG_ERR_NOMEM;
@@ -966,6 +968,10 @@ int bidiag_set_option(bidiag_handle h, int option, int64_t value) {
     case BIDIAG_OPT_WINDOW:
       if (value < -1 || value > 1024) return -3;
       h->window = (int)value;
+      return BIDIAG_OK;
+    case BIDIAG_OPT_PRIORITY:
+      if (value != 0 && value != 1) return -3;
+      h->prio = (int)value;
       return BIDIAG_OK;
     default:
       return -2;

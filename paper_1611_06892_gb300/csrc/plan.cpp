@@ -507,8 +507,20 @@ inline int32_t make_op(int type, bool tr, bool notrans, int strip, int blk, int 
 
 }  // namespace
 
+// Priority weight of a sub-task: its Table 1 flops times the time per flop of its kind relative to a
+// TSMQR strip, in percent (mode 1), measured from per-sub-task traces of the executor on a GB300 (nb 256,
+// ib 32; FP32 storage at 8192^2 with the tcgen05 updates, FP64 at 4096^2).  Mode 0 is the flop count
+// alone, with FP32-storage panel factors counted twice.
+enum WeightClass { W_PF_GE, W_PF_TS, W_PF_TT, W_PU_GE, W_PU_TS, W_PU_TT, W_UNMQR, W_TSMQR, W_TTMQR };
+static int64_t prio_weight(int64_t flops, int cls, int esize, int mode) {
+  static const int64_t kF32[9] = {640, 400, 650, 125, 115, 210, 135, 100, 150};
+  static const int64_t kF64[9] = {71, 51, 74, 71, 70, 79, 117, 100, 119};
+  if (mode == 0) return (cls <= W_PF_TT && esize == 4 ? 2 : 1) * flops;
+  return std::max<int64_t>(1, flops * (esize == 4 ? kF32[cls] : kF64[cls]) / 100);
+}
+
 void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t R, int strip_w,
-                int esize) {
+                int esize, int prio) {
   pl.m = m;
   pl.n = n;
   pl.nb = nb;
@@ -599,10 +611,7 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
         wr.push_back(it.t(slot, b));
         const int64_t rows = kind == PK_GE ? nb - (int64_t)b * ib : (kind == PK_TS ? nb : (int64_t)(b + 1) * ib);
         d.op = make_op(PF, lq, false, 0, b, kind);
-        // priority weights: Table 1 flops, scaled by the measured time per flop of each sub-task kind
-        // relative to the update strips (per-sub-task traces at 8192^2 on a GB300: with FP32 storage
-        // the panel chain is relatively twice as slow; panel-block updates 1.5x in both precisions)
-        last = g.add(d, (esize == 4 ? 2 : 1) * 12 * ib2 * rows, rd, wr, -1);
+        last = g.add(d, prio_weight(12 * ib2 * rows, W_PF_GE + kind, esize, prio), rd, wr, -1);
         // PU(b, s)
         for (int s = b + 1; s < nblk; ++s) {
           rd.clear();
@@ -623,7 +632,7 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
           }
           rd.push_back(it.t(slot, b));
           d.op = make_op(PU, lq, false, s, b, kind);
-          last = g.add(d, 6 * ib2 * rows, rd, wr, -1);
+          last = g.add(d, prio_weight(6 * ib2 * rows, W_PU_GE + kind, esize, prio), rd, wr, -1);
         }
       }
       panel_last[x] = last;
@@ -648,7 +657,8 @@ void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int va
           }
         }
         d.op = make_op(t.type, lq, false, s, 0, 0);
-        g.add(d, per_strip, rd, wr, panel_last[owner]);
+        g.add(d, prio_weight(per_strip, t.type == UNMQR ? W_UNMQR : (t.type == TSMQR ? W_TSMQR : W_TTMQR), esize, prio),
+              rd, wr, panel_last[owner]);
       }
     } else {   // COPY(i, j): R part of A's tile (i, j) into the second phase's tile (i, j)
       DevTask d{};

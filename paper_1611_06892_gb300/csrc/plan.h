@@ -114,9 +114,10 @@ int choose_variant(int p, int q, int tree, int64_t resources, int64_t* cp_bidiag
 // the smallest s); returns s and, if cp is not null, its critical path.
 int best_split(int p, int q, int tree, int64_t resources, int64_t* cp);
 // Full plan for a reduction: tasks, DAG, device sub-tasks ordered by critical-path priority.  esize
-// (8: FP64, 4: FP32 storage) only sets the priority weights.
+// (8: FP64, 4: FP32 storage) and prio (1: calibrated per-kind times, 0: flop counts) only set the
+// priority weights.
 void build_plan(Plan& pl, int64_t m, int64_t n, int nb, int ib, int tree, int variant, int64_t resources,
-                int strip_w, int esize = 8);
+                int strip_w, int esize = 8, int prio = 1);
 
 // Several independent plans as one device program: the queues are merged by decreasing bottom level
 // (each plan's own order is kept, so the result is topological), matrix b's sub-tasks carry b in
