@@ -1018,31 +1018,33 @@ __device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int mt_n = kb >> 4, nt_n = ncols >> 3, ntile = mt_n * nt_n;
   // kb = 32 (mt_n = 2 divides kWarps): tiles warp and warp + 8 share their 16 reflectors, so their V
-  // fragments are read once per k-step; each tile keeps its own accumulation order
+  // fragments are read once per k-step; each tile keeps its own accumulation order.  Fragment rows g and
+  // g + 8 stand for reflectors m0 + 2 g and m0 + 2 g + 1, adjacent in the core-matrix layout, so that each
+  // pair of A registers is one 8-byte load (the row order of an MMA does not change its sums).
   for (int tile = warp; tile < ntile; tile += 2 * kWarps) {
     const int m0 = (tile % mt_n) << 4, n0 = (tile / mt_n) << 3;
     const int tile2 = tile + kWarps;
     const bool two = tile2 < ntile;
     const int n1 = two ? (tile2 / mt_n) << 3 : n0;
+    const int ra = m0 + 2 * g, rb = ra + 1;   // reflectors of fragment rows g and g + 8
     float acc[4] = {0.f, 0.f, 0.f, 0.f}, acc2[4] = {0.f, 0.f, 0.f, 0.f};
     if (Ct) {
-      acc[0] = Ct[(m0 + g) * lc + n0 + 2 * t];
-      acc[1] = Ct[(m0 + g) * lc + n0 + 2 * t + 1];
-      acc[2] = Ct[(m0 + g + 8) * lc + n0 + 2 * t];
-      acc[3] = Ct[(m0 + g + 8) * lc + n0 + 2 * t + 1];
-      acc2[0] = Ct[(m0 + g) * lc + n1 + 2 * t];
-      acc2[1] = Ct[(m0 + g) * lc + n1 + 2 * t + 1];
-      acc2[2] = Ct[(m0 + g + 8) * lc + n1 + 2 * t];
-      acc2[3] = Ct[(m0 + g + 8) * lc + n1 + 2 * t + 1];
+      acc[0] = Ct[ra * lc + n0 + 2 * t];
+      acc[1] = Ct[ra * lc + n0 + 2 * t + 1];
+      acc[2] = Ct[rb * lc + n0 + 2 * t];
+      acc[3] = Ct[rb * lc + n0 + 2 * t + 1];
+      acc2[0] = Ct[ra * lc + n1 + 2 * t];
+      acc2[1] = Ct[ra * lc + n1 + 2 * t + 1];
+      acc2[2] = Ct[rb * lc + n1 + 2 * t];
+      acc2[3] = Ct[rb * lc + n1 + 2 * t + 1];
     }
 #pragma unroll 2
     for (int k0 = 0; k0 < vrows; k0 += 8) {
-      const int i00 = core_idx(k0 + t, m0 + g, kb), i01 = core_idx(k0 + t, m0 + g + 8, kb);
-      const int i10 = core_idx(k0 + t + 4, m0 + g, kb), i11 = core_idx(k0 + t + 4, m0 + g + 8, kb);
-      const uint32_t ah[4] = {__float_as_uint(Vh[i00]), __float_as_uint(Vh[i01]), __float_as_uint(Vh[i10]),
-                              __float_as_uint(Vh[i11])};
-      const uint32_t al[4] = {__float_as_uint(Vl[i00]), __float_as_uint(Vl[i01]), __float_as_uint(Vl[i10]),
-                              __float_as_uint(Vl[i11])};
+      const int i0 = core_idx(k0 + t, ra, kb), i1 = core_idx(k0 + t + 4, ra, kb);
+      const uint2 h0 = *reinterpret_cast<const uint2*>(Vh + i0), h1 = *reinterpret_cast<const uint2*>(Vh + i1);
+      const uint2 l0 = *reinterpret_cast<const uint2*>(Vl + i0), l1 = *reinterpret_cast<const uint2*>(Vl + i1);
+      const uint32_t ah[4] = {h0.x, h0.y, h1.x, h1.y};
+      const uint32_t al[4] = {l0.x, l0.y, l1.x, l1.y};
       const float b[2] = {C[(k0 + t) + (n0 + g) * ldc], C[(k0 + t + 4) + (n0 + g) * ldc]};
       mma_3xtf32(acc, ah, al, b);
       if (two) {
@@ -1050,15 +1052,15 @@ __device__ void apply_phase1_tc_core(const float* Vh, const float* Vl, int vrows
         mma_3xtf32(acc2, ah, al, b2);
       }
     }
-    W[(m0 + g) * lc + n0 + 2 * t] = acc[0];
-    W[(m0 + g) * lc + n0 + 2 * t + 1] = acc[1];
-    W[(m0 + g + 8) * lc + n0 + 2 * t] = acc[2];
-    W[(m0 + g + 8) * lc + n0 + 2 * t + 1] = acc[3];
+    W[ra * lc + n0 + 2 * t] = acc[0];
+    W[ra * lc + n0 + 2 * t + 1] = acc[1];
+    W[rb * lc + n0 + 2 * t] = acc[2];
+    W[rb * lc + n0 + 2 * t + 1] = acc[3];
     if (two) {
-      W[(m0 + g) * lc + n1 + 2 * t] = acc2[0];
-      W[(m0 + g) * lc + n1 + 2 * t + 1] = acc2[1];
-      W[(m0 + g + 8) * lc + n1 + 2 * t] = acc2[2];
-      W[(m0 + g + 8) * lc + n1 + 2 * t + 1] = acc2[3];
+      W[ra * lc + n1 + 2 * t] = acc2[0];
+      W[ra * lc + n1 + 2 * t + 1] = acc2[1];
+      W[rb * lc + n1 + 2 * t] = acc2[2];
+      W[rb * lc + n1 + 2 * t + 1] = acc2[3];
     }
   }
 }
