@@ -56,8 +56,8 @@ WORKLOADS = {
 # DFMA-loop rate (bidiag_measure_fp64_peaks), the FP64 unit the reduction's contractions run on.
 FP64_DERIVED_GFLOPS = 152 * 4 * 2.070
 # DRAM bytes (read + write) of one executor launch on the 8192^2 Auto workload, from the ncu capture
-# summarised under profiles/ (None until the current kernel has been captured).
-EXEC_TRAFFIC_BYTES = None
+# summarised under profiles/exec_kernel_square8192_launches.md (set to None when the kernel changes).
+EXEC_TRAFFIC_BYTES = 11630062080 + 11609937920
 CPU_SAMPLE_SECONDS = 12.0
 
 
