@@ -479,6 +479,7 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
           };
           if (refl) {
             float sum = 0.0f;
+#pragma unroll 4
             for (int r = t0 + lane; r < t1; r += 32) sum += P[r + jj * lp] * P[r + c * lp];
             sum = warp_sum(sum);
             float* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
@@ -486,6 +487,7 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
             __syncwarp();
             if (lane == 0) *top = *top - (float)tauE * wv;
             const float tw = (float)tauE * wv * (float)se;
+#pragma unroll 4
             for (int r = t0 + lane; r < t1; r += 32) {
               const float x = P[r + c * lp] - P[r + jj * lp] * tw;
               P[r + c * lp] = x;
@@ -539,7 +541,7 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
         __syncwarp();
         if (lane == 0 && !pairs) scalars(c, part);
       }
-    } else if (refl) {
+    } else if (refl && sizeof(E) == 8) {   // FP64: one column per pass (the FP64 pipe is the limit)
       const E taue = tauE;
       for (int c = jj + 2 + (warp - 1); c < kb; c += kWarps - 1) {
         E sum = E(0);
@@ -551,6 +553,42 @@ __device__ void factor_panel(int mode, E* P, int lp, int rows, int kb, E* Rt, in
         if (lane == 0) *top = *top - taue * wv;
         const E tw = taue * wv * se;
         for (int r = t0 + lane; r < t1; r += 32) P[r + c * lp] -= P[r + jj * lp] * tw;
+      }
+    } else if (refl) {
+      // FP32: two columns c and c + 7 per pass (independent, so their reductions overlap; a lone last
+      // column is reduced twice); each column's arithmetic is the single-column form's
+      const E taue = tauE;
+      for (int c = jj + 2 + (warp - 1); c < kb; c += 2 * (kWarps - 1)) {
+        const int c2 = c + (kWarps - 1);
+        const bool two = c2 < kb;
+        const int cb = two ? c2 : c;
+        E sum = E(0), sum2 = E(0);
+#pragma unroll 4
+        for (int r = t0 + lane; r < t1; r += 32) {
+          const E v = P[r + jj * lp];
+          sum += v * P[r + c * lp];
+          sum2 += v * P[r + cb * lp];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          sum += __shfl_xor_sync(kFull, sum, o);
+          sum2 += __shfl_xor_sync(kFull, sum2, o);
+        }
+        E* top = (mode == PM_GE) ? &P[jj + c * lp] : &Rt[jj + c * lrt];
+        E* top2 = (mode == PM_GE) ? &P[jj + cb * lp] : &Rt[jj + cb * lrt];
+        const E wv = *top + se * sum, wv2 = *top2 + se * sum2;
+        __syncwarp();
+        if (lane == 0) {
+          *top = *top - taue * wv;
+          if (two) *top2 = *top2 - taue * wv2;
+        }
+        const E tw = taue * wv * se, tw2 = taue * wv2 * se;
+#pragma unroll 4
+        for (int r = t0 + lane; r < t1; r += 32) {
+          const E v = P[r + jj * lp];
+          P[r + c * lp] -= v * tw;
+          if (two) P[r + c2 * lp] -= v * tw2;
+        }
       }
     }
     __syncthreads();
