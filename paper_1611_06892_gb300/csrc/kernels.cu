@@ -758,9 +758,14 @@ __device__ __forceinline__ void mma_3xtf32(float* acc, const uint32_t* ah, const
 // FP64: register-blocked DFMA (phase 1: 1 column x 4 reflectors per thread, phase 3: 1 row x 8
 // columns).  FP32: phases 1 and 3 on the tensor cores (three TF32 products) when kb and vrows are
 // multiples of 16 and ncols of 8, register-blocked FFMA otherwise.
+// Zero structure of an update block's V (oriented rows 0 .. vrows - 1, reflectors 0 .. kb - 1): none, unit
+// lower triangle on top (GEQRT reflectors: V(r, a) = 0 for r < a), or upper triangle at the bottom (TTQRT
+// reflectors: V(r, a) = 0 for r > vrows - kb + a).  The FP64 / FFMA phases skip those zeros.
+enum TriShape : int { TRI_NONE = 0, TRI_UNITLOWER = 1, TRI_UPPER = 2 };
+
 template <typename E>
 __device__ void apply_phase1_simt(const E* V, int lv, int vrows, int kb, const E* Ct, const E* C, int lc, int ncols,
-                                  E* W) {
+                                  E* W, int tri = TRI_NONE) {
   using V2 = typename Vec2<E>::type;
   if ((kb & 3) == 0) {
     const int nunits = ncols * (kb >> 2);
@@ -772,8 +777,11 @@ __device__ void apply_phase1_simt(const E* V, int lv, int vrows, int kb, const E
       }
       const E* vp = V + a0;
       const E* cp = C + c;
+      // rows where reflectors a0 .. a0 + 3 are all zero are skipped (their terms are exact zeros)
+      const int rb = tri == TRI_UNITLOWER ? a0 : 0;
+      const int re = tri == TRI_UPPER ? vrows - kb + a0 + 4 : vrows;
 #pragma unroll 4
-      for (int r = 0; r < vrows; ++r) {
+      for (int r = rb; r < re; ++r) {
         const V2 v01 = *reinterpret_cast<const V2*>(vp + r * lv);
         const V2 v23 = *reinterpret_cast<const V2*>(vp + r * lv + 2);
         const E x = cp[r * lc];
@@ -798,7 +806,8 @@ __device__ void apply_phase1_simt(const E* V, int lv, int vrows, int kb, const E
 }
 
 template <typename E>
-__device__ void apply_phase3_simt(const E* V, int lv, int vrows, int kb, E* C, int lc, int ncols, const E* W2) {
+__device__ void apply_phase3_simt(const E* V, int lv, int vrows, int kb, E* C, int lc, int ncols, const E* W2,
+                                  int tri = TRI_NONE) {
   using V2 = typename Vec2<E>::type;
   if ((ncols & 7) == 0 && (kb & 1) == 0) {
     const int nunits = vrows * (ncols >> 3);
@@ -807,8 +816,11 @@ __device__ void apply_phase3_simt(const E* V, int lv, int vrows, int kb, E* C, i
       V2* cp = reinterpret_cast<V2*>(C + r * lc + c0);
       V2 a0 = cp[0], a1 = cp[1], a2 = cp[2], a3 = cp[3];
       const E* vp = V + r * lv;
+      // pairs of reflectors whose entries in row r are both zero are skipped
+      const int ab = tri == TRI_UPPER ? max(0, r - (vrows - kb)) & ~1 : 0;
+      const int ae = tri == TRI_UNITLOWER ? min(kb, (r + 2) & ~1) : kb;
 #pragma unroll 2
-      for (int a = 0; a < kb; a += 2) {
+      for (int a = ab; a < ae; a += 2) {
         const V2 v = *reinterpret_cast<const V2*>(vp + a);
         const V2* w0 = reinterpret_cast<const V2*>(W2 + a * lc + c0);
         const V2* w1 = reinterpret_cast<const V2*>(W2 + (a + 1) * lc + c0);
@@ -921,15 +933,15 @@ __device__ __forceinline__ bool use_tc(bool simt, int kb, int vrows, int ncols) 
 // Vh = high parts; otherwise V holds the values and the phases run on the FMA units.
 template <typename E>
 __device__ void apply_rm(const E* V, const E* Vh, int lv, int vrows, int kb, const E* Tb, bool notrans, E* Ct, E* C,
-                         int lc, int ncols, E* W, E* W2) {
+                         int lc, int ncols, E* W, E* W2, int tri = TRI_NONE) {
   constexpr bool kF32 = sizeof(E) == 4;
   const bool tc = kF32 && Vh != nullptr;
   // phase 1
   if constexpr (kF32) {
     if (tc) apply_phase1_tc(Vh, V, lv, vrows, kb, Ct, C, lc, ncols, W);
-    else apply_phase1_simt(V, lv, vrows, kb, Ct, C, lc, ncols, W);
+    else apply_phase1_simt(V, lv, vrows, kb, Ct, C, lc, ncols, W, tri);
   } else {
-    apply_phase1_simt(V, lv, vrows, kb, Ct, C, lc, ncols, W);
+    apply_phase1_simt(V, lv, vrows, kb, Ct, C, lc, ncols, W, tri);
   }
   __syncthreads();
   // phase 2: W2 = op(T) W, then Ct -= W2.  For kb = 32 and ncols = 32 each thread takes the rows
@@ -966,9 +978,9 @@ __device__ void apply_rm(const E* V, const E* Vh, int lv, int vrows, int kb, con
   // phase 3: C -= V W2
   if constexpr (kF32) {
     if (tc) apply_phase3_tc(Vh, V, lv, vrows, kb, C, lc, ncols, W2);
-    else apply_phase3_simt(V, lv, vrows, kb, C, lc, ncols, W2);
+    else apply_phase3_simt(V, lv, vrows, kb, C, lc, ncols, W2, tri);
   } else {
-    apply_phase3_simt(V, lv, vrows, kb, C, lc, ncols, W2);
+    apply_phase3_simt(V, lv, vrows, kb, C, lc, ncols, W2, tri);
   }
   __syncthreads();
 }
@@ -1283,7 +1295,8 @@ __device__ void task_update(unsigned char* smb, int type, const E* X, E* Cp, E* 
     }
     for (int o = threadIdx.x + 4 * kThreads; o < kb * kb; o += kThreads) Tb[o] = ldg(Tg + (size_t)c0 * ib + o);
     __syncthreads();
-    apply_rm(V, Vh, L.lv, vrows, kb, Tb, notrans, Ctop, Cb, L.lc, ncols, W, W2);
+    apply_rm(V, Vh, L.lv, vrows, kb, Tb, notrans, Ctop, Cb, L.lc, ncols, W, W2,
+             type == UNMQR ? TRI_UNITLOWER : (type == TTMQR ? TRI_UPPER : TRI_NONE));
     if (Ctop) {
       store_tile(Ct, L.lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
       __syncthreads();
