@@ -81,9 +81,9 @@ enum {
   BIDIAG_OPT_WINDOW = 9           /* executor look-ahead, -1..1024: a CTA looking for work scans this many
                                      queue entries from the head and takes the first whose dependencies
                                      are done; only when none is ready does it take the head's entry and
-                                     wait for it.  0 = strict queue order; -1 (default) = 512 for a
+                                     wait for it.  0 = strict queue order; -1 (default) = 1024 for a
                                      one-matrix FP64 BiDiag reduction, else 0 (measured on 8192^2 and
-                                     4096^2: 2.8 / 3.2 % faster; FP32 storage, R-BiDiag and batches are
+                                     4096^2: 3.2 / 4.1 % faster; FP32 storage, R-BiDiag and batches are
                                      not faster).  Results do not depend on it: the program orders every
                                      access to shared data, the window only changes timing */,
   BIDIAG_OPT_PRIORITY = 10        /* queue order of the device program, by bottom level (longest weighted

@@ -46,9 +46,9 @@ struct BwdParams {
 };
 
 // Executor look-ahead of one-matrix FP64 BiDiag reductions (queue entries scanned for a ready sub-task):
-// 8192^2 1374 -> 1336 ms, 4096^2 232 -> 224 ms against strict queue order; FP32 storage, R-BiDiag and
+// 8192^2 1374 -> 1330 ms, 4096^2 232 -> 222 ms against strict queue order; FP32 storage, R-BiDiag and
 // batches were not faster with it and keep strict order.
-constexpr int kWindowF64BiDiag = 512;
+constexpr int kWindowF64BiDiag = 1024;
 
 struct ExecParams {
   const DevTask* tasks;

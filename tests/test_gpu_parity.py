@@ -170,24 +170,28 @@ def test_determinism(handle, torch_mod):
     (1536, 1536, 256, 32, "auto", "bidiag", "f32"),
 ])
 def test_window_does_not_change_results(torch_mod, m, n, nb, ib, tree, variant, dtype):
-    """The executor's look-ahead (out-of-order claims of ready sub-tasks) changes only timing: the
-    band is bitwise the same with strict queue order and with several windows."""
+    """The executor's look-ahead (out-of-order claims of ready sub-tasks) and the priority weights of
+    the queue order change only timing: the band is bitwise the same with strict queue order, several
+    windows and both weightings."""
     A = inputs.gaussian(m, n, seed=57)
     dA = to_dev(torch_mod, A)
     if dtype == "f32":
         dA = dA.float().t().contiguous().t()
     bands = {}
-    for window in (0, 32, 512, 1024):
+    settings = [(0, 1), (32, 1), (512, 1), (1024, 1), (0, 0), (512, 0)]
+    for window, prio in settings:
         h = G.Handle()
         h.set_option(G.OPT_AUTO_RESOURCES, R_AUTO)
         h.set_option(G.OPT_WINDOW, window)
+        h.set_option(G.OPT_PRIORITY, prio)
         res = h.band(dA, nb, ib, tree, variant)
         h.sync()
-        bands[window] = res.band().cpu()
+        bands[(window, prio)] = res.band().cpu()
         res.free()
         h.close()
-    for window in (32, 512, 1024):
-        assert torch_mod.equal(bands[window], bands[0]), window
+    for key in settings[1:]:
+        assert torch_mod.equal(bands[key], bands[(0, 1)]), key
+    bands[0] = bands[(0, 1)]
     if dtype == "f64":
         ref = OB.bidiag_band(A, nb, ib, TREES[tree], T.BIDIAG if variant == "bidiag" else T.RBIDIAG,
                              resources=R_AUTO) if m * n <= 1 << 20 else None
