@@ -57,7 +57,7 @@ WORKLOADS = {
 FP64_DERIVED_GFLOPS = 152 * 4 * 2.070
 # DRAM bytes (read + write) of one executor launch on the 8192^2 Auto workload, from the ncu capture
 # summarised under profiles/exec_kernel_square8192_launches.md (set to None when the kernel changes).
-EXEC_TRAFFIC_BYTES = 11630062080 + 11609937920
+EXEC_TRAFFIC_BYTES = 11638296576 + 11605000704
 CPU_SAMPLE_SECONDS = 12.0
 
 

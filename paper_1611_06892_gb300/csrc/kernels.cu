@@ -1470,8 +1470,14 @@ __device__ bool task_update_umma(unsigned char* smb, int type, const float* X, f
     }
     __syncthreads();                       // the staging buffers are free again
     if (bb + 1 < nbk) prefetch_block(blk_of(bb + 1) * ib);
-    apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, top ? Ct : nullptr, top ? Cs : Cs + c0, ldc, lc, ncols, W, W,
-                  Bh, Bl, um, prm);
+    if (!apply_rm_umma(Vh, Vl, vrows, kb, Tb, notrans, top ? Ct : nullptr, top ? Cs : Cs + c0, ldc, lc, ncols, W, W,
+                       Bh, Bl, um, prm)) {
+      // the MMA completion wait ran out (the error word is set): no further MMA is issued, the copies
+      // in flight are waited for, and nothing is written back
+      cp_async_wait_all();
+      __syncthreads();
+      return true;
+    }
     if (top) {
       store_tile(Ct, lc, 1, Cp, nb, tr, c0, col0, kb, ncols, M_NONE);
       __syncthreads();
