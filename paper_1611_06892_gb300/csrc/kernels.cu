@@ -1041,8 +1041,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint64
   }
 }
 // 32 consecutive TMEM columns of this warp's 32 lanes into v (one column per register).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// 32 consecutive TMEM columns of this warp's 32 lanes into r (no wait: call tmem_wait_ld before use).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
       "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -1051,10 +1051,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Core-matrix index (in floats) of element (row, k) of a K-major operand with kb columns of K.
 __device__ __forceinline__ int core_idx(int row, int k, int kb) {
@@ -1191,14 +1189,23 @@ __device__ bool apply_rm_umma(const float* Vh, const float* Vl, int vrows, int k
   if (ok && mc < mch) {
     const int r = mc * 128 + q * 32 + lane;
     for (int cg = 0; cg < ncols; cg += 32) {
-      float acc[32], part[32];
+      float acc[32];
       const int nc = min(32, ncols - cg);
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = (r < vrows && j < nc) ? C[r + (cg + j) * ldc] : 0.f;
-      for (int ks = 0; ks < nks; ++ks) {
-        tmem_ld32(um.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((mc * nks + ks) * npad + cg), part);
+      // two k-steps per TMEM round trip; the adds stay in increasing k
+      for (int ks = 0; ks < nks; ks += 2) {
+        const uint32_t ta = um.tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((mc * nks + ks) * npad + cg);
+        uint32_t p0[32], p1[32];
+        tmem_ld32_nowait(ta, p0);
+        if (ks + 1 < nks) tmem_ld32_nowait(ta + (uint32_t)npad, p1);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] += part[j];
+        for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(p0[j]);
+        if (ks + 1 < nks) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(p1[j]);
+        }
       }
       if (r < vrows) {
 #pragma unroll
