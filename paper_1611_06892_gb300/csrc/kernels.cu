@@ -1945,13 +1945,13 @@ __device__ int next_task(const ExecParams& prm) {
   int err = 0;
   if (lane == 0) err = ld_relaxed(prm.err);
   if (__shfl_sync(kFull, err, 0) != 0) return n;   // warp-uniform exit
+  int h = 0;
+  if (lane == 0) h = ld_relaxed(prm.head);
+  h = __shfl_sync(kFull, h, 0);     // one head value for the whole warp and the whole scan
+  if (h >= n) return n;
   for (int base = 0; base < prm.window; base += 32) {
-    int h = 0;
-    if (lane == 0) h = ld_relaxed(prm.head);
-    h = __shfl_sync(kFull, h, 0);   // one head value for the whole warp
-    if (h >= n) return n;
     const int i = h + base + lane;
-    int st = 1;
+    int st = 0;                     // entries not inspected (past the window or the queue) stop the skip
     bool ready = false;
     if (i < n && base + lane < prm.window) {
       st = ld_relaxed(prm.done + i);

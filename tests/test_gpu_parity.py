@@ -178,7 +178,7 @@ def test_window_does_not_change_results(torch_mod, m, n, nb, ib, tree, variant, 
     if dtype == "f32":
         dA = dA.float().t().contiguous().t()
     bands = {}
-    settings = [(0, 1), (32, 1), (512, 1), (1024, 1), (0, 0), (512, 0)]
+    settings = [(0, 1), (16, 1), (32, 1), (512, 1), (1024, 1), (0, 0), (512, 0)]
     for window, prio in settings:
         h = G.Handle()
         h.set_option(G.OPT_AUTO_RESOURCES, R_AUTO)
