@@ -73,19 +73,19 @@ enum {
                                      C -= V W product on tcgen05 (one matrix; default), 1 = updates by FP32
                                      FMA on the CUDA cores (FP32-exact products), 2 = three TF32 products on
                                      the warp-level MMA only */
-  BIDIAG_OPT_F32_SCALARS = 8      /* FP32 storage: each reflector's beta, tau and tail scale from alpha and
+  BIDIAG_OPT_F32_SCALARS = 8,     /* FP32 storage: each reflector's beta, tau and tail scale from alpha and
                                      the tail's squared norm (always a compensated sum, FP64-level accuracy)
                                      0 = in float-pair arithmetic, about 44 bits (default), 1 = in FP64.
                                      Both give the FP32 values the reduction stores to within their
-                                     rounding; FP64 costs ~1.7K cycles of serial FP64 latency per column */,
-  BIDIAG_OPT_WINDOW = 9           /* executor look-ahead, -1..1024: a CTA looking for work scans this many
+                                     rounding; FP64 costs ~1.7K cycles of serial FP64 latency per column */
+  BIDIAG_OPT_WINDOW = 9,          /* executor look-ahead, -1..1024: a CTA looking for work scans this many
                                      queue entries from the head and takes the first whose dependencies
                                      are done; only when none is ready does it take the head's entry and
                                      wait for it.  0 = strict queue order; -1 (default) = 1024 for a
                                      one-matrix FP64 BiDiag reduction, else 0 (measured on 8192^2 and
                                      4096^2: 3.2 / 4.1 % faster; FP32 storage, R-BiDiag and batches are
                                      not faster).  Results do not depend on it: the program orders every
-                                     access to shared data, the window only changes timing */,
+                                     access to shared data, the window only changes timing */
   BIDIAG_OPT_PRIORITY = 10        /* queue order of the device program, by bottom level (longest weighted
                                      path to the end) with sub-task weights 1 = Table 1 flops times the
                                      measured time per flop of each sub-task kind (default), 0 = flops
