@@ -1469,9 +1469,10 @@ __device__ bool task_update_umma(unsigned char* smb, int type, const float* X, f
       const int r = o & 31, c = o >> 5;
       Tb[notrans ? r + c * (kb + 4) : c + r * (kb + 4)] = Tr[o];
     }
-    if (top) {
+    if (top) {   // lanes along the columns: the row-major stores are conflict-free
+      const int lgc = ncols == 64 ? 6 : 5;
       for (int o = threadIdx.x; o < kb * ncols; o += kThreads) {
-        const int r = o & 31, c = o >> 5;
+        const int c = o & (ncols - 1), r = o >> lgc;
         Ct[r * lc + c] = tr ? Cr[r * lc + c] : Cr[c * (kb + 4) + r];
       }
     }
